@@ -1,0 +1,42 @@
+"""Seeded synthetic inputs for the 1D problem, shared by the tests, the
+bench and the oracle-based checks.
+
+Holds none of the method's arithmetic: only the initial value u^0 on the
+mesh and the source samples f^1..f^Nt.  Recipes (one per workload):
+
+* ``"sine1_uniform"``: u^0(x) = sin(pi x); f i.i.d. uniform on [-1, 1].
+* ``"sine8_normal"``:  u^0(x) = sum_{k=1}^{8} a_k sin(k pi x), a_k ~ N(0, 1);
+  f i.i.d. N(0, 1).
+
+The mesh is x_i = i h, h = 1/(M+1), i = 1..M (interior points of (0, 1)).
+Random numbers come from numpy's PCG64 generator seeded with ``seed``; the
+amplitudes a_k are drawn first, then f in row-major (Nt, M) order.
+"""
+import numpy as np
+
+
+def mesh(M):
+    h = 1.0 / (M + 1)
+    return h * np.arange(1, M + 1, dtype=np.float64)
+
+
+def make_inputs(M, Nt, seed=0, recipe="sine8_normal"):
+    """Returns (u0 [M], f [Nt, M]) as float64 numpy arrays."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = mesh(M)
+    if recipe == "sine1_uniform":
+        u0 = np.sin(np.pi * x)
+        f = rng.uniform(-1.0, 1.0, size=(Nt, M))
+    elif recipe == "sine8_normal":
+        a = rng.standard_normal(8)
+        u0 = sum(a[k] * np.sin((k + 1) * np.pi * x) for k in range(8))
+        f = rng.standard_normal((Nt, M))
+    else:
+        raise ValueError("unknown recipe %r" % recipe)
+    return np.ascontiguousarray(u0), np.ascontiguousarray(f)
+
+
+def random_vector(Nt, M, seed=0):
+    """A generic space-time vector with N(0, 1) entries (for operator tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((Nt, M))
