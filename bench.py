@@ -1,0 +1,383 @@
+"""Benchmark: unknowns*steps/s to a true relative residual of 1e-10 for the
+all-at-once BDF2 system of the 1D Riesz fractional diffusion equation.
+
+Workload (one step = one full solve, x0 = 0 -> ||F - calA U|| / ||F|| <= 1e-10):
+M = 8191 interior points, Nt = 1024 time steps, kappa = 1, T = 1, alpha cycling
+over {1.2, 1.5, 1.8} by step, u0 = seeded sum of 8 sine modes with N(0,1)
+amplitudes, f i.i.d. N(0,1) (paper_2003_07020_gb300.workloads, "sine8_normal").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+                    [--inner strang|tau] [--impl ours|reference]
+
+Under torchrun every rank solves its own seeded instance (independent
+problems, no data-path collective; "scaling": "weak"); value = total
+unknowns*steps over all ranks / max rank time.  ``--impl reference`` times
+the CPU oracle (sequential BDF2 with LU) on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M_DEF, NT_DEF, ALPHAS = 8191, 1024, (1.2, 1.5, 1.8)
+METRIC = "unknowns·steps/s to rel. residual 1e-10; mixed+learned vs plain FP64, 1 GB300"
+UNIT = "unknowns*steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--inner", default="strang", choices=["strang", "tau"])
+    ap.add_argument("--M", type=int, default=M_DEF)
+    ap.add_argument("--Nt", type=int, default=NT_DEF)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            busy = [s for s in sm if s >= 0.5 * max(sm)] or sm
+            out.update(sm_mhz=statistics.median(busy), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def time_oracle_sample(M, Nt, alpha, n_steps, seed=0):
+    """Times the oracle's sequential BDF2 (dense LU, then forward/back
+    substitutions) on the first n_steps time levels.  Returns (t_lu, t_step)."""
+    from oracle import fcd
+    import scipy.linalg as sla
+    from paper_2003_07020_gb300 import workloads
+    u0, f = workloads.make_inputs(M, Nt, seed=seed)
+    tau = 1.0 / Nt
+    t0 = time.perf_counter()
+    K = fcd.jacobian_1d(alpha, 1.0, M, 1.0 / (M + 1))
+    I = np.eye(M)
+    lu1 = sla.lu_factor(I - tau * K)
+    lu2 = sla.lu_factor(1.5 * I - tau * K)
+    t1 = time.perf_counter()
+    u_prev2, u_prev1 = u0, sla.lu_solve(lu1, tau * f[0] + u0)
+    for k in range(1, n_steps):
+        u = sla.lu_solve(lu2, tau * f[k] + 2.0 * u_prev1 - 0.5 * u_prev2)
+        u_prev2, u_prev1 = u_prev1, u
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / n_steps
+
+
+def cpu_baseline(M, Nt):
+    n_steps = 64
+    t_lu, t_step = time_oracle_sample(M, Nt, 1.8, n_steps)
+    total = t_lu + Nt * t_step
+    return {"value": M * Nt / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": ("sequential BDF2 (numpy/scipy FP64, dense LU) at M=%d, alpha=1.8: LU of both step "
+                       "matrices %.2f s + %d of %d time steps at %.4f s each; value = M*Nt / (LU + Nt*step)"
+                       % (M, t_lu, n_steps, Nt, t_step))}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    M, Nt = args.M, args.Nt
+    n_steps = 16
+    from oracle import fcd
+    import scipy.linalg as sla
+    from paper_2003_07020_gb300 import workloads
+    u0, f = workloads.make_inputs(M, Nt, seed=0)
+    tau = 1.0 / Nt
+    t0 = time.perf_counter()
+    K = fcd.jacobian_1d(1.8, 1.0, M, 1.0 / (M + 1))
+    lu2 = sla.lu_factor(1.5 * np.eye(M) - tau * K)
+    t_lu = time.perf_counter() - t0
+
+    def step(s):
+        up2, up1 = u0, u0
+        for k in range(n_steps):
+            u = sla.lu_solve(lu2, tau * f[(s * n_steps + k) % Nt] + 2.0 * up1 - 0.5 * up2)
+            up2, up1 = up1, u
+        return u
+
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        step(s)
+    dt = time.perf_counter() - t0
+    value = M * n_steps * args.steps / dt
+    sample = ("oracle sequential BDF2 time stepping (numpy/scipy FP64) at M=%d, alpha=1.8; one step = %d "
+              "forward/back substitutions with the dense LU factors (factorisation %.2f s, done once "
+              "before the timed steps)" % (M, n_steps, t_lu))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "1D Riesz FDE all-at-once BDF2, M=%d, Nt=%d, kappa=1" % (M, Nt), "M": M,
+                       "Nt": Nt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# FP64 and FP32 issue rates measured on GB300 by a throughput probe (DFMA and
+# FFMA chains, 152 SMs): ~1.60 DFMA and ~114 FFMA per SM per 2.07 GHz clock.
+FP64_PEAK_TFLOPS = 2 * 1.60 * 152 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 2 * 114.0 * 152 * 2.07e9 / 1e12
+
+
+def fft_flops(n):
+    """Nominal flops of a complex FFT of length n (5 n log2 n)."""
+    return 5.0 * n * np.log2(n)
+
+
+def matvec_flops(M, Nt):
+    """Algorithmic flops of one all-at-once matvec: per time row a real FFT
+    convolution of length L (two complex FFTs of L/2 plus the real-signal
+    split/merge and spectrum product, ~20 flops per half-length point) and
+    the 5-flop BDF band."""
+    L = 4
+    while L < 2 * M:
+        L *= 2
+    return Nt * (2 * fft_flops(L // 2) + 20.0 * (L // 2) + 5.0 * M)
+
+
+def cocg_flops(M, inner, inner_iters_sum, n_apply, nsys):
+    """Algorithmic flops of Step (b): per COCG iteration one Toeplitz product
+    (2 complex FFTs of L) plus one preconditioner solve (Strang: 4, tau: 2
+    complex FFTs of L) and ~40 flops per point of vector updates; each system
+    also applies the preconditioner once before its first iteration."""
+    L = 4
+    while L < 2 * M:
+        L *= 2
+    pre = (4 if inner == "strang" else 2) * fft_flops(L)
+    per_it = 2 * fft_flops(L) + pre + 40.0 * M
+    return inner_iters_sum * per_it + n_apply * nsys * pre
+
+
+def run_ours(args):
+    import torch
+    from paper_2003_07020_gb300 import aao, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    M, Nt = args.M, args.Nt
+    prec = aao.AAO_PREC_MIXED if args.prec == "mixed" else aao.AAO_PREC_FP64
+    inner = aao.AAO_INNER_STRANG if args.inner == "strang" else aao.AAO_INNER_TAU
+    plans, Fs = [], []
+    for i, a in enumerate(ALPHAS):
+        p = aao.Plan(M, Nt, a, kappa=1.0, T=1.0, prec=prec, inner=inner)
+        u0, f = workloads.make_inputs(M, Nt, seed=1000 * rank + i)
+        F = torch.empty((Nt, M), dtype=torch.float64, device=dev)
+        p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
+        plans.append(p)
+        Fs.append(F)
+    U = torch.zeros((Nt, M), dtype=torch.float64, device=dev)
+    infos = []
+
+    def step(s):
+        i = s % len(ALPHAS)
+        U.zero_()
+        return plans[i].gmres_solve(Fs[i], U)
+
+    for s in range(args.warmup):
+        step(s)
+    for p in plans:
+        p.get_profile(reset=True)
+        p.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        ev0.record(stream)
+        for s in range(args.steps):
+            infos.append(step(s))
+        ev1.record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = {}
+    for p in plans:
+        p.set_profiling(False)
+        for k, (t_ms, nl) in p.get_profile(reset=True).items():
+            a, b = prof.get(k, (0.0, 0))
+            prof[k] = (a + t_ms, b + nl)
+    clocks = clk.summary()
+    value = world * M * Nt * args.steps / (ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    Fh = [torch.empty((Nt, M), dtype=torch.float64, pin_memory=True) for _ in ALPHAS]
+    for i in range(len(ALPHAS)):
+        Fh[i].copy_(Fs[i].cpu())
+    Uh = torch.empty((Nt, M), dtype=torch.float64, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        plans[s % len(ALPHAS)].gmres_solve_host(Fh[s % len(ALPHAS)], Uh)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * M * Nt * args.steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": M * Nt * 8, "d2h_bytes_per_step": M * Nt * 8}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    pk = peaks()
+    dom = max(("matvec", "cocg", "tdft_fwd", "tdft_inv", "vector"), key=lambda k: prof[k][0])
+    n_apply = sum(i["outer_iters"] for i in infos)
+    inner_sum = sum(i["inner_iters_sum"] for i in infos)
+    nsys = Nt // 2 + 1
+    if dom == "matvec":
+        t_launch = prof["matvec"][0] / max(prof["matvec"][1], 1)
+        achieved = matvec_flops(M, Nt) / (t_launch * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "matvec_f64_kernel",
+                "peak_source": "FP64 FMA issue rate x 152 SMs x 2.07 GHz (derived)"}
+    elif dom == "cocg":
+        t_launch = prof["cocg"][0] / max(prof["cocg"][1], 1)
+        fl = cocg_flops(M, args.inner, inner_sum, n_apply, nsys) / max(prof["cocg"][1], 1)
+        pkv = FP32_PEAK_TFLOPS if args.prec == "mixed" else FP64_PEAK_TFLOPS
+        achieved = fl / (t_launch * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": pkv, "unit": "TFLOP/s", "frac": achieved / pkv,
+                "traffic": None, "kernel": "cocg_kernel",
+                "peak_source": "FMA issue rate x 152 SMs x 2.07 GHz (derived)"}
+    else:
+        t_launch = prof[dom][0] / max(prof[dom][1], 1)
+        hb = pk.get("hbm_gbs", 6800.0)
+        bytes_ = {"tdft_fwd": 16.0, "tdft_inv": 16.0, "vector": 16.0}[dom] * M * Nt
+        achieved = bytes_ / (t_launch * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hb, "unit": "GB/s", "frac": achieved / hb,
+                "traffic": None, "kernel": dom}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": "1D Riesz FDE all-at-once BDF2 to TRR<=1e-10, M=%d, Nt=%d, alpha cycling %s, "
+                               "kappa=1, T=1, sine8_normal inputs" % (M, Nt, list(ALPHAS)),
+                   "M": M, "Nt": Nt, "precision": args.prec, "inner_precond": args.inner, "restart": 20,
+                   "l2": "no explicit flush: every solve streams a >2 GB Krylov working set through the "
+                         "129 MB L2",
+                   "outer_iters": [i["outer_iters"] for i in infos],
+                   "inner_iters_max": max(i["inner_iters_max"] for i in infos),
+                   "true_rel_res_max": max(i["true_rel_res"] for i in infos),
+                   "stage_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                   "stage_launches": {k: v[1] for k, v in prof.items()}},
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "clocks": clocks, "roofline": roof, "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(M, Nt)
+    print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

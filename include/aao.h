@@ -1,0 +1,184 @@
+/*
+ * aao.h -- C ABI of the GB300 (sm_103a) solver for the all-at-once BDF2
+ * system of the Riesz fractional diffusion equation
+ * (Gu, Zhao, Zhao, Carpentieri, Huang, arXiv:2003.07020).
+ *
+ * Problem (Sec. 2.1, Eqs. 11-12): find U = [u^1; ...; u^Nt] with
+ *     calA U = F,   calA = C (x) I_s - tau I_t (x) K,
+ * C the BDF2 time matrix of Eq. 1.7 (BDF1 in its first row), K the
+ * fractional-centred-difference Jacobian A = -(kappa/h^alpha) T(g)
+ * (Sec. 2.1; Eq. 4.2 in 2D), tau = T/Nt, h = 1/(M+1) on (0,1).
+ *
+ * Notation: alpha is the fractional order (the paper's gamma); eps is the
+ * circulant parameter of the preconditioner (the paper's alpha, Eq. 1.11).
+ *
+ * Conventions for every call below:
+ *   - Vectors are caller-owned DEVICE buffers unless a name ends in _host.
+ *     Space-time vectors are double[Nt][M], row-major: row k is time level
+ *     k+1, space contiguous (the stacking of Eq. 12).  No alignment beyond
+ *     the natural 8 bytes is required.
+ *   - The plan owns all workspace (Krylov bases, spectra, tables); it is
+ *     allocated in aao_plan_create and released in aao_plan_destroy.
+ *   - Work is enqueued on the plan's stream.  aao_matvec and
+ *     aao_bc_precond_apply return without synchronising; aao_gmres_solve and
+ *     aao_gmres_solve_host synchronise the stream before returning.
+ *   - Errors are reported by return code only; aao_last_error gives a
+ *     message for the last failing call on a plan.  A plan is not
+ *     thread-safe: calls on one plan must not overlap.
+ */
+#ifndef AAO_H
+#define AAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AAO_OK = 0,
+  AAO_EINVAL = 1,       /* bad argument (size, pointer, parameter range) */
+  AAO_ENOMEM = 2,       /* device or host allocation failed */
+  AAO_ECUDA = 3,        /* a CUDA runtime call failed */
+  AAO_ENOCONV = 4,      /* solver hit its iteration cap above tolerance */
+  AAO_EBREAKDOWN = 5,   /* Krylov breakdown (zero pivot) */
+  AAO_ENONFINITE = 6    /* NaN or Inf detected */
+} aao_status;
+
+typedef enum {
+  AAO_PREC_FP64 = 0,    /* every step in FP64 ("plain") */
+  AAO_PREC_MIXED = 1    /* preconditioner steps (a)-(c) in FP32, rest FP64 */
+} aao_precision;
+
+typedef enum {
+  AAO_INNER_STRANG = 0, /* Strang circulant of T, applied by Bluestein FFTs */
+  AAO_INNER_TAU = 1     /* natural tau-matrix T - H(T), applied by DST-I (Sec. 3.2) */
+} aao_inner_precond;
+
+/* Problem description (Sec. 2.1).  1D only: dim must be 1. */
+typedef struct {
+  int dim;              /* 1 */
+  int64_t M;            /* interior points; h = 1/(M+1); M+1 a power of two for AAO_INNER_TAU */
+  int64_t Nt;           /* time steps, a power of two >= 4; tau = T/Nt */
+  double T;             /* final time (> 0) */
+  double alpha;         /* fractional order, 1 < alpha <= 2 */
+  double kappa;         /* diffusion coefficient, > 0 */
+  double eps;           /* circulant parameter in (0,1]; <= 0 selects min(0.5, 0.5 tau) (Sec. 4) */
+} aao_problem;
+
+/* Solver options.  aao_default_opts fills the defaults given in brackets. */
+typedef struct {
+  int restart;          /* FGMRES restart length m [20], 1..64 */
+  int max_cycles;       /* restart cycles before AAO_ENOCONV [50] */
+  double tol;           /* true relative residual ||F - calA U||/||F|| [1e-10] */
+  double inner_tol;     /* COCG relative residual per shifted system [1e-6 mixed, 1e-12 fp64] */
+  int inner_maxit;      /* COCG iteration cap per system [200] */
+  aao_precision prec;   /* [AAO_PREC_MIXED] */
+  aao_inner_precond inner; /* [AAO_INNER_STRANG] */
+} aao_opts;
+
+/* Result of a solve. */
+typedef struct {
+  int outer_iters;      /* FGMRES iterations (preconditioner applications) */
+  int cycles;           /* restart cycles */
+  int inner_iters_max;  /* largest COCG iteration count of any shifted system */
+  int matvecs;          /* calA v products, including true-residual checks */
+  double true_rel_res;  /* final ||F - calA U||_2 / ||F||_2 computed in FP64 */
+  int status_detail;    /* AAO_OK, or the inner failure code that was seen */
+  int64_t inner_iters_sum; /* COCG iterations summed over all systems and applications */
+} aao_info;
+
+typedef struct aao_plan aao_plan;
+
+/* Fills *opts with the defaults listed in aao_opts for precision prec. */
+void aao_default_opts(aao_opts* opts, aao_precision prec);
+
+/*
+ * g_k of Eq. 2.4, k = 0 .. n-1, on the HOST in FP64:
+ *   g_k = (-1)^k Gamma(1+alpha) / (Gamma(1+alpha/2-k) Gamma(1+alpha/2+k)),
+ * evaluated by g_0 = Gamma(1+alpha)/Gamma(1+alpha/2)^2 and the ratio
+ * g_{k+1} = g_k (k - alpha/2)/(alpha/2 + k + 1) (from Gamma(z+1) = z Gamma(z)).
+ * g_host: caller-owned host array of n doubles.  AAO_EINVAL if n < 1,
+ * g_host is NULL or alpha is outside (0, 2].
+ */
+aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host);
+
+/*
+ * Creates a plan for one problem: host FP64 setup of g_k, the circulant
+ * embedding spectrum of T, the eigenvalues lambda_n of C_eps (Eq. 1.6a) for
+ * n = 0..Nt/2, the inner preconditioner's spectrum, FFT twiddle tables, and
+ * all device workspace (about (2m+6) * 8 * M * Nt bytes for restart m).
+ * cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * On failure *out is NULL.
+ */
+aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* cuda_stream,
+                           aao_plan** out);
+aao_status aao_plan_destroy(aao_plan* plan);
+
+/* Bytes of device workspace the plan holds. */
+size_t aao_plan_workspace_bytes(const aao_plan* plan);
+
+/*
+ * Right-hand side of Eq. 12: F_1 = tau f^1 + u^0, F_2 = tau f^2 - u^0/2,
+ * F_k = tau f^k (k >= 3).  u0_dev: double[M]; f_dev: double[Nt][M] holding
+ * f^1 .. f^Nt; F_dev: double[Nt][M] output (may alias f_dev).
+ */
+aao_status aao_build_rhs(aao_plan* plan, const double* u0_dev, const double* f_dev, double* F_dev);
+
+/*
+ * w = calA v (Sec. 3.2): row k of w is sum_{j<=2} C[k,k-j] v_{k-j} - tau K v_k,
+ * with the Toeplitz product by circulant embedding and FFT, in FP64.
+ * v_dev, w_dev: double[Nt][M], must not alias.
+ */
+aao_status aao_matvec(aao_plan* plan, const double* v_dev, double* w_dev);
+
+/*
+ * z ~= P_eps^{-1} v by Steps (a)-(c) of Sec. 3.1: (a) scale row k by
+ * eps^{k/Nt} and DFT along time (half spectrum n = 0..Nt/2, Sec. 3.2);
+ * (b) solve (lambda_n I - tau K) x_n = zhat_n for every n by preconditioned
+ * COCG to the plan's inner_tol; (c) inverse DFT along time and unscale.
+ * Precision of (a)-(c) follows opts.prec.  v_dev, z_dev: double[Nt][M];
+ * they may alias.
+ */
+aao_status aao_bc_precond_apply(aao_plan* plan, const double* v_dev, double* z_dev);
+
+/*
+ * Solves calA U = F by restarted right-preconditioned flexible GMRES with
+ * the preconditioner of aao_bc_precond_apply, CGS2 orthogonalisation and
+ * Givens rotations in FP64.  Stops when the true relative residual, computed
+ * in FP64 at the end of a cycle, is <= opts.tol.
+ * F_dev: double[Nt][M]; U_dev: double[Nt][M], initial guess on entry (zero it
+ * for x0 = 0), solution on exit.  info may be NULL.  Returns AAO_ENOCONV if
+ * max_cycles pass without meeting tol (U then holds the last iterate).
+ * Synchronises the plan's stream.
+ */
+aao_status aao_gmres_solve(aao_plan* plan, const double* F_dev, double* U_dev, aao_info* info);
+
+/*
+ * As aao_gmres_solve with HOST buffers: copies F_host to the device, solves
+ * from x0 = 0, copies U back to U_host.  Both are double[Nt][M] in host
+ * memory (pinned memory gives the fastest copies).
+ */
+aao_status aao_gmres_solve_host(aao_plan* plan, const double* F_host, double* U_host, aao_info* info);
+
+/*
+ * Tracing.  When profiling is on, every kernel the plan launches is
+ * bracketed by CUDA events recorded on the plan's stream, and the elapsed
+ * times are accumulated per stage.  Stages: 0 matvec (Sec. 3.2), 1 Step (a)
+ * time DFT, 2 Step (b) shifted solves, 3 Step (c) inverse time DFT,
+ * 4 Gram-Schmidt and other vector kernels.  aao_plan_get_profile
+ * synchronises the stream, fills ms[i] (milliseconds) and launches[i] for
+ * i < AAO_NUM_STAGES, and resets the counters when reset != 0.
+ */
+#define AAO_NUM_STAGES 5
+aao_status aao_plan_set_profiling(aao_plan* plan, int on);
+aao_status aao_plan_get_profile(aao_plan* plan, double* ms, int64_t* launches, int reset);
+
+/* Message for the last failing call on plan (or on plan creation if NULL). */
+const char* aao_last_error(const aao_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAO_H */

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C ABI in ``include/aao.h``.
+
+Argument marshalling only: every step of the solver runs in ``libaao.so``
+(hand-written sm_103a kernels).  Device buffers are passed as torch CUDA
+tensors (float64, contiguous, shape (Nt, M)); the binding checks shapes and
+dtypes and forwards raw pointers and the current torch stream.  There is no
+CPU fallback: if the library is missing, loading raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaao.so")
+
+AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOCONV, AAO_EBREAKDOWN, AAO_ENONFINITE = range(7)
+AAO_PREC_FP64, AAO_PREC_MIXED = 0, 1
+AAO_INNER_STRANG, AAO_INNER_TAU = 0, 1
+STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4: "AAO_ENOCONV",
+                5: "AAO_EBREAKDOWN", 6: "AAO_ENONFINITE"}
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan_destroy",
+            "aao_plan_workspace_bytes", "aao_build_rhs", "aao_matvec", "aao_bc_precond_apply",
+            "aao_gmres_solve", "aao_gmres_solve_host", "aao_plan_set_profiling", "aao_plan_get_profile",
+            "aao_last_error")
+STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector")
+
+
+class AaoProblem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("M", ctypes.c_int64), ("Nt", ctypes.c_int64), ("T", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("kappa", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class AaoOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int), ("prec", ctypes.c_int),
+                ("inner", ctypes.c_int)]
+
+
+class AaoInfo(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("cycles", ctypes.c_int), ("inner_iters_max", ctypes.c_int),
+                ("matvecs", ctypes.c_int), ("true_rel_res", ctypes.c_double), ("status_detail", ctypes.c_int),
+                ("inner_iters_sum", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class AaoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Loads libaao.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libaao.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.aao_default_opts.argtypes = [ctypes.POINTER(AaoOpts), ctypes.c_int]
+    lib.aao_default_opts.restype = None
+    lib.aao_setup_coeffs.argtypes = [dbl, i64, vp]
+    lib.aao_plan_create.argtypes = [ctypes.POINTER(AaoProblem), ctypes.POINTER(AaoOpts), vp,
+                                    ctypes.POINTER(vp)]
+    lib.aao_plan_destroy.argtypes = [vp]
+    lib.aao_plan_workspace_bytes.argtypes = [vp]
+    lib.aao_plan_workspace_bytes.restype = ctypes.c_size_t
+    lib.aao_build_rhs.argtypes = [vp, vp, vp, vp]
+    lib.aao_matvec.argtypes = [vp, vp, vp]
+    lib.aao_bc_precond_apply.argtypes = [vp, vp, vp]
+    lib.aao_gmres_solve.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
+    lib.aao_gmres_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
+    lib.aao_plan_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.aao_plan_get_profile.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.aao_last_error.argtypes = [vp]
+    lib.aao_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("aao_default_opts", "aao_plan_workspace_bytes", "aao_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, plan_handle=None):
+    if status != AAO_OK:
+        msg = load().aao_last_error(plan_handle)
+        raise AaoError(status, msg.decode() if msg else "")
+
+
+def aao_setup_coeffs(alpha, n):
+    """g_0 .. g_{n-1} (Eq. 2.4) computed by the library on the host, FP64."""
+    g = np.empty(int(n), dtype=np.float64)
+    _check(load().aao_setup_coeffs(float(alpha), int(n), g.ctypes.data_as(ctypes.c_void_p)))
+    return g
+
+
+def default_opts(prec=AAO_PREC_MIXED, **kw):
+    o = AaoOpts()
+    load().aao_default_opts(ctypes.byref(o), int(prec))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """An ``aao_plan``: one 1D problem with its device workspace."""
+
+    def __init__(self, M, Nt, alpha, kappa=1.0, T=1.0, eps=0.0, opts=None, stream=None, **opt_kw):
+        lib = load()
+        self.M, self.Nt = int(M), int(Nt)
+        self.problem = AaoProblem(1, self.M, self.Nt, float(T), float(alpha), float(kappa), float(eps))
+        self.opts = opts if opts is not None else default_opts(**opt_kw)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.aao_plan_create(ctypes.byref(self.problem), ctypes.byref(self.opts),
+                                   _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().aao_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def workspace_bytes(self):
+        return load().aao_plan_workspace_bytes(self.handle)
+
+    def _vec(self, t, name):
+        if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+        if t.numel() != self.M * self.Nt:
+            raise ValueError("%s must have Nt*M = %d elements" % (name, self.M * self.Nt))
+        return ctypes.c_void_p(t.data_ptr())
+
+    def set_profiling(self, on=True):
+        """Bracket every kernel launch with CUDA events on the plan's stream."""
+        _check(load().aao_plan_set_profiling(self.handle, int(bool(on))), self.handle)
+
+    def get_profile(self, reset=True):
+        """{stage: (milliseconds, kernel launches)} accumulated since the last reset."""
+        ms = np.zeros(len(STAGES))
+        ln = np.zeros(len(STAGES), dtype=np.int64)
+        _check(load().aao_plan_get_profile(self.handle, ms.ctypes.data_as(ctypes.c_void_p),
+                                           ln.ctypes.data_as(ctypes.c_void_p), int(bool(reset))), self.handle)
+        return {s: (float(ms[i]), int(ln[i])) for i, s in enumerate(STAGES)}
+
+    def build_rhs(self, u0, f, F):
+        if not (u0.is_cuda and u0.numel() == self.M):
+            raise ValueError("u0 must be a CUDA tensor of M elements")
+        _check(load().aao_build_rhs(self.handle, ctypes.c_void_p(u0.data_ptr()), self._vec(f, "f"),
+                                    self._vec(F, "F")), self.handle)
+
+    def matvec(self, v, w):
+        _check(load().aao_matvec(self.handle, self._vec(v, "v"), self._vec(w, "w")), self.handle)
+
+    def bc_precond_apply(self, v, z):
+        _check(load().aao_bc_precond_apply(self.handle, self._vec(v, "v"), self._vec(z, "z")), self.handle)
+
+    def gmres_solve(self, F, U, raise_on_noconv=True):
+        info = AaoInfo()
+        st = load().aao_gmres_solve(self.handle, self._vec(F, "F"), self._vec(U, "U"), ctypes.byref(info))
+        if st != AAO_OK and (raise_on_noconv or st != AAO_ENOCONV):
+            _check(st, self.handle)
+        return info.as_dict()
+
+    def gmres_solve_host(self, F_host, U_host, raise_on_noconv=True):
+        """F_host, U_host: float64 host arrays/tensors of Nt*M elements (pinned preferred)."""
+        def ptr(a, name):
+            n = self.M * self.Nt
+            if hasattr(a, "data_ptr"):  # torch tensor
+                if a.is_cuda or a.element_size() != 8 or not a.is_contiguous() or a.numel() != n:
+                    raise ValueError("%s must be a contiguous float64 host tensor of Nt*M elements" % name)
+                return ctypes.c_void_p(a.data_ptr())
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+                raise ValueError("%s must be a contiguous float64 array of Nt*M elements" % name)
+            return a.ctypes.data_as(ctypes.c_void_p)
+        info = AaoInfo()
+        st = load().aao_gmres_solve_host(self.handle, ptr(F_host, "F_host"), ptr(U_host, "U_host"),
+                                         ctypes.byref(info))
+        if st != AAO_OK and (raise_on_noconv or st != AAO_ENOCONV):
+            _check(st, self.handle)
+        return info.as_dict()
+
+
+# Module-level aliases with the C names, for callers that prefer them.
+def aao_plan_create(M, Nt, alpha, **kw):
+    return Plan(M, Nt, alpha, **kw)
+
+
+def aao_plan_destroy(plan):
+    plan.close()
+
+
+def aao_build_rhs(plan, u0, f, F):
+    plan.build_rhs(u0, f, F)
+
+
+def aao_matvec(plan, v, w):
+    plan.matvec(v, w)
+
+
+def aao_bc_precond_apply(plan, v, z):
+    plan.bc_precond_apply(v, z)
+
+
+def aao_gmres_solve(plan, F, U):
+    return plan.gmres_solve(F, U)
+
+
+def aao_gmres_solve_host(plan, F_host, U_host):
+    return plan.gmres_solve_host(F_host, U_host)

@@ -1,0 +1,210 @@
+// FP64 vector kernels for the flexible GMRES driver: classical Gram-Schmidt
+// with re-orthogonalisation (two passes) fused into three sweeps, the
+// solution update U += Z y, the right-hand side of Eq. 12, and deterministic
+// two-stage reductions (per-block partial sums, then a fixed-order sum).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace aao {
+
+constexpr int kBlasThreads = 256;
+constexpr int kBlasBlocks = 152 * 4;
+constexpr int kMaxVec = 65;
+
+int blas_partial_blocks() { return kBlasBlocks; }
+
+// Block partial sums of NV-vectors held per thread (runtime nv <= kMaxVec):
+// writes partial[blockIdx.x * nv + i].
+template <int NVMAX>
+__device__ __forceinline__ void block_partials(double (&acc)[NVMAX], int nv, double* partial) {
+  __shared__ double sred[kBlasThreads / 32][kMaxVec];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) {
+    if (i >= nv) break;
+    double v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sred[warp][i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double s = 0;
+    for (int w = 0; w < kBlasThreads / 32; ++w) s += sred[w][i];
+    partial[(size_t)blockIdx.x * nv + i] = s;
+  }
+}
+
+template <int NVMAX>
+__global__ void __launch_bounds__(kBlasThreads) dots_kernel(const double* __restrict__ w, const double* __restrict__ V,
+                                                            size_t vstride, int nv, size_t n,
+                                                            double* __restrict__ partial) {
+  double acc[NVMAX];
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) acc[i] = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double we = w[e];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) acc[i] = fma(we, __ldg(&V[i * vstride + e]), acc[i]);
+  }
+  block_partials(acc, nv, partial);
+}
+
+template <int NVMAX>
+__global__ void __launch_bounds__(kBlasThreads) update_dots_kernel(double* __restrict__ w, const double* __restrict__ V,
+                                                                   size_t vstride, int nv, size_t n,
+                                                                   const double* __restrict__ h,
+                                                                   double* __restrict__ partial) {
+  __shared__ double hs[NVMAX];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  double acc[NVMAX];
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) acc[i] = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double vv[NVMAX];
+    double we = w[e];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) { vv[i] = __ldg(&V[i * vstride + e]); we = fma(-hs[i], vv[i], we); }
+    w[e] = we;
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) acc[i] = fma(we, vv[i], acc[i]);
+  }
+  __syncthreads();
+  block_partials(acc, nv, partial);
+}
+
+template <int NVMAX>
+__global__ void __launch_bounds__(kBlasThreads) update_norm_kernel(double* __restrict__ w, const double* __restrict__ V,
+                                                                   size_t vstride, int nv, size_t n,
+                                                                   const double* __restrict__ h,
+                                                                   double* __restrict__ partial) {
+  __shared__ double hs[NVMAX];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  double acc[1] = {0};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double we = w[e];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) we = fma(-hs[i], __ldg(&V[i * vstride + e]), we);
+    w[e] = we;
+    acc[0] = fma(we, we, acc[0]);
+  }
+  __syncthreads();
+  block_partials(acc, 1, partial);
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int nv,
+                                       double* __restrict__ out) {
+  __shared__ double s[256];
+  for (int i = 0; i < nv; ++i) {
+    double a = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partial[(size_t)b * nv + i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = s[0];
+    __syncthreads();
+  }
+}
+
+__global__ void scale_kernel(double* __restrict__ out, const double* __restrict__ in, double a, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = a * in[e];
+}
+
+template <typename TZ, int NZMAX>
+__global__ void __launch_bounds__(kBlasThreads) zy_kernel(double* __restrict__ U, const TZ* __restrict__ Z,
+                                                          size_t zstride, int nz, size_t n,
+                                                          const double* __restrict__ y) {
+  __shared__ double ys[NZMAX];
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double u = U[e];
+#pragma unroll 4
+    for (int j = 0; j < nz; ++j) u = fma(ys[j], (double)__ldg(&Z[j * zstride + e]), u);
+    U[e] = u;
+  }
+}
+
+__global__ void build_rhs_kernel(const double* __restrict__ u0, const double* __restrict__ f, double* __restrict__ F,
+                                 double tau, int M, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = tau * f[e];
+    if (e < (size_t)M) v += u0[e];
+    else if (e < 2 * (size_t)M) v -= 0.5 * u0[e - M];
+    F[e] = v;
+  }
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = (double)in[e];
+}
+
+// Dispatch on the number of vectors with a few compile-time caps.
+#define AAO_NV_DISPATCH(KERNEL, nv, ...)                                                          \
+  do {                                                                                            \
+    if (nv <= 4) KERNEL<4><<<kBlasBlocks, kBlasThreads, 0, s>>>(__VA_ARGS__);                     \
+    else if (nv <= 8) KERNEL<8><<<kBlasBlocks, kBlasThreads, 0, s>>>(__VA_ARGS__);                \
+    else if (nv <= 16) KERNEL<16><<<kBlasBlocks, kBlasThreads, 0, s>>>(__VA_ARGS__);              \
+    else if (nv <= 24) KERNEL<24><<<kBlasBlocks, kBlasThreads, 0, s>>>(__VA_ARGS__);              \
+    else if (nv <= 32) KERNEL<32><<<kBlasBlocks, kBlasThreads, 0, s>>>(__VA_ARGS__);              \
+    else if (nv <= kMaxVec) KERNEL<kMaxVec><<<kBlasBlocks, kBlasThreads, 0, s>>>(__VA_ARGS__);    \
+    else return cudaErrorInvalidValue;                                                            \
+  } while (0)
+
+cudaError_t launch_dots(const double* w, const double* V, size_t vstride, int nv, size_t n, double* partial,
+                        cudaStream_t s) {
+  AAO_NV_DISPATCH(dots_kernel, nv, w, V, vstride, nv, n, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_update_dots(double* w, const double* V, size_t vstride, int nv, size_t n, const double* h,
+                               double* partial, cudaStream_t s) {
+  AAO_NV_DISPATCH(update_dots_kernel, nv, w, V, vstride, nv, n, h, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_update_norm(double* w, const double* V, size_t vstride, int nv, size_t n, const double* h,
+                               double* partial, cudaStream_t s) {
+  AAO_NV_DISPATCH(update_norm_kernel, nv, w, V, vstride, nv, n, h, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_reduce_partials(const double* partial, int nblocks, int nv, double* out, cudaStream_t s) {
+  reduce_partials_kernel<<<1, 256, 0, s>>>(partial, nblocks, nv, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale(double* out, const double* in, double a, size_t n, cudaStream_t s) {
+  scale_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(out, in, a, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
+                                 cudaStream_t s) {
+  if (nz > kMaxVec) return cudaErrorInvalidValue;
+  zy_kernel<float, kMaxVec><<<kBlasBlocks, kBlasThreads, 0, s>>>(U, Z, zstride, nz, n, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int nz, size_t n, const double* y,
+                                 cudaStream_t s) {
+  if (nz > kMaxVec) return cudaErrorInvalidValue;
+  zy_kernel<double, kMaxVec><<<kBlasBlocks, kBlasThreads, 0, s>>>(U, Z, zstride, nz, n, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_build_rhs(const double* u0, const double* f, double* F, double tau, int M, int Nt,
+                             cudaStream_t s) {
+  build_rhs_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(u0, f, F, tau, M, (size_t)M * Nt);
+  return cudaGetLastError();
+}
+cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s) {
+  f32_to_f64_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace aao

@@ -1,0 +1,237 @@
+// Step (b) of the block-circulant preconditioner (Sec. 3.1): for every
+// frequency n = 0 .. Nt/2 solve the complex-shifted Toeplitz system
+//     (lambda_n I - tau K) x = zhat_n,    -tau K = c T,
+// by preconditioned COCG (conjugate-orthogonal CG: CG with the bilinear form
+// u^T w, which is the right Krylov method for a complex SYMMETRIC matrix).
+//
+// One CTA solves one system with all iterations inside the kernel.  Products
+// with T use the length-L circulant embedding (FFT in shared memory); the
+// preconditioner is either
+//   * the Strang circulant S of T: (lambda I + c S)^{-1} r = IDFT_M(DFT_M(r)
+//     / (lambda + c s_hat)), each length-M DFT done by Bluestein's chirp-z
+//     convolution with length-L FFTs; or
+//   * the natural tau matrix tau(T) = T - H(T) (the tau-algebra approximation
+//     of Sec. 3.2): (lambda I + c tau(T))^{-1} r = (2/(M+1)) S D S r with the
+//     DST-I matrix S, each DST done as an FFT of length L = 2(M+1) of the odd
+//     extension.
+// Vectors r and p live in global memory (L2-resident per-system workspace);
+// x accumulates in the output buffer.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace aao {
+
+template <typename R> struct Tabs;
+template <> struct Tabs<float> { using type = CocgTables32; };
+template <> struct Tabs<double> { using type = CocgTables64; };
+
+template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
+  const auto d = b.x * b.x + b.y * b.y;
+  return C{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+
+// buf <- FFT-domain product: DIF, multiply by kernel, DIT.  The multiply is
+// given as a functor of (position p) -> complex factor.
+template <typename C, typename F>
+__device__ __forceinline__ void convolve(C* buf, int logL, const C* __restrict__ tw, F factor) {
+  __syncthreads();
+  fft_forward(buf, logL, 1, 0, tw, 0);
+  const int L = 1 << logL;
+  for (int p = threadIdx.x; p < L; p += blockDim.x) buf[pad16(p)] = cmul(buf[pad16(p)], factor(p));
+  __syncthreads();
+  fft_backward(buf, logL, 1, 0, tw, 0);
+}
+
+// z = P^{-1} r, written to buf[pad16(i)], i < M (natural order).
+template <typename R, int KIND>
+__device__ __forceinline__ void precond(typename cplx_t<R>::type* buf, const typename cplx_t<R>::type* r, int M,
+                                        int logL, typename cplx_t<R>::type lam, const typename Tabs<R>::type& tb) {
+  using C = typename cplx_t<R>::type;
+  const int L = 1 << logL;
+  if (KIND == 0) {
+    // a_j = r_j w_j, zero-padded; c = a * conj-chirp filter; X_k = w_k c_k;
+    // then a'_k = X_k conj(w_k) / (M (lambda + s_k)) = c_k / (M (lambda + s_k)); z_j = conj(w_j) (a' * chirp filter)_j
+    for (int j = threadIdx.x; j < L; j += blockDim.x)
+      buf[pad16(j)] = (j < M) ? cmul(r[j], __ldg(&tb.chirp[j])) : C{0, 0};
+    convolve(buf, logL, tb.twL, [&](int p) { return __ldg(&tb.chat_br[p]); });
+    const R invM = (R)1 / (R)M;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+      if (k < M) {
+        C d = lam;
+        d.x += __ldg(&tb.seig[k]);
+        buf[pad16(k)] = cscale(cdiv(buf[pad16(k)], d), invM);
+      } else {
+        buf[pad16(k)] = C{0, 0};
+      }
+    }
+    convolve(buf, logL, tb.twL, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); });
+    for (int j = threadIdx.x; j < M; j += blockDim.x) buf[pad16(j)] = cmulc(buf[pad16(j)], __ldg(&tb.chirp[j]));
+    __syncthreads();
+  } else {
+    // odd extension y (length L = 2(M+1)), DIF, multiply by 1/(L (lambda + c sigma_f)), DIT; z_{l-1} = buf[l]
+    const int Mp1 = M + 1;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+      C y{0, 0};
+      if (l >= 1 && l <= M) y = r[l - 1];
+      else if (l > Mp1) { const C t = r[L - l - 1]; y = C{-t.x, -t.y}; }
+      buf[pad16(l)] = y;
+    }
+    const R invL = (R)1 / (R)L;
+    convolve(buf, logL, tb.twL, [&](int p) {
+      const int f = bitrev(p, logL);
+      if (f == 0 || f == Mp1) return C{0, 0};
+      C d = lam;
+      d.x += __ldg(&tb.taueig_br[p]);
+      return cdiv(C{invL, 0}, d);
+    });
+    // z_i = buf[pad16(i + 1)], see z_at
+  }
+}
+
+template <typename R, int KIND>
+__device__ __forceinline__ typename cplx_t<R>::type z_at(const typename cplx_t<R>::type* buf, int i) {
+  return KIND == 0 ? buf[pad16(i)] : buf[pad16(i + 1)];
+}
+
+template <typename R, int KIND, bool GBUF>
+__global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __restrict__ xb,
+                                                   typename cplx_t<R>::type* __restrict__ rws,
+                                                   typename cplx_t<R>::type* __restrict__ pws,
+                                                   typename cplx_t<R>::type* __restrict__ gbuf, int M, int logL,
+                                                   int nsys, typename Tabs<R>::type tb, R tol, int maxit,
+                                                   int* __restrict__ iters, int* __restrict__ flags) {
+  using C = typename cplx_t<R>::type;
+  extern __shared__ unsigned char smraw[];
+  __shared__ R red[4 * 32];
+  C* buf = GBUF ? gbuf + (size_t)blockIdx.x * padded_size(1 << logL) : reinterpret_cast<C*>(smraw);
+  const int L = 1 << logL;
+  for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
+    const double2 lamd = tb.lambda[n];
+    const C lam = C{(R)lamd.x, (R)lamd.y};
+    C* x = xb + (size_t)n * M;
+    C* r = rws + (size_t)n * M;
+    C* p = pws + (size_t)n * M;
+    R nb2[1] = {0};
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const C b = x[i];
+      r[i] = b;
+      x[i] = C{0, 0};
+      nb2[0] += b.x * b.x + b.y * b.y;
+    }
+    block_sum<R, 1>(nb2, red);
+    if (nb2[0] == (R)0) {
+      if (threadIdx.x == 0) { iters[n] = 0; flags[n] = 0; }
+      continue;
+    }
+    const R thr = tol * tol * nb2[0];
+    precond<R, KIND>(buf, r, M, logL, lam, tb);
+    R rho2[2] = {0, 0};
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const C z = z_at<R, KIND>(buf, i);
+      const C ri = r[i];
+      rho2[0] += ri.x * z.x - ri.y * z.y;
+      rho2[1] += ri.x * z.y + ri.y * z.x;
+      p[i] = z;
+    }
+    block_sum<R, 2>(rho2, red);
+    C rho{rho2[0], rho2[1]};
+    int it = 0, flag = 1;
+    while (it < maxit) {
+      // q = (lambda I + c T) p
+      for (int j = threadIdx.x; j < L; j += blockDim.x) buf[pad16(j)] = (j < M) ? p[j] : C{0, 0};
+      convolve(buf, logL, tb.twL, [&](int q) { return C{__ldg(&tb.Ebr[q]), (R)0}; });
+      R pq2[2] = {0, 0};
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const C pi = p[i];
+        const C q = cadd(buf[pad16(i)], cmul(lam, pi));
+        buf[pad16(i)] = q;
+        pq2[0] += pi.x * q.x - pi.y * q.y;
+        pq2[1] += pi.x * q.y + pi.y * q.x;
+      }
+      block_sum<R, 2>(pq2, red);
+      const C pq{pq2[0], pq2[1]};
+      if (!(pq.x * pq.x + pq.y * pq.y > (R)0)) { flag = 2; break; }
+      const C a = cdiv(rho, pq);
+      R rr[1] = {0};
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const C pi = p[i];
+        const C q = buf[pad16(i)];
+        C xi = x[i];
+        xi = cadd(xi, cmul(a, pi));
+        x[i] = xi;
+        C ri = r[i];
+        ri = csub(ri, cmul(a, q));
+        r[i] = ri;
+        rr[0] += ri.x * ri.x + ri.y * ri.y;
+      }
+      block_sum<R, 1>(rr, red);
+      ++it;
+      if (!(rr[0] == rr[0]) || rr[0] > (R)1e30 * nb2[0]) { flag = 3; break; }
+      if (rr[0] <= thr) { flag = 0; break; }
+      precond<R, KIND>(buf, r, M, logL, lam, tb);
+      R rn2[2] = {0, 0};
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const C z = z_at<R, KIND>(buf, i);
+        const C ri = r[i];
+        rn2[0] += ri.x * z.x - ri.y * z.y;
+        rn2[1] += ri.x * z.y + ri.y * z.x;
+      }
+      block_sum<R, 2>(rn2, red);
+      const C rho_new{rn2[0], rn2[1]};
+      if (!(rho.x * rho.x + rho.y * rho.y > (R)0)) { flag = 2; break; }
+      const C beta = cdiv(rho_new, rho);
+      rho = rho_new;
+      for (int i = threadIdx.x; i < M; i += blockDim.x) p[i] = cadd(z_at<R, KIND>(buf, i), cmul(beta, p[i]));
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) { iters[n] = it; flags[n] = flag; }
+    __syncthreads();
+  }
+  (void)L;
+}
+
+template <typename R>
+static size_t cocg_smem(int logL) { return (size_t)padded_size(1 << logL) * sizeof(typename cplx_t<R>::type); }
+
+static const size_t kSmemLimit = 200 * 1024;
+
+size_t cocg_gbuf_elems_f64(int logL, int grid) {
+  if (cocg_smem<double>(logL) <= kSmemLimit) return 0;
+  return (size_t)padded_size(1 << logL) * (size_t)grid;
+}
+
+template <typename R, int KIND, bool GBUF>
+static cudaError_t launch_k(typename cplx_t<R>::type* xb, typename cplx_t<R>::type* rws,
+                            typename cplx_t<R>::type* pws, typename cplx_t<R>::type* gbuf, int M, int logL,
+                            int nsys, const typename Tabs<R>::type& tb, R tol, int maxit, int* iters, int* flags,
+                            int grid, cudaStream_t s) {
+  const size_t smem = GBUF ? 0 : cocg_smem<R>(logL);
+  cudaError_t e = cudaFuncSetAttribute(cocg_kernel<R, KIND, GBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cocg_kernel<R, KIND, GBUF><<<grid, 512, smem, s>>>(xb, rws, pws, gbuf, M, logL, nsys, tb, tol, maxit, iters,
+                                                     flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys, int inner,
+                            const CocgTables32& tb, float tol, int maxit, int* iters, int* flags, int grid,
+                            cudaStream_t s) {
+  if (inner == 0)
+    return launch_k<float, 0, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+  return launch_k<float, 1, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+}
+
+cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gbuf, int M, int logL, int nsys,
+                            int inner, const CocgTables64& tb, double tol, int maxit, int* iters, int* flags,
+                            int grid, cudaStream_t s) {
+  const bool g = cocg_smem<double>(logL) > kSmemLimit;
+  if (inner == 0) {
+    if (g) return launch_k<double, 0, true>(xb, rws, pws, gbuf, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+    return launch_k<double, 0, false>(xb, rws, pws, gbuf, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+  }
+  if (g) return launch_k<double, 1, true>(xb, rws, pws, gbuf, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+  return launch_k<double, 1, false>(xb, rws, pws, gbuf, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+}
+
+}  // namespace aao

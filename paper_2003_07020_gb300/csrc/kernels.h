@@ -1,0 +1,89 @@
+// Launchers of the sm_103a kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace aao {
+
+// ---- all-at-once matvec (FP64), matvec.cu -------------------------------------------
+// w = calA v, or w = rhs - calA v when rhs != nullptr.  v is double or float.
+// If sq_partial != nullptr, sq_partial[k] = sum_i w[k][i]^2 for every row k.
+cudaError_t launch_matvec_f64(const double* v, const double* rhs, double* w, double* sq_partial,
+                              int M, int Nt, int logL, const double* Ehalf, const double2* twL,
+                              cudaStream_t s);
+cudaError_t launch_matvec_f64_fin(const float* v, const double* rhs, double* w, double* sq_partial,
+                                  int M, int Nt, int logL, const double* Ehalf, const double2* twL,
+                                  cudaStream_t s);
+size_t matvec_smem_bytes(int logL);
+
+// ---- time DFT, Steps (a) and (c), tdft.cu -------------------------------------------
+// Step (a): out[n][i] = sum_k scale[k] theta^{nk} v[k][i], n = 0..Nt/2, theta = exp(2 pi i/Nt)
+cudaError_t launch_tdft_fwd_f32(const double* v, float2* out, int M, int Nt, const float* scale,
+                                const float2* twNt, cudaStream_t s);
+cudaError_t launch_tdft_fwd_f64(const double* v, double2* out, int M, int Nt, const double* scale,
+                                const double2* twNt, cudaStream_t s);
+// Step (c): z[k][i] = scale_inv[k] * Re sum_{n<Nt} x_n theta^{-nk}, x_{Nt-n} = conj(x_n)
+cudaError_t launch_tdft_inv_f32(const float2* in, float* z, int M, int Nt, const float* scale_inv,
+                                const float2* twNt, cudaStream_t s);
+cudaError_t launch_tdft_inv_f32_to_f64(const float2* in, double* z, int M, int Nt,
+                                       const float* scale_inv, const float2* twNt, cudaStream_t s);
+cudaError_t launch_tdft_inv_f64(const double2* in, double* z, int M, int Nt, const double* scale_inv,
+                                const double2* twNt, cudaStream_t s);
+
+// ---- shifted solves, Step (b), cocg.cu -----------------------------------------------
+struct CocgTables32 {
+  const float2* twL;      // exp(-2 pi i m/L), m < L/2
+  const float* Ebr;       // c * DFT_L(e) / L, bit-reversed
+  const double2* lambda;  // lambda_n, n < nsys
+  const float2* chirp;    // Strang: exp(-pi i j^2/M)
+  const float2* chat_br;  // Strang: DFT_L(conj chirp filter)/L, bit-reversed
+  const float* seig;      // Strang: c * eigenvalues of S
+  const float* taueig_br; // tau: c * sigma_f, bit-reversed frequency order
+};
+struct CocgTables64 {
+  const double2* twL;
+  const double* Ebr;
+  const double2* lambda;
+  const double2* chirp;
+  const double2* chat_br;
+  const double* seig;
+  const double* taueig_br;
+};
+// xb: [nsys][M] complex, right-hand sides on entry, solutions on exit.
+// rws, pws: [nsys][M] complex workspace.  gbuf: global FFT scratch used when
+// the transform does not fit in shared memory (may be null otherwise).
+// iters[n]: iterations used; flags[n]: 0 ok, 1 not converged, 2 breakdown, 3 non-finite.
+cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys,
+                            int inner, const CocgTables32& tb, float tol, int maxit, int* iters,
+                            int* flags, int grid, cudaStream_t s);
+cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gbuf, int M, int logL,
+                            int nsys, int inner, const CocgTables64& tb, double tol, int maxit,
+                            int* iters, int* flags, int grid, cudaStream_t s);
+size_t cocg_gbuf_elems_f64(int logL, int grid);
+
+// ---- vector kernels (FP64), blas.cu ----------------------------------------------------
+int blas_partial_blocks();
+// partial[b*nv + i] = sum over block b's elements of w[e] * V[i*vstride + e]
+cudaError_t launch_dots(const double* w, const double* V, size_t vstride, int nv, size_t n,
+                        double* partial, cudaStream_t s);
+// w -= sum_i h[i] V_i; then partial dots of the updated w with V_i
+cudaError_t launch_update_dots(double* w, const double* V, size_t vstride, int nv, size_t n,
+                               const double* h, double* partial, cudaStream_t s);
+// w -= sum_i h[i] V_i; then partial sum of squares of the updated w
+cudaError_t launch_update_norm(double* w, const double* V, size_t vstride, int nv, size_t n,
+                               const double* h, double* partial, cudaStream_t s);
+// out[i] = sum_b partial[b*nv + i], fixed order
+cudaError_t launch_reduce_partials(const double* partial, int nblocks, int nv, double* out,
+                                   cudaStream_t s);
+cudaError_t launch_scale(double* out, const double* in, double a, size_t n, cudaStream_t s);
+// U += sum_j y[j] Z_j  (Z float or double)
+cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n,
+                                 const double* y, cudaStream_t s);
+cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int nz, size_t n,
+                                 const double* y, cudaStream_t s);
+cudaError_t launch_build_rhs(const double* u0, const double* f, double* F, double tau, int M, int Nt,
+                             cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
+
+}  // namespace aao

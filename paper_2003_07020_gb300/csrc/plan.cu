@@ -1,0 +1,566 @@
+// The C ABI of include/aao.h: plan creation (host FP64 setup + device
+// workspace), the three hot-path calls, and the restarted flexible GMRES
+// driver (Sec. 4: right preconditioning, x0 = 0, stopping on the true
+// relative residual).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/aao.h"
+#include "kernels.h"
+#include "setup.h"
+
+extern "C" int aao_setup_coeffs_impl(double alpha, int64_t n, double* g);
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kMaxRestart = 64;
+
+__global__ void iter_stats_kernel(const int* __restrict__ iters, const int* __restrict__ flags, int n,
+                                  int* __restrict__ out) {
+  __shared__ int smax[256], fmax_[256], ssum[256];
+  int a = 0, b = 0, c = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { a = max(a, iters[i]); b = max(b, flags[i]); c += iters[i]; }
+  smax[threadIdx.x] = a;
+  fmax_[threadIdx.x] = b;
+  ssum[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smax[threadIdx.x] = max(smax[threadIdx.x], smax[threadIdx.x + o]);
+      fmax_[threadIdx.x] = max(fmax_[threadIdx.x], fmax_[threadIdx.x + o]);
+      ssum[threadIdx.x] += ssum[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = smax[0]; out[1] = fmax_[0]; out[2] = ssum[0]; }
+}
+
+}  // namespace
+
+struct aao_plan {
+  aao_problem prob{};
+  aao_opts opts{};
+  cudaStream_t stream = nullptr;
+  aao::HostTables ht;
+  int M = 0, Nt = 0, logL = 0, nsys = 0, m = 0;
+  size_t n = 0;
+  bool mixed = true;
+  std::vector<void*> allocs;
+  size_t ws_bytes = 0;
+  std::string err;
+  // tables
+  double* Ehalf = nullptr;
+  double2* twL64 = nullptr;
+  float2* twL32 = nullptr;
+  double2* twNt64 = nullptr;
+  float2* twNt32 = nullptr;
+  double* Ebr64 = nullptr;
+  float* Ebr32 = nullptr;
+  double2* lambda = nullptr;
+  double* sfwd64 = nullptr;
+  double* sinv64 = nullptr;
+  float* sfwd32 = nullptr;
+  float* sinv32 = nullptr;
+  double2* chirp64 = nullptr;
+  float2* chirp32 = nullptr;
+  double2* chat64 = nullptr;
+  float2* chat32 = nullptr;
+  double* seig64 = nullptr;
+  float* seig32 = nullptr;
+  double* tau64 = nullptr;
+  float* tau32 = nullptr;
+  // workspace
+  double* V = nullptr;   // (m+1) x n
+  void* Z = nullptr;     // m x n, float (mixed) or double
+  void* spec = nullptr;  // nsys x M complex
+  void* rws = nullptr;
+  void* pws = nullptr;
+  double2* gbuf = nullptr;
+  int cocg_grid = 0;
+  int* iters = nullptr;
+  int* flags = nullptr;
+  int* stats = nullptr;
+  double* partial = nullptr;
+  double* hdev = nullptr;   // 3 x kMaxVec doubles + y
+  double* sq = nullptr;     // Nt row partials
+  double* pinned = nullptr; // host pinned scratch
+  double* Fh = nullptr;     // device copies for the host-buffer entry point
+  double* Uh = nullptr;
+  // tracing (aao_plan_set_profiling / aao_plan_get_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  cudaEvent_t ev_open = nullptr;
+  double prof_ms[AAO_NUM_STAGES] = {0};
+  int64_t prof_launches[AAO_NUM_STAGES] = {0};
+};
+
+namespace {
+
+aao_status fail(aao_plan* p, aao_status st, const std::string& msg) {
+  if (p) p->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(p, AAO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+enum { ST_MATVEC = 0, ST_TDFT_FWD = 1, ST_COCG = 2, ST_TDFT_INV = 3, ST_VEC = 4 };
+
+cudaEvent_t take_event(aao_plan* p) {
+  if (!p->ev_pool.empty()) {
+    cudaEvent_t e = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_begin(aao_plan* p) {
+  if (!p->prof_on) return;
+  p->ev_open = take_event(p);
+  cudaEventRecord(p->ev_open, p->stream);
+}
+
+void prof_end(aao_plan* p, int stage, int nkern) {
+  p->prof_launches[stage] += nkern;
+  if (!p->prof_on || !p->ev_open) return;
+  cudaEvent_t e = take_event(p);
+  cudaEventRecord(e, p->stream);
+  p->ev_pending.push_back({stage, {p->ev_open, e}});
+  p->ev_open = nullptr;
+}
+
+// Launch `call` (which enqueues nkern kernels) as part of stage `stage`.
+#define LAUNCH(stage, nkern, call)       \
+  do {                                   \
+    prof_begin(p);                       \
+    CK(call);                            \
+    prof_end(p, stage, nkern);           \
+  } while (0)
+
+template <typename T>
+aao_status dalloc(aao_plan* p, T** ptr, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return fail(p, AAO_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  p->allocs.push_back(q);
+  p->ws_bytes += bytes;
+  *ptr = static_cast<T*>(q);
+  return AAO_OK;
+}
+
+template <typename Td, typename Ts>
+aao_status upload(aao_plan* p, Td** dst, const std::vector<Ts>& src) {
+  std::vector<Td> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (Td)src[i];
+  aao_status st = dalloc(p, dst, tmp.size());
+  if (st != AAO_OK) return st;
+  CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(Td), cudaMemcpyHostToDevice));
+  return AAO_OK;
+}
+
+template <typename Td>
+aao_status upload_c(aao_plan* p, Td** dst, const std::vector<aao::cd>& src) {
+  std::vector<Td> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) {
+    tmp[i].x = (decltype(tmp[i].x))src[i].real();
+    tmp[i].y = (decltype(tmp[i].y))src[i].imag();
+  }
+  aao_status st = dalloc(p, dst, tmp.size());
+  if (st != AAO_OK) return st;
+  CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(Td), cudaMemcpyHostToDevice));
+  return AAO_OK;
+}
+
+#define TRY(x)                         \
+  do {                                 \
+    aao_status s_ = (x);               \
+    if (s_ != AAO_OK) return s_;       \
+  } while (0)
+
+// sum of the first cnt doubles of a device array of per-block partials -> host
+aao_status reduce_to_host(aao_plan* p, const double* partials, int nblocks, int nv, double* host_out) {
+  LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(partials, nblocks, nv, p->hdev, p->stream));
+  CK(cudaMemcpyAsync(p->pinned, p->hdev, nv * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  std::memcpy(host_out, p->pinned, nv * sizeof(double));
+  return AAO_OK;
+}
+
+aao_status matvec_any(aao_plan* p, const void* v, bool v_is_f32, const double* rhs, double* w, double* sq) {
+  if (v_is_f32)
+    LAUNCH(ST_MATVEC, 1, aao::launch_matvec_f64_fin((const float*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->Ehalf,
+                                                    p->twL64, p->stream));
+  else
+    LAUNCH(ST_MATVEC, 1, aao::launch_matvec_f64((const double*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->Ehalf,
+                                                p->twL64, p->stream));
+  return AAO_OK;
+}
+
+// out = P^{-1} v.  out_kind: 0 float (mixed Z basis), 1 double.
+aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
+  if (p->mixed) {
+    float2* spec = (float2*)p->spec;
+    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f32(v, spec, p->M, p->Nt, p->sfwd32, p->twNt32, p->stream));
+    aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
+    LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
+                                            (int)p->opts.inner, tb, (float)p->opts.inner_tol, p->opts.inner_maxit,
+                                            p->iters, p->flags, p->cocg_grid, p->stream));
+    if (out_kind == 0)
+      LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32(spec, (float*)out, p->M, p->Nt, p->sinv32, p->twNt32,
+                                                      p->stream));
+    else
+      LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32_to_f64(spec, (double*)out, p->M, p->Nt, p->sinv32,
+                                                             p->twNt32, p->stream));
+  } else {
+    double2* spec = (double2*)p->spec;
+    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f64(v, spec, p->M, p->Nt, p->sfwd64, p->twNt64, p->stream));
+    aao::CocgTables64 tb{p->twL64, p->Ebr64, p->lambda, p->chirp64, p->chat64, p->seig64, p->tau64};
+    LAUNCH(ST_COCG, 1, aao::launch_cocg_f64(spec, (double2*)p->rws, (double2*)p->pws, p->gbuf, p->M, p->logL,
+                                            p->nsys, (int)p->opts.inner, tb, p->opts.inner_tol, p->opts.inner_maxit,
+                                            p->iters, p->flags, p->cocg_grid, p->stream));
+    LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f64(spec, (double*)out, p->M, p->Nt, p->sinv64, p->twNt64,
+                                                    p->stream));
+  }
+  return AAO_OK;
+}
+
+aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
+  if (!prob || !o) return fail(nullptr, AAO_EINVAL, "null problem or options");
+  if (prob->dim != 1) return fail(nullptr, AAO_EINVAL, "only dim = 1 is supported");
+  if (prob->M < 1 || prob->M > 8191) return fail(nullptr, AAO_EINVAL, "M must be in [1, 8191]");
+  if (prob->Nt < 4 || prob->Nt > 65536 || (prob->Nt & (prob->Nt - 1)))
+    return fail(nullptr, AAO_EINVAL, "Nt must be a power of two in [4, 65536]");
+  if (o->restart < 1 || o->restart > kMaxRestart) return fail(nullptr, AAO_EINVAL, "restart must be in [1, 64]");
+  if (o->max_cycles < 1) return fail(nullptr, AAO_EINVAL, "max_cycles must be >= 1");
+  if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(nullptr, AAO_EINVAL, "tolerances must be > 0");
+  if (o->inner_maxit < 1) return fail(nullptr, AAO_EINVAL, "inner_maxit must be >= 1");
+  if (o->prec != AAO_PREC_FP64 && o->prec != AAO_PREC_MIXED) return fail(nullptr, AAO_EINVAL, "bad precision");
+  if (o->inner != AAO_INNER_STRANG && o->inner != AAO_INNER_TAU) return fail(nullptr, AAO_EINVAL, "bad inner");
+  if (o->inner == AAO_INNER_TAU && ((prob->M + 1) & prob->M))
+    return fail(nullptr, AAO_EINVAL, "the tau preconditioner needs M+1 to be a power of two");
+  return AAO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void aao_default_opts(aao_opts* o, aao_precision prec) {
+  if (!o) return;
+  o->restart = 20;
+  o->max_cycles = 50;
+  o->tol = 1e-10;
+  o->inner_tol = prec == AAO_PREC_MIXED ? 1e-6 : 1e-12;
+  o->inner_maxit = 200;
+  o->prec = prec;
+  o->inner = AAO_INNER_STRANG;
+}
+
+aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host) {
+  if (aao_setup_coeffs_impl(alpha, n, g_host) != 0)
+    return fail(nullptr, AAO_EINVAL, "aao_setup_coeffs: need n >= 1, g_host != NULL, 0 < alpha <= 2");
+  return AAO_OK;
+}
+
+const char* aao_last_error(const aao_plan* plan) {
+  return plan ? plan->err.c_str() : g_create_error.c_str();
+}
+
+size_t aao_plan_workspace_bytes(const aao_plan* plan) { return plan ? plan->ws_bytes : 0; }
+
+aao_status aao_plan_destroy(aao_plan* p) {
+  if (!p) return AAO_OK;
+  for (auto& pr : p->ev_pending) {
+    cudaEventDestroy(pr.second.first);
+    cudaEventDestroy(pr.second.second);
+  }
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (void* q : p->allocs) cudaFree(q);
+  if (p->pinned) cudaFreeHost(p->pinned);
+  delete p;
+  return AAO_OK;
+}
+
+aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* cuda_stream, aao_plan** out) {
+  if (!out) return fail(nullptr, AAO_EINVAL, "out is NULL");
+  *out = nullptr;
+  TRY(check_problem(prob, opts));
+  aao_plan* p = new aao_plan();
+  p->prob = *prob;
+  p->opts = *opts;
+  p->stream = (cudaStream_t)cuda_stream;
+  p->mixed = opts->prec == AAO_PREC_MIXED;
+  const char* emsg = nullptr;
+  if (!aao::build_tables(prob->M, prob->Nt, prob->T, prob->alpha, prob->kappa, prob->eps, p->ht, &emsg)) {
+    delete p;
+    return fail(nullptr, AAO_EINVAL, emsg);
+  }
+  p->M = (int)prob->M;
+  p->Nt = (int)prob->Nt;
+  p->logL = p->ht.logL;
+  p->nsys = p->Nt / 2 + 1;
+  p->m = opts->restart;
+  p->n = (size_t)p->M * p->Nt;
+  auto bail = [&](aao_status st) {
+    g_create_error = p->err;
+    aao_plan_destroy(p);
+    return st;
+  };
+#define TRYP(x)                          \
+  do {                                   \
+    aao_status s_ = (x);                 \
+    if (s_ != AAO_OK) return bail(s_);   \
+  } while (0)
+  const aao::HostTables& t = p->ht;
+  TRYP(upload(p, &p->Ehalf, t.Ehat_half));
+  TRYP(upload_c(p, &p->twL64, t.tw_L));
+  TRYP(upload_c(p, &p->twL32, t.tw_L));
+  TRYP(upload_c(p, &p->twNt64, t.tw_Nt));
+  TRYP(upload_c(p, &p->twNt32, t.tw_Nt));
+  TRYP(upload(p, &p->Ebr64, t.Ehat_br));
+  TRYP(upload(p, &p->Ebr32, t.Ehat_br));
+  TRYP(upload_c(p, &p->lambda, t.lambda));
+  TRYP(upload(p, &p->sfwd64, t.scale_fwd));
+  TRYP(upload(p, &p->sinv64, t.scale_inv));
+  TRYP(upload(p, &p->sfwd32, t.scale_fwd));
+  TRYP(upload(p, &p->sinv32, t.scale_inv));
+  TRYP(upload_c(p, &p->chirp64, t.chirp));
+  TRYP(upload_c(p, &p->chirp32, t.chirp));
+  TRYP(upload_c(p, &p->chat64, t.chirp_hat_br));
+  TRYP(upload_c(p, &p->chat32, t.chirp_hat_br));
+  TRYP(upload(p, &p->seig64, t.strang_eig));
+  TRYP(upload(p, &p->seig32, t.strang_eig));
+  if (t.tau_ok) {
+    TRYP(upload(p, &p->tau64, t.tau_eig_br));
+    TRYP(upload(p, &p->tau32, t.tau_eig_br));
+  }
+  const size_t n = p->n;
+  const size_t csz = p->mixed ? sizeof(float2) : sizeof(double2);
+  TRYP(dalloc(p, &p->V, (size_t)(p->m + 1) * n));
+  {
+    void* z = nullptr;
+    TRYP(dalloc(p, reinterpret_cast<unsigned char**>(&z), (size_t)p->m * n * (p->mixed ? 4 : 8)));
+    p->Z = z;
+  }
+  {
+    unsigned char* q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->M * csz));
+    p->spec = q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->M * csz));
+    p->rws = q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->M * csz));
+    p->pws = q;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  p->cocg_grid = std::min(p->nsys, std::max(1, sms));
+  if (!p->mixed) {
+    const size_t ge = aao::cocg_gbuf_elems_f64(p->logL, p->cocg_grid);
+    if (ge) TRYP(dalloc(p, &p->gbuf, ge));
+  } else {
+    p->cocg_grid = p->nsys;  // shared-memory transforms: one CTA per system
+  }
+  if (!p->mixed) p->cocg_grid = p->gbuf ? p->cocg_grid : p->nsys;
+  TRYP(dalloc(p, &p->iters, (size_t)p->nsys));
+  TRYP(dalloc(p, &p->flags, (size_t)p->nsys));
+  TRYP(dalloc(p, &p->stats, 4));
+  TRYP(dalloc(p, &p->partial, (size_t)std::max(aao::blas_partial_blocks() * 65, p->Nt)));
+  TRYP(dalloc(p, &p->hdev, 4 * 65));
+  TRYP(dalloc(p, &p->sq, (size_t)p->Nt));
+  if (cudaMallocHost(&p->pinned, 4 * 65 * sizeof(double)) != cudaSuccess) {
+    p->pinned = nullptr;
+    p->err = "cudaMallocHost failed";
+    return bail(AAO_ENOMEM);
+  }
+#undef TRYP
+  *out = p;
+  return AAO_OK;
+}
+
+aao_status aao_plan_set_profiling(aao_plan* p, int on) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  p->prof_on = on != 0;
+  return AAO_OK;
+}
+
+aao_status aao_plan_get_profile(aao_plan* p, double* ms, int64_t* launches, int reset) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  CK(cudaStreamSynchronize(p->stream));
+  for (auto& pr : p->ev_pending) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, pr.second.first, pr.second.second));
+    p->prof_ms[pr.first] += t;
+    p->ev_pool.push_back(pr.second.first);
+    p->ev_pool.push_back(pr.second.second);
+  }
+  p->ev_pending.clear();
+  for (int i = 0; i < AAO_NUM_STAGES; ++i) {
+    if (ms) ms[i] = p->prof_ms[i];
+    if (launches) launches[i] = p->prof_launches[i];
+    if (reset) { p->prof_ms[i] = 0; p->prof_launches[i] = 0; }
+  }
+  return AAO_OK;
+}
+
+aao_status aao_build_rhs(aao_plan* p, const double* u0, const double* f, double* F) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!u0 || !f || !F) return fail(p, AAO_EINVAL, "null pointer");
+  LAUNCH(ST_VEC, 1, aao::launch_build_rhs(u0, f, F, p->ht.tau, p->M, p->Nt, p->stream));
+  return AAO_OK;
+}
+
+aao_status aao_matvec(aao_plan* p, const double* v, double* w) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!v || !w || v == w) return fail(p, AAO_EINVAL, "null or aliased pointers");
+  return matvec_any(p, v, false, nullptr, w, nullptr);
+}
+
+aao_status aao_bc_precond_apply(aao_plan* p, const double* v, double* z) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!v || !z) return fail(p, AAO_EINVAL, "null pointer");
+  return precond_any(p, v, z, 1);
+}
+
+aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* info) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!F || !U) return fail(p, AAO_EINVAL, "null pointer");
+  const size_t n = p->n;
+  const int m = p->m;
+  const int nb = aao::blas_partial_blocks();
+  aao_info inf{};
+  double nF2 = 0;
+  LAUNCH(ST_VEC, 1, aao::launch_dots(F, F, 0, 1, n, p->partial, p->stream));
+  TRY(reduce_to_host(p, p->partial, nb, 1, &nF2));
+  const double nF = std::sqrt(nF2);
+  if (!std::isfinite(nF)) return fail(p, AAO_ENONFINITE, "non-finite right-hand side");
+  if (nF == 0.0) {
+    CK(cudaMemsetAsync(U, 0, n * sizeof(double), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (info) *info = inf;
+    return AAO_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  const double tol = p->opts.tol;
+  aao_status result = AAO_ENOCONV;
+  for (int cycle = 0; cycle <= p->opts.max_cycles; ++cycle) {
+    // r = F - calA U  (into V_0) with row partial sums of squares
+    TRY(matvec_any(p, U, false, F, p->V, p->sq));
+    inf.matvecs++;
+    double beta2 = 0;
+    TRY(reduce_to_host(p, p->sq, p->Nt, 1, &beta2));
+    const double beta = std::sqrt(beta2);
+    if (!std::isfinite(beta)) { result = AAO_ENONFINITE; p->err = "non-finite residual"; break; }
+    inf.true_rel_res = beta / nF;
+    inf.cycles = cycle;
+    if (inf.true_rel_res <= tol) { result = AAO_OK; break; }
+    if (cycle == p->opts.max_cycles) break;
+    LAUNCH(ST_VEC, 1, aao::launch_scale(p->V, p->V, 1.0 / beta, n, p->stream));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    bool stop = false;
+    for (int j = 0; j < m && !stop; ++j) {
+      double* vj = p->V + (size_t)j * n;
+      double* w = p->V + (size_t)(j + 1) * n;
+      void* zj = p->mixed ? (void*)((float*)p->Z + (size_t)j * n) : (void*)((double*)p->Z + (size_t)j * n);
+      TRY(precond_any(p, vj, zj, p->mixed ? 0 : 1));
+      LAUNCH(ST_VEC, 1, (iter_stats_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->stats),
+                         cudaGetLastError()));
+      TRY(matvec_any(p, zj, p->mixed, nullptr, w, nullptr));
+      inf.matvecs++;
+      // CGS2: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2; ||w||
+      const int nv = j + 1;
+      LAUNCH(ST_VEC, 1, aao::launch_dots(w, p->V, n, nv, n, p->partial, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_update_dots(w, p->V, n, nv, n, p->hdev, p->partial, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev + 65, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_update_norm(w, p->V, n, nv, n, p->hdev + 65, p->partial, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, 1, p->hdev + 130, p->stream));
+      CK(cudaMemcpyAsync(p->pinned, p->hdev, 131 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+      int st[3] = {0, 0, 0};
+      CK(cudaMemcpyAsync(p->pinned + 200, p->stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+      CK(cudaStreamSynchronize(p->stream));
+      std::memcpy(st, p->pinned + 200, 3 * sizeof(int));
+      inf.inner_iters_max = std::max(inf.inner_iters_max, st[0]);
+      inf.inner_iters_sum += st[2];
+      if (st[1] != 0 && inf.status_detail == 0)
+        inf.status_detail = st[1] == 1 ? AAO_ENOCONV : (st[1] == 2 ? AAO_EBREAKDOWN : AAO_ENONFINITE);
+      for (int i = 0; i <= j; ++i) Hij(i, j) = p->pinned[i] + p->pinned[65 + i];
+      const double hn = std::sqrt(p->pinned[130]);
+      Hij(j + 1, j) = hn;
+      if (!std::isfinite(hn)) { result = AAO_ENONFINITE; p->err = "non-finite Arnoldi vector"; stop = true; break; }
+      if (hn > 0) LAUNCH(ST_VEC, 1, aao::launch_scale(w, w, 1.0 / hn, n, p->stream));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double d = std::hypot(Hij(j, j), Hij(j + 1, j));
+      if (d == 0.0) { result = AAO_EBREAKDOWN; p->err = "GMRES breakdown"; stop = true; break; }
+      cs[j] = Hij(j, j) / d;
+      sn[j] = Hij(j + 1, j) / d;
+      Hij(j, j) = d;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      inf.outer_iters++;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= 0.5 * tol * nF || hn == 0.0) break;
+    }
+    if (result == AAO_ENONFINITE || result == AAO_EBREAKDOWN) break;
+    for (int i = jdone - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < jdone; ++k) s -= Hij(i, k) * y[k];
+      y[i] = s / Hij(i, i);
+    }
+    std::memcpy(p->pinned, y.data(), jdone * sizeof(double));
+    CK(cudaMemcpyAsync(p->hdev + 195, p->pinned, jdone * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    if (p->mixed)
+      LAUNCH(ST_VEC, 1, aao::launch_zy_update_f32(U, (const float*)p->Z, n, jdone, n, p->hdev + 195, p->stream));
+    else
+      LAUNCH(ST_VEC, 1, aao::launch_zy_update_f64(U, (const double*)p->Z, n, jdone, n, p->hdev + 195, p->stream));
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  if (info) *info = inf;
+  if (result == AAO_ENOCONV) p->err = "FGMRES did not reach the tolerance within max_cycles";
+  return result;
+}
+
+aao_status aao_gmres_solve_host(aao_plan* p, const double* F_host, double* U_host, aao_info* info) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!F_host || !U_host) return fail(p, AAO_EINVAL, "null pointer");
+  if (!p->Fh) {
+    TRY(dalloc(p, &p->Fh, p->n));
+    TRY(dalloc(p, &p->Uh, p->n));
+  }
+  CK(cudaMemcpyAsync(p->Fh, F_host, p->n * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemsetAsync(p->Uh, 0, p->n * sizeof(double), p->stream));
+  aao_status st = aao_gmres_solve(p, p->Fh, p->Uh, info);
+  if (st != AAO_OK && st != AAO_ENOCONV) return st;
+  CK(cudaMemcpyAsync(U_host, p->Uh, p->n * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return st;
+}
+
+}  // extern "C"

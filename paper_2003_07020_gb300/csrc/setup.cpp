@@ -1,0 +1,175 @@
+// Host FP64 setup of a plan (see setup.h).
+//
+// Paper references: the weights g_k (Eq. 2.4), the Toeplitz Jacobian
+// (Sec. 2.1), the eigenvalues lambda_n of the eps-circulant C_eps (Eq. 1.6a),
+// the scaling Lambda_eps of Eq. 1.6a used by Steps (a) and (c) (Sec. 3.1),
+// and the tau-matrix of Sec. 3.2 (here in its natural T - H(T) form).
+#include "setup.h"
+
+#include <cmath>
+
+namespace aao {
+
+static const double kPi = 3.14159265358979323846;
+
+void fcd_weights_recurrence(double alpha, int64_t n, double* g) {
+  if (n <= 0) return;
+  const double a2 = 0.5 * alpha;
+  const double gh = std::tgamma(1.0 + a2);
+  g[0] = std::tgamma(1.0 + alpha) / (gh * gh);
+  for (int64_t k = 0; k + 1 < n; ++k) g[k + 1] = g[k] * ((double)k - a2) / (a2 + (double)k + 1.0);
+}
+
+int ilog2_exact(int64_t n) {
+  if (n <= 0 || (n & (n - 1))) return -1;
+  int l = 0;
+  while ((int64_t(1) << l) < n) ++l;
+  return l;
+}
+
+cd unit_root(int64_t m, int64_t n, int sign) {
+  int64_t r = m % n;
+  if (r < 0) r += n;
+  if (2 * r > n) r -= n;  // angle in (-pi, pi]
+  const double ang = 2.0 * kPi * (double)r / (double)n;
+  return cd(std::cos(ang), sign * std::sin(ang));
+}
+
+void host_fft(std::vector<cd>& a, int sign) {
+  const int64_t n = (int64_t)a.size();
+  const int logn = ilog2_exact(n);
+  for (int64_t i = 0, j = 0; i < n; ++i) {  // bit-reversal permutation
+    if (i < j) std::swap(a[i], a[j]);
+    int64_t bit = n >> 1;
+    while (bit && (j & bit)) { j ^= bit; bit >>= 1; }
+    j |= bit;
+  }
+  std::vector<cd> tw((size_t)(n / 2 > 0 ? n / 2 : 1));
+  for (int64_t m = 0; m < n / 2; ++m) tw[m] = unit_root(m, n, sign);
+  for (int s = 1; s <= logn; ++s) {
+    const int64_t len = int64_t(1) << s, half = len >> 1, step = n / len;
+    for (int64_t st = 0; st < n; st += len)
+      for (int64_t j = 0; j < half; ++j) {
+        const cd u = a[st + j], v = a[st + j + half] * tw[j * step];
+        a[st + j] = u + v;
+        a[st + j + half] = u - v;
+      }
+  }
+}
+
+static int64_t bitrev64(int64_t k, int logn) {
+  int64_t r = 0;
+  for (int b = 0; b < logn; ++b) r |= ((k >> b) & 1) << (logn - 1 - b);
+  return r;
+}
+
+bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, double eps,
+                  HostTables& t, const char** err) {
+  if (M < 1) { *err = "M must be >= 1"; return false; }
+  if (ilog2_exact(Nt) < 2) { *err = "Nt must be a power of two >= 4"; return false; }
+  if (!(T > 0.0)) { *err = "T must be > 0"; return false; }
+  if (!(alpha > 0.0 && alpha <= 2.0)) { *err = "alpha must be in (0, 2]"; return false; }
+  if (!(kappa > 0.0)) { *err = "kappa must be > 0"; return false; }
+  t.M = M;
+  t.Nt = Nt;
+  t.logNt = ilog2_exact(Nt);
+  int64_t L = 4;
+  while (L < 2 * M) L <<= 1;  // L >= 2M - 1, a power of two, at least 4
+  t.L = L;
+  t.logL = ilog2_exact(L);
+  if (t.logL > 14) { *err = "M too large: the circulant embedding is limited to 16384 points"; return false; }
+  t.tau = T / (double)Nt;
+  t.h = 1.0 / (double)(M + 1);
+  t.c = t.tau * kappa / std::pow(t.h, alpha);
+  t.eps = eps > 0.0 ? eps : std::min(0.5, 0.5 * t.tau);
+  if (!(t.eps > 0.0 && t.eps <= 1.0)) { *err = "eps must be in (0, 1]"; return false; }
+  const double c = t.c;
+
+  t.g.resize((size_t)M + 2);
+  fcd_weights_recurrence(alpha, M + 2, t.g.data());
+
+  // circulant embedding of T: e_j = g_min(j, L-j) when that index is < M, else 0
+  std::vector<cd> e((size_t)L, cd(0, 0));
+  for (int64_t j = 0; j < L; ++j) {
+    const int64_t d = std::min(j, L - j);
+    if (d < M) e[j] = t.g[d];
+  }
+  host_fft(e, -1);
+  t.Ehat_half.resize((size_t)L / 2 + 1);
+  for (int64_t m = 0; m <= L / 2; ++m) t.Ehat_half[m] = c * e[m].real() / (double)(L / 2);
+  t.Ehat_br.resize((size_t)L);
+  for (int64_t p = 0; p < L; ++p) t.Ehat_br[p] = c * e[bitrev64(p, t.logL)].real() / (double)L;
+
+  t.tw_L.resize((size_t)L / 2);
+  for (int64_t m = 0; m < L / 2; ++m) t.tw_L[m] = unit_root(m, L, -1);
+  t.tw_Nt.resize((size_t)Nt / 2);
+  for (int64_t m = 0; m < Nt / 2; ++m) t.tw_Nt[m] = unit_root(m, Nt, -1);
+
+  // eigenvalues of C_eps, Eq. 1.6a: lambda_n = 3/2 - 2 eps^{1/Nt} theta^n + 1/2 eps^{2/Nt} theta^{2n}
+  t.lambda.resize((size_t)Nt / 2 + 1);
+  const double e1 = std::pow(t.eps, 1.0 / (double)Nt), e2 = std::pow(t.eps, 2.0 / (double)Nt);
+  for (int64_t n = 0; n <= Nt / 2; ++n)
+    t.lambda[n] = 1.5 - 2.0 * e1 * unit_root(n, Nt, +1) + 0.5 * e2 * unit_root(2 * n, Nt, +1);
+  t.scale_fwd.resize((size_t)Nt);
+  t.scale_inv.resize((size_t)Nt);
+  const double le = std::log(t.eps);
+  for (int64_t k = 0; k < Nt; ++k) {
+    t.scale_fwd[k] = std::exp(le * (double)k / (double)Nt);
+    t.scale_inv[k] = std::exp(-le * (double)k / (double)Nt) / (double)Nt;
+  }
+
+  // Strang circulant s of T: s_k = g_k (k <= M/2), g_{M-k} otherwise; its
+  // eigenvalues DFT_M(s) by Bluestein's chirp-z identity with FFTs of length L.
+  t.chirp.resize((size_t)M);
+  for (int64_t j = 0; j < M; ++j) t.chirp[j] = unit_root((j * j) % (2 * M), 2 * M, -1);
+  std::vector<cd> b((size_t)L, cd(0, 0));
+  for (int64_t d = 0; d < M; ++d) {
+    b[d] = std::conj(t.chirp[d]);
+    if (d > 0) b[L - d] = std::conj(t.chirp[d]);
+  }
+  host_fft(b, -1);  // DFT_L of the chirp filter
+  t.chirp_hat_br.resize((size_t)L);
+  for (int64_t p = 0; p < L; ++p) t.chirp_hat_br[p] = b[bitrev64(p, t.logL)] / (double)L;
+  std::vector<cd> a((size_t)L, cd(0, 0));
+  for (int64_t k = 0; k < M; ++k) {
+    const double s = (k <= M / 2) ? t.g[k] : t.g[M - k];
+    a[k] = s * t.chirp[k];
+  }
+  host_fft(a, -1);
+  for (int64_t m = 0; m < L; ++m) a[m] *= b[m];
+  host_fft(a, +1);
+  t.strang_eig.resize((size_t)M);
+  for (int64_t k = 0; k < M; ++k) t.strang_eig[k] = c * (t.chirp[k] * a[k] / (double)L).real();
+
+  // natural tau matrix tau(T) = T - H(T): first column q_i = g_i - g_{i+2}
+  // (i <= M-3), q_{M-2} = g_{M-2}, q_{M-1} = g_{M-1}; eigenvalues
+  // sigma_j = (S q)_j / sin(pi j/(M+1)), S_{jl} = sin(pi j l/(M+1)).
+  t.tau_ok = (L == 2 * (M + 1));
+  if (t.tau_ok) {
+    std::vector<cd> y((size_t)L, cd(0, 0));
+    for (int64_t l = 1; l <= M; ++l) {
+      const int64_t i = l - 1;
+      const double q = (i + 2 <= M - 1) ? t.g[i] - t.g[i + 2] : t.g[i];
+      y[l] = q;
+      y[L - l] = -q;
+    }
+    host_fft(y, -1);  // = -2i (S q)_j
+    std::vector<double> sig((size_t)L, 0.0);
+    for (int64_t j = 1; j <= M; ++j) {
+      const double sq = -0.5 * y[j].imag();
+      sig[j] = sq / unit_root(j, L, +1).imag();  // sin(pi j/(M+1)) = sin(2 pi j / L)
+      sig[L - j] = sig[j];
+    }
+    t.tau_eig_br.resize((size_t)L);
+    for (int64_t p = 0; p < L; ++p) t.tau_eig_br[p] = c * sig[bitrev64(p, t.logL)];
+  }
+  return true;
+}
+
+}  // namespace aao
+
+extern "C" int aao_setup_coeffs_impl(double alpha, int64_t n, double* g) {
+  if (n < 1 || g == nullptr || !(alpha > 0.0 && alpha <= 2.0)) return 1;
+  aao::fcd_weights_recurrence(alpha, n, g);
+  return 0;
+}

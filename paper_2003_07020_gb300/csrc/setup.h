@@ -1,0 +1,50 @@
+// Host-side FP64 setup for a plan: FCD weights, spectra, eigenvalues and
+// FFT tables.  Everything here runs once per plan on the CPU in double
+// precision; the device kernels only read the tables it produces.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+namespace aao {
+
+using cd = std::complex<double>;
+
+// g_0 .. g_{n-1} of Eq. 2.4 by the Gamma-ratio recurrence.
+void fcd_weights_recurrence(double alpha, int64_t n, double* g);
+
+// In-place radix-2 complex FFT of length n (a power of two), natural order
+// in and out.  sign = -1: sum x_j exp(-2 pi i jk/n); sign = +1: exp(+...).
+void host_fft(std::vector<cd>& a, int sign);
+
+// exp(sign * 2 pi i * m / n), with the angle reduced exactly in integers.
+cd unit_root(int64_t m, int64_t n, int sign);
+
+int ilog2_exact(int64_t n);  // -1 if n is not a power of two
+
+struct HostTables {
+  int64_t M = 0, Nt = 0, L = 0;
+  int logL = 0, logNt = 0;
+  double tau = 0, h = 0, c = 0, eps = 0;
+  std::vector<double> g;            // g_0 .. g_{M+1}
+  std::vector<double> Ehat_half;    // c * DFT_L(e)_m / (L/2), m = 0 .. L/2 (matvec, FP64 R2C form)
+  std::vector<double> Ehat_br;      // c * DFT_L(e)_m / L in bit-reversed order (complex-vector form)
+  std::vector<cd> tw_L;             // exp(-2 pi i m / L), m < L/2
+  std::vector<cd> tw_Nt;            // exp(-2 pi i m / Nt), m < Nt/2
+  std::vector<cd> lambda;           // lambda_n of C_eps, n = 0 .. Nt/2
+  std::vector<double> scale_fwd;    // eps^{k/Nt}
+  std::vector<double> scale_inv;    // eps^{-k/Nt} / Nt
+  // Strang circulant (Bluestein form)
+  std::vector<double> strang_eig;   // c * DFT_M(s)_k, k < M
+  std::vector<cd> chirp;            // exp(-pi i j^2 / M), j < M
+  std::vector<cd> chirp_hat_br;     // DFT_L(b)_m / L, bit-reversed, b_d = conj(chirp_|d|)
+  // natural tau matrix (DST form), valid when L == 2(M+1)
+  std::vector<double> tau_eig_br;   // c * sigma_j for frequency j = bitrev(position); 0 at j = 0, M+1
+  bool tau_ok = false;
+};
+
+// Fills every table for the 1D problem.  Returns false with a message on bad input.
+bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, double eps,
+                  HostTables& out, const char** err);
+
+}  // namespace aao

@@ -1,0 +1,140 @@
+// Time-direction DFTs of the block-circulant preconditioner, Sec. 3.1:
+//   Step (a): zhat_n = sum_k eps^{k/Nt} theta^{nk} v_k,        n = 0 .. Nt/2
+//   Step (c): z_k    = eps^{-k/Nt} (1/Nt) sum_n x_n theta^{-nk}, x_{Nt-n} = conj(x_n)
+// with theta = exp(2 pi i / Nt).  Only the half spectrum is kept because v
+// is real (Sec. 3.2: the systems come in conjugate pairs).
+//
+// Each CTA owns a tile of TW spatial columns over all Nt time rows; the rows
+// are read as contiguous TW-column segments (coalesced) and the column pairs
+// (q, q + TW/2) are packed as one complex transform.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace aao {
+
+constexpr int TW = 16;   // columns per CTA
+constexpr int TWH = TW / 2;
+
+template <typename R> __device__ __forceinline__ R ldv(const double* p) { return (R)__ldg(p); }
+
+// ---- Step (a) ----
+template <typename R>
+__global__ void __launch_bounds__(256) tdft_fwd_kernel(const double* __restrict__ v,
+                                                       typename cplx_t<R>::type* __restrict__ out, int M,
+                                                       int logNt, const R* __restrict__ scale,
+                                                       const typename cplx_t<R>::type* __restrict__ tw) {
+  using C = typename cplx_t<R>::type;
+  extern __shared__ unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  R* smr = reinterpret_cast<R*>(smraw);
+  const int Nt = 1 << logNt;
+  const int bstride = padded_size(Nt);
+  const int c0 = blockIdx.x * TW;
+  // load y_k = scale_k v_k (real) into position bitrev(k); column cc -> transform cc % TWH, part cc / TWH
+  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
+    const int k = idx / TW, cc = idx - k * TW;
+    const int col = c0 + cc;
+    const R val = (col < M) ? ldv<R>(v + (size_t)k * M + col) * __ldg(&scale[k]) : (R)0;
+    const int q = cc & (TWH - 1), part = cc / TWH;
+    smr[2 * (q * bstride + pad16(bitrev(k, logNt))) + part] = val;
+  }
+  __syncthreads();
+  fft_backward(sm, logNt, TWH, bstride, tw, 0);  // sum_k y_k exp(+2 pi i nk/Nt), natural order
+  const int half = Nt / 2;
+  for (int idx = threadIdx.x; idx < (half + 1) * TW; idx += blockDim.x) {
+    const int n = idx / TW, cc = idx - n * TW;
+    const int col = c0 + cc;
+    if (col >= M) continue;
+    const int q = cc & (TWH - 1), part = cc / TWH;
+    const C Zn = sm[q * bstride + pad16(n)];
+    const C Zm = sm[q * bstride + pad16((Nt - n) & (Nt - 1))];
+    C X;
+    if (part == 0) X = C{(R)0.5 * (Zn.x + Zm.x), (R)0.5 * (Zn.y - Zm.y)};   // (Z_n + conj Z_{-n})/2
+    else X = C{(R)0.5 * (Zn.y + Zm.y), (R)-0.5 * (Zn.x - Zm.x)};          // (Z_n - conj Z_{-n})/(2i)
+    out[(size_t)n * M + col] = X;
+  }
+}
+
+// ---- Step (c) ----
+template <typename R, typename TOut>
+__global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>::type* __restrict__ in,
+                                                       TOut* __restrict__ z, int M, int logNt,
+                                                       const R* __restrict__ scale_inv,
+                                                       const typename cplx_t<R>::type* __restrict__ tw) {
+  using C = typename cplx_t<R>::type;
+  extern __shared__ unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int Nt = 1 << logNt;
+  const int bstride = padded_size(Nt);
+  const int c0 = blockIdx.x * TW;
+  const int half = Nt / 2;
+  for (int idx = threadIdx.x; idx < (half + 1) * TWH; idx += blockDim.x) {
+    const int n = idx / TWH, q = idx - n * TWH;
+    const int ca = c0 + q, cb = c0 + q + TWH;
+    C Xa = (ca < M) ? in[(size_t)n * M + ca] : C{0, 0};
+    C Xb = (cb < M) ? in[(size_t)n * M + cb] : C{0, 0};
+    if (n == 0 || n == half) { Xa.y = 0; Xb.y = 0; }
+    sm[q * bstride + pad16(n)] = C{Xa.x - Xb.y, Xa.y + Xb.x};                  // Xa + i Xb
+    if (n != 0 && n != half) sm[q * bstride + pad16(Nt - n)] = C{Xa.x + Xb.y, Xb.x - Xa.y};  // conj Xa + i conj Xb
+  }
+  __syncthreads();
+  fft_forward(sm, logNt, TWH, bstride, tw, 0);  // sum_n Z_n exp(-2 pi i nk/Nt), bit-reversed
+  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
+    const int k = idx / TW, cc = idx - k * TW;
+    const int col = c0 + cc;
+    if (col >= M) continue;
+    const int q = cc & (TWH - 1), part = cc / TWH;
+    const C Zk = sm[q * bstride + pad16(bitrev(k, logNt))];
+    const R val = (part == 0 ? Zk.x : Zk.y) * __ldg(&scale_inv[k]);
+    z[(size_t)k * M + col] = (TOut)val;
+  }
+}
+
+template <typename R>
+static size_t tdft_smem(int Nt) { return (size_t)TWH * padded_size(Nt) * sizeof(typename cplx_t<R>::type); }
+
+static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+template <typename R>
+static cudaError_t fwd(const double* v, typename cplx_t<R>::type* out, int M, int Nt, const R* scale,
+                       const typename cplx_t<R>::type* tw, cudaStream_t s) {
+  const size_t smem = tdft_smem<R>(Nt);
+  cudaError_t e = cudaFuncSetAttribute(tdft_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tdft_fwd_kernel<R><<<(M + TW - 1) / TW, 256, smem, s>>>(v, out, M, ilog2i(Nt), scale, tw);
+  return cudaGetLastError();
+}
+
+template <typename R, typename TOut>
+static cudaError_t inv(const typename cplx_t<R>::type* in, TOut* z, int M, int Nt, const R* scale_inv,
+                       const typename cplx_t<R>::type* tw, cudaStream_t s) {
+  const size_t smem = tdft_smem<R>(Nt);
+  cudaError_t e = cudaFuncSetAttribute(tdft_inv_kernel<R, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  tdft_inv_kernel<R, TOut><<<(M + TW - 1) / TW, 256, smem, s>>>(in, z, M, ilog2i(Nt), scale_inv, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tdft_fwd_f32(const double* v, float2* out, int M, int Nt, const float* scale,
+                                const float2* twNt, cudaStream_t s) {
+  return fwd<float>(v, out, M, Nt, scale, twNt, s);
+}
+cudaError_t launch_tdft_fwd_f64(const double* v, double2* out, int M, int Nt, const double* scale,
+                                const double2* twNt, cudaStream_t s) {
+  return fwd<double>(v, out, M, Nt, scale, twNt, s);
+}
+cudaError_t launch_tdft_inv_f32(const float2* in, float* z, int M, int Nt, const float* scale_inv,
+                                const float2* twNt, cudaStream_t s) {
+  return inv<float, float>(in, z, M, Nt, scale_inv, twNt, s);
+}
+cudaError_t launch_tdft_inv_f32_to_f64(const float2* in, double* z, int M, int Nt, const float* scale_inv,
+                                       const float2* twNt, cudaStream_t s) {
+  return inv<float, double>(in, z, M, Nt, scale_inv, twNt, s);
+}
+cudaError_t launch_tdft_inv_f64(const double2* in, double* z, int M, int Nt, const double* scale_inv,
+                                const double2* twNt, cudaStream_t s) {
+  return inv<double, double>(in, z, M, Nt, scale_inv, twNt, s);
+}
+
+}  // namespace aao

@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.
+
+Tolerances (stated per check below):
+  * matvec (FP64 FFT, Sec. 3.2): relative 1e-13 in 2-norm at small sizes and
+    1e-12 of the row scale at sampled full-size outputs (FFT rounding is
+    about eps * log2(L) relative to c ||T|| ||v||);
+  * preconditioner (Sec. 3.1): FP64 path with inner tol 1e-12 -> residual
+    ||P z - v|| / ||v|| <= 1e-10 and z within 1e-9; mixed path with inner tol
+    t = 1e-6 in FP32 -> ||z - z_exact|| / ||z_exact|| <= 4 (t + 64 u32) / eps:
+    Step (c) multiplies time row k by eps^{-k/Nt}, so any relative error of
+    the FP32 spectrum (inner tolerance plus FP32 rounding, u32 = 2^-24) is
+    amplified up to cond(V_eps) = 1/eps (the conditioning of V_eps noted
+    after Eq. 1.6b);
+  * solve: true relative residual <= 1e-10 (computed by the oracle) and
+    ||U - U_seq|| / ||U_seq|| <= 1e-10 (FP64 path) or 1e-9 (mixed path).
+"""
+import numpy as np
+import pytest
+
+from paper_2003_07020_gb300 import aao, workloads
+from oracle import aao as oaao, fcd, precond as oprec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def jac(M, alpha, kappa=1.0):
+    return fcd.jacobian_1d(alpha, kappa, M, 1.0 / (M + 1))
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+# ---------------------------------------------------------------- matvec
+@pytest.mark.parametrize("M,Nt,alpha", [(63, 64, 1.5), (100, 16, 1.2), (1, 4, 1.5), (2, 8, 1.9),
+                                        (1023, 32, 1.8), (4095, 8, 1.3)])
+def test_matvec_matches_dense_oracle(M, Nt, alpha):
+    v = workloads.random_vector(Nt, M, seed=M + Nt)
+    with aao.Plan(M, Nt, alpha) as plan:
+        w = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.matvec(cu(v), w)
+        torch.cuda.synchronize()
+    ref = oaao.matvec(jac(M, alpha), 1.0 / Nt, v)
+    assert rel(host(w), ref) <= 1e-13
+
+
+def test_matvec_full_size_sampled():
+    M, Nt, alpha = 8191, 1024, 1.8
+    v = workloads.random_vector(Nt, M, seed=7)
+    with aao.Plan(M, Nt, alpha) as plan:
+        w = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.matvec(cu(v), w)
+        torch.cuda.synchronize()
+    W = host(w)
+    c = (1.0 / Nt) / (1.0 / (M + 1)) ** alpha
+    gs = c * fcd.fcd_weights(alpha, M)
+    rng = np.random.default_rng(0)
+    rows = np.r_[[0, 0, 1, 1, 2, Nt - 1, Nt - 1], rng.integers(0, Nt, 57)]
+    cols = np.r_[[0, M - 1, 0, 4096, M - 1, 0, M - 1], rng.integers(0, M, 57)]
+    ref = oaao.matvec_rows(gs, v, rows, cols)
+    scale = np.abs(ref).max()
+    assert np.abs(W[rows, cols] - ref).max() <= 1e-12 * scale
+
+
+# ---------------------------------------------------------------- preconditioner
+PREC_CASES = [(63, 64, 1.5), (100, 16, 1.2), (255, 32, 1.8), (1023, 16, 1.3), (3, 4, 1.5)]
+
+
+@pytest.mark.parametrize("M,Nt,alpha", PREC_CASES)
+@pytest.mark.parametrize("inner", [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU])
+def test_precond_fp64_matches_three_step_oracle(M, Nt, alpha, inner):
+    if inner == aao.AAO_INNER_TAU and (M + 1) & M:
+        pytest.skip("tau preconditioner needs M+1 a power of two")
+    v = workloads.random_vector(Nt, M, seed=3)
+    tau = 1.0 / Nt
+    eps = oprec.default_eps(tau)
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_FP64, inner=inner) as plan:
+        z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z)
+        torch.cuda.synchronize()
+    K = jac(M, alpha)
+    zr, _, _ = oprec.precond_apply(K, tau, eps, v)
+    Z = host(z)
+    assert rel(oprec.P_eps_matvec(K, tau, eps, Z), v) <= 1e-10
+    assert rel(Z, zr) <= 1e-9
+
+
+@pytest.mark.parametrize("M,Nt,alpha", PREC_CASES)
+@pytest.mark.parametrize("inner", [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU])
+def test_precond_mixed_residual(M, Nt, alpha, inner):
+    if inner == aao.AAO_INNER_TAU and (M + 1) & M:
+        pytest.skip("tau preconditioner needs M+1 a power of two")
+    v = workloads.random_vector(Nt, M, seed=4)
+    tau = 1.0 / Nt
+    eps = oprec.default_eps(tau)
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED, inner=inner) as plan:
+        z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z)
+        torch.cuda.synchronize()
+    K = jac(M, alpha)
+    zr, _, _ = oprec.precond_apply(K, tau, eps, v)
+    err = rel(host(z), zr)
+    bound = 4 * (1e-6 + 64 * 2.0 ** -24) / eps
+    assert err <= bound, (err, bound, rel(oprec.P_eps_matvec(K, tau, eps, host(z)), v))
+
+
+def test_precond_aliasing_allowed():
+    M, Nt = 63, 16
+    v = workloads.random_vector(Nt, M, seed=5)
+    with aao.Plan(M, Nt, 1.5, prec=aao.AAO_PREC_FP64) as plan:
+        a = cu(v)
+        b = torch.empty_like(a)
+        plan.bc_precond_apply(a, b)
+        plan.bc_precond_apply(a, a)
+        torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_precond_full_size_mixed_residual():
+    M, Nt, alpha = 8191, 1024, 1.8
+    v = workloads.random_vector(Nt, M, seed=9)
+    tau = 1.0 / Nt
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED) as plan:
+        z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z)
+        torch.cuda.synchronize()
+    K = jac(M, alpha)
+    # residual of the eps-circulant equation; the bound follows the z-error bound above
+    # times ||P_eps|| ||z|| / ||v||, evaluated with ||P_eps|| <= 4 + c 2^alpha
+    eps = oprec.default_eps(tau)
+    Z = host(z)
+    res = rel(oprec.P_eps_matvec(K, tau, eps, Z), v)
+    c = tau / (1.0 / (M + 1)) ** alpha
+    bound = 4 * (1e-6 + 64 * 2.0 ** -24) / eps * (4 + c * 2 ** alpha) * np.linalg.norm(Z) / np.linalg.norm(v)
+    assert res <= bound, (res, bound)
+
+
+# ---------------------------------------------------------------- right-hand side
+def test_build_rhs():
+    M, Nt = 37, 8
+    u0, f = workloads.make_inputs(M, Nt, seed=1)
+    with aao.Plan(M, Nt, 1.5) as plan:
+        F = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.build_rhs(cu(u0), cu(f), F)
+        torch.cuda.synchronize()
+    np.testing.assert_allclose(host(F), oaao.build_rhs(u0, f, 1.0 / Nt), rtol=1e-15, atol=1e-15)
+
+
+# ---------------------------------------------------------------- solve
+def solve_case(M, Nt, alpha, prec, inner, recipe="sine8_normal", seed=0):
+    u0, f = workloads.make_inputs(M, Nt, seed=seed, recipe=recipe)
+    with aao.Plan(M, Nt, alpha, prec=prec, inner=inner) as plan:
+        F = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        U = torch.zeros_like(F)
+        plan.build_rhs(cu(u0), cu(f), F)
+        info = plan.gmres_solve(F, U)
+    return u0, f, host(U), info
+
+
+@pytest.mark.parametrize("prec,bound", [(aao.AAO_PREC_FP64, 1e-10), (aao.AAO_PREC_MIXED, 1e-9)])
+@pytest.mark.parametrize("inner", [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU])
+@pytest.mark.parametrize("M,Nt,alpha,recipe", [(63, 64, 1.5, "sine1_uniform"), (255, 128, 1.8, "sine8_normal"),
+                                               (1023, 32, 1.2, "sine8_normal")])
+def test_gmres_solve_matches_time_stepping(M, Nt, alpha, recipe, prec, bound, inner):
+    u0, f, U, info = solve_case(M, Nt, alpha, prec, inner, recipe)
+    K = jac(M, alpha)
+    tau = 1.0 / Nt
+    Useq = oaao.sequential_bdf2(K, tau, u0, f)
+    trr = oaao.true_relative_residual(K, tau, oaao.build_rhs(u0, f, tau), U)
+    assert info["true_rel_res"] <= 1e-10 and trr <= 1e-10, (info, trr)
+    assert rel(U, Useq) <= bound, (rel(U, Useq), info)
+
+
+def test_gmres_full_size_config():
+    M, Nt, alpha = 8191, 1024, 1.8
+    u0, f, U, info = solve_case(M, Nt, alpha, aao.AAO_PREC_MIXED, aao.AAO_INNER_STRANG)
+    K = jac(M, alpha)
+    tau = 1.0 / Nt
+    F = oaao.build_rhs(u0, f, tau)
+    trr = oaao.true_relative_residual(K, tau, F, U)
+    assert info["true_rel_res"] <= 1e-10 and trr <= 1e-10, (info, trr)
+    Useq = oaao.sequential_bdf2(K, tau, u0, f)
+    assert rel(U, Useq) <= 1e-9, rel(U, Useq)
+
+
+def test_gmres_host_buffers_equal_device_path():
+    M, Nt, alpha = 255, 64, 1.5
+    u0, f = workloads.make_inputs(M, Nt, seed=2)
+    F = oaao.build_rhs(u0, f, 1.0 / Nt)
+    with aao.Plan(M, Nt, alpha) as plan:
+        Uh = np.zeros((Nt, M))
+        info_h = plan.gmres_solve_host(np.ascontiguousarray(F), Uh)
+        Ud = torch.zeros((Nt, M), dtype=torch.float64, device=DEV)
+        info_d = plan.gmres_solve(cu(F), Ud)
+    assert info_h["outer_iters"] == info_d["outer_iters"]
+    np.testing.assert_array_equal(Uh, host(Ud))
+
+
+def test_zero_rhs_and_nonfinite_rhs():
+    M, Nt = 31, 8
+    with aao.Plan(M, Nt, 1.5) as plan:
+        F = torch.zeros((Nt, M), dtype=torch.float64, device=DEV)
+        U = torch.ones_like(F)
+        info = plan.gmres_solve(F, U)
+        assert info["outer_iters"] == 0 and torch.count_nonzero(U) == 0
+        F[3, 4] = float("nan")
+        with pytest.raises(aao.AaoError) as e:
+            plan.gmres_solve(F, U)
+        assert e.value.status == aao.AAO_ENONFINITE
+
+
+def test_iteration_cap_reports_noconv():
+    M, Nt = 63, 64
+    u0, f = workloads.make_inputs(M, Nt, seed=0)
+    with aao.Plan(M, Nt, 1.5, restart=1, max_cycles=1) as plan:
+        F = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.build_rhs(cu(u0), cu(f), F)
+        U = torch.zeros_like(F)
+        with pytest.raises(aao.AaoError) as e:
+            plan.gmres_solve(F, U)
+        assert e.value.status == aao.AAO_ENOCONV
