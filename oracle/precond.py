@@ -216,3 +216,13 @@ def tau_inverse(g_scaled, M, lam):
     P = lam * np.eye(M) + tau_matrix(g_scaled, M)
     lu = sla.lu_factor(P)
     return lambda r: sla.lu_solve(lu, r)
+
+
+def P_eps_matvec(K, tau, eps, Z):
+    """P_eps z = vec(Z C_eps^T) - tau vec(K Z) in the row layout (dense C_eps and
+    K; library matmuls).  For checking a computed z ~= P_eps^{-1} v by its
+    residual at sizes where P_eps is too large to form."""
+    Z = np.asarray(Z, dtype=np.float64)
+    Nt = Z.shape[0]
+    Zf = Z.reshape(Nt, -1)
+    return (C_eps(Nt, eps) @ Zf - tau * (Zf @ K.T)).reshape(Z.shape)
