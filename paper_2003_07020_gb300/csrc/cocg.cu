@@ -30,22 +30,18 @@ template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
   return C{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
 
-// buf <- FFT-domain product: DIF, multiply by kernel, DIT.  The multiply is
-// given as a functor of (position p) -> complex factor.
+// buf <- FFT-domain product: forward FFT, multiply by kernel, backward FFT.
+// The multiply is a functor of the bit-reversed position p.
 template <typename C, typename F>
-__device__ __forceinline__ void convolve(C* buf, int logL, const C* __restrict__ tw, F factor) {
-  __syncthreads();
-  fft_forward(buf, logL, 1, 0, tw, 0);
-  const int L = 1 << logL;
-  for (int p = threadIdx.x; p < L; p += blockDim.x) buf[pad16(p)] = cmul(buf[pad16(p)], factor(p));
-  __syncthreads();
-  fft_backward(buf, logL, 1, 0, tw, 0);
+__device__ __forceinline__ void convolve(C* buf, int logL, const C* q, F factor) {
+  fft_convolve(buf, logL, q, logL, factor);
 }
 
 // z = P^{-1} r, written to buf[pad16(i)], i < M (natural order).
 template <typename R, int KIND>
 __device__ __forceinline__ void precond(typename cplx_t<R>::type* buf, const typename cplx_t<R>::type* r, int M,
-                                        int logL, typename cplx_t<R>::type lam, const typename Tabs<R>::type& tb) {
+                                        int logL, typename cplx_t<R>::type lam, const typename Tabs<R>::type& tb,
+                                        const typename cplx_t<R>::type* q) {
   using C = typename cplx_t<R>::type;
   const int L = 1 << logL;
   if (KIND == 0) {
@@ -53,7 +49,7 @@ __device__ __forceinline__ void precond(typename cplx_t<R>::type* buf, const typ
     // then a'_k = X_k conj(w_k) / (M (lambda + s_k)) = c_k / (M (lambda + s_k)); z_j = conj(w_j) (a' * chirp filter)_j
     for (int j = threadIdx.x; j < L; j += blockDim.x)
       buf[pad16(j)] = (j < M) ? cmul(r[j], __ldg(&tb.chirp[j])) : C{0, 0};
-    convolve(buf, logL, tb.twL, [&](int p) { return __ldg(&tb.chat_br[p]); });
+    convolve(buf, logL, q, [&](int p) { return __ldg(&tb.chat_br[p]); });
     const R invM = (R)1 / (R)M;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
       if (k < M) {
@@ -64,7 +60,7 @@ __device__ __forceinline__ void precond(typename cplx_t<R>::type* buf, const typ
         buf[pad16(k)] = C{0, 0};
       }
     }
-    convolve(buf, logL, tb.twL, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); });
+    convolve(buf, logL, q, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); });
     for (int j = threadIdx.x; j < M; j += blockDim.x) buf[pad16(j)] = cmulc(buf[pad16(j)], __ldg(&tb.chirp[j]));
     __syncthreads();
   } else {
@@ -77,13 +73,12 @@ __device__ __forceinline__ void precond(typename cplx_t<R>::type* buf, const typ
       buf[pad16(l)] = y;
     }
     const R invL = (R)1 / (R)L;
-    convolve(buf, logL, tb.twL, [&](int p) {
-      const int f = bitrev(p, logL);
-      if (f == 0 || f == Mp1) return C{0, 0};
+    convolve(buf, logL, q, [&](int p) {
       C d = lam;
       d.x += __ldg(&tb.taueig_br[p]);
       return cdiv(C{invL, 0}, d);
     });
+    (void)Mp1;
     // z_i = buf[pad16(i + 1)], see z_at
   }
 }
@@ -104,7 +99,9 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
   extern __shared__ unsigned char smraw[];
   __shared__ R red[4 * 32];
   C* buf = GBUF ? gbuf + (size_t)blockIdx.x * padded_size(1 << logL) : reinterpret_cast<C*>(smraw);
+  C* q = GBUF ? reinterpret_cast<C*>(smraw) : reinterpret_cast<C*>(smraw) + padded_size(1 << logL);
   const int L = 1 << logL;
+  load_quarter(q, tb.twL, L / 4);
   for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
     const double2 lamd = tb.lambda[n];
     const C lam = C{(R)lamd.x, (R)lamd.y};
@@ -124,7 +121,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
       continue;
     }
     const R thr = tol * tol * nb2[0];
-    precond<R, KIND>(buf, r, M, logL, lam, tb);
+    precond<R, KIND>(buf, r, M, logL, lam, tb, q);
     R rho2[2] = {0, 0};
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       const C z = z_at<R, KIND>(buf, i);
@@ -139,7 +136,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
     while (it < maxit) {
       // q = (lambda I + c T) p
       for (int j = threadIdx.x; j < L; j += blockDim.x) buf[pad16(j)] = (j < M) ? p[j] : C{0, 0};
-      convolve(buf, logL, tb.twL, [&](int q) { return C{__ldg(&tb.Ebr[q]), (R)0}; });
+      convolve(buf, logL, q, [&](int q) { return C{__ldg(&tb.Ebr[q]), (R)0}; });
       R pq2[2] = {0, 0};
       for (int i = threadIdx.x; i < M; i += blockDim.x) {
         const C pi = p[i];
@@ -168,7 +165,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
       ++it;
       if (!(rr[0] == rr[0]) || rr[0] > (R)1e30 * nb2[0]) { flag = 3; break; }
       if (rr[0] <= thr) { flag = 0; break; }
-      precond<R, KIND>(buf, r, M, logL, lam, tb);
+      precond<R, KIND>(buf, r, M, logL, lam, tb, q);
       R rn2[2] = {0, 0};
       for (int i = threadIdx.x; i < M; i += blockDim.x) {
         const C z = z_at<R, KIND>(buf, i);
@@ -190,8 +187,187 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
   (void)L;
 }
 
+// ---- FP32 path with register-resident vectors -------------------------------------------
+// 512 threads; thread t owns elements i = t + 512 j, j < 16 (M <= 8192), so r and p live in
+// registers for the whole solve and only x is updated in global memory.
+constexpr int kRegThreads = 512;
+constexpr int kRegElems = 16;
+
+template <int KIND>
+__device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegElems], int M, int logL, float2 lam,
+                                            const CocgTables32& tb, const float2* q, const float2* pt) {
+  const int L = 1 << logL;
+  const int t = threadIdx.x;
+  if (KIND == 0) {
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + kRegThreads * j;
+      if (i < L) buf[pad16(i)] = (i < M) ? cmul(r[j], __ldg(&tb.chirp[i])) : float2{0, 0};
+    }
+    for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+    fft_convolve(buf, logL, q, logL, [&](int p) { return __ldg(&tb.chat_br[p]); }, pt);
+    const float invM = 1.0f / (float)M;
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int k = t + kRegThreads * j;
+      if (k < M) {
+        float2 d = lam;
+        d.x += __ldg(&tb.seig[k]);
+        buf[pad16(k)] = cscale(cdiv(buf[pad16(k)], d), invM);
+      } else if (k < L) {
+        buf[pad16(k)] = float2{0, 0};
+      }
+    }
+    for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+    fft_convolve(buf, logL, q, logL, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); }, pt);
+  } else {
+    if (t == 0) {
+      buf[pad16(0)] = float2{0, 0};
+      buf[pad16(M + 1)] = float2{0, 0};
+    }
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + kRegThreads * j;
+      if (i < M) {
+        buf[pad16(i + 1)] = r[j];
+        buf[pad16(L - 1 - i)] = float2{-r[j].x, -r[j].y};
+      }
+    }
+    const int Mp1 = M + 1;
+    const float invL = 1.0f / (float)L;
+    fft_convolve(buf, logL, q, logL, [&](int p) {
+      float2 d = lam;
+      d.x += __ldg(&tb.taueig_br[p]);
+      return cdiv(float2{invL, 0}, d);
+    }, pt);
+    (void)Mp1;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kRegThreads, 1)
+    cocg_reg_kernel(float2* __restrict__ xb, int M, int logL, int nsys, CocgTables32 tb, float tol, int maxit,
+                    int* __restrict__ iters, int* __restrict__ flags) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ float red[4 * 32];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* q = buf + padded_size(1 << logL);
+  float2* pt = q + (1 << logL) / 4;  // per-pass twiddle tables
+  const int L = 1 << logL;
+  const int t = threadIdx.x;
+  load_quarter(q, tb.twL, L / 4);
+  __syncthreads();
+  build_pass_tables(pt, q, logL, logL);
+  for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
+    const double2 lamd = tb.lambda[n];
+    const float2 lam{(float)lamd.x, (float)lamd.y};
+    float2* x = xb + (size_t)n * M;
+    float2 r[kRegElems], p[kRegElems];
+    float nb2[1] = {0};
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + kRegThreads * j;
+      r[j] = (i < M) ? x[i] : float2{0, 0};
+      nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+    }
+    block_sum<float, 1>(nb2, red);
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + kRegThreads * j;
+      if (i < M) x[i] = float2{0, 0};
+    }
+    if (nb2[0] == 0.0f) {
+      if (t == 0) { iters[n] = 0; flags[n] = 0; }
+      continue;
+    }
+    const float thr = tol * tol * nb2[0];
+    // z = P^{-1} r, p = z, rho = r^T z
+    precond_reg<KIND>(buf, r, M, logL, lam, tb, q, pt);
+    float rho2[2] = {0, 0};
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + kRegThreads * j;
+      float2 z{0, 0};
+      if (i < M) z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
+      p[j] = z;
+      rho2[0] += r[j].x * z.x - r[j].y * z.y;
+      rho2[1] += r[j].x * z.y + r[j].y * z.x;
+    }
+    block_sum<float, 2>(rho2, red);
+    float2 rho{rho2[0], rho2[1]};
+    int it = 0, flag = 1;
+    while (it < maxit) {
+      // q = (lambda I + c T) p
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        if (i < L) buf[pad16(i)] = (i < M) ? p[j] : float2{0, 0};
+      }
+      for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+      fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
+      float pq2[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        if (i < M) {
+          const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
+          pq2[0] += p[j].x * qq.x - p[j].y * qq.y;
+          pq2[1] += p[j].x * qq.y + p[j].y * qq.x;
+        }
+      }
+      block_sum<float, 2>(pq2, red);
+      const float2 pq{pq2[0], pq2[1]};
+      if (!(pq.x * pq.x + pq.y * pq.y > 0.0f)) { flag = 2; break; }
+      const float2 a = cdiv(rho, pq);
+      float rr[1] = {0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        if (i < M) {
+          const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
+          x[i] = cadd(x[i], cmul(a, p[j]));
+          r[j] = csub(r[j], cmul(a, qq));
+          rr[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+        }
+      }
+      block_sum<float, 1>(rr, red);
+      ++it;
+      if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
+      if (rr[0] <= thr) { flag = 0; break; }
+      precond_reg<KIND>(buf, r, M, logL, lam, tb, q, pt);
+      float rn2[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        if (i < M) {
+          const float2 z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
+          rn2[0] += r[j].x * z.x - r[j].y * z.y;
+          rn2[1] += r[j].x * z.y + r[j].y * z.x;
+        }
+      }
+      block_sum<float, 2>(rn2, red);
+      const float2 rho_new{rn2[0], rn2[1]};
+      if (!(rho.x * rho.x + rho.y * rho.y > 0.0f)) { flag = 2; break; }
+      const float2 beta = cdiv(rho_new, rho);
+      rho = rho_new;
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        float2 z{0, 0};
+        if (i < M) z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
+        p[j] = cadd(z, cmul(beta, p[j]));
+      }
+      __syncthreads();
+    }
+    if (t == 0) { iters[n] = it; flags[n] = flag; }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 static size_t cocg_smem(int logL) { return (size_t)padded_size(1 << logL) * sizeof(typename cplx_t<R>::type); }
+template <typename R>
+static size_t cocg_table_bytes(int logL) { return (size_t)(1 << (logL - 2)) * sizeof(typename cplx_t<R>::type); }
 
 static const size_t kSmemLimit = 200 * 1024;
 
@@ -205,7 +381,7 @@ static cudaError_t launch_k(typename cplx_t<R>::type* xb, typename cplx_t<R>::ty
                             typename cplx_t<R>::type* pws, typename cplx_t<R>::type* gbuf, int M, int logL,
                             int nsys, const typename Tabs<R>::type& tb, R tol, int maxit, int* iters, int* flags,
                             int grid, cudaStream_t s) {
-  const size_t smem = GBUF ? 0 : cocg_smem<R>(logL);
+  const size_t smem = (GBUF ? 0 : cocg_smem<R>(logL)) + cocg_table_bytes<R>(logL);
   cudaError_t e = cudaFuncSetAttribute(cocg_kernel<R, KIND, GBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -217,6 +393,15 @@ static cudaError_t launch_k(typename cplx_t<R>::type* xb, typename cplx_t<R>::ty
 cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys, int inner,
                             const CocgTables32& tb, float tol, int maxit, int* iters, int* flags, int grid,
                             cudaStream_t s) {
+  if (M <= kRegThreads * kRegElems) {
+    const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
+                        (size_t)pass_table_size(logL) * sizeof(float2);
+    auto kern = inner == 0 ? cocg_reg_kernel<0> : cocg_reg_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kRegThreads, smem, s>>>(xb, M, logL, nsys, tb, tol, maxit, iters, flags);
+    return cudaGetLastError();
+  }
   if (inner == 0)
     return launch_k<float, 0, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
   return launch_k<float, 1, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);

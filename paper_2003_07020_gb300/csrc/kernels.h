@@ -34,12 +34,12 @@ cudaError_t launch_tdft_inv_f64(const double2* in, double* z, int M, int Nt, con
 // ---- shifted solves, Step (b), cocg.cu -----------------------------------------------
 struct CocgTables32 {
   const float2* twL;      // exp(-2 pi i m/L), m < L/2
-  const float* Ebr;       // c * DFT_L(e) / L, bit-reversed
+  const float* Ebr;       // c * DFT_L(e) / L, fused-pass order
   const double2* lambda;  // lambda_n, n < nsys
   const float2* chirp;    // Strang: exp(-pi i j^2/M)
-  const float2* chat_br;  // Strang: DFT_L(conj chirp filter)/L, bit-reversed
+  const float2* chat_br;  // Strang: DFT_L(conj chirp filter)/L, fused-pass order
   const float* seig;      // Strang: c * eigenvalues of S
-  const float* taueig_br; // tau: c * sigma_f, bit-reversed frequency order
+  const float* taueig_br; // tau: c * sigma_f, fused-pass order (1e30 where the DST multiplier vanishes)
 };
 struct CocgTables64 {
   const double2* twL;

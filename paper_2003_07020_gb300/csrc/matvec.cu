@@ -20,7 +20,7 @@ __device__ __forceinline__ double ld(const TIn* p) { return (double)__ldg(p); }
 // the packed signal: Z -> Z' such that backward(Z') packs c T x (see the
 // derivation in the file comment).  Ehalf[m] = c * Ehat_m / N, m = 0..N.
 __device__ __forceinline__ void r2c_mult_c2r(double2* sm, int logN, const double* __restrict__ Ehalf,
-                                             const double2* __restrict__ twL) {
+                                             const double2* q) {
   const int N = 1 << logN;
   for (int k = threadIdx.x; k <= N / 2; k += blockDim.x) {
     if (k == 0) {
@@ -39,7 +39,7 @@ __device__ __forceinline__ void r2c_mult_c2r(double2* sm, int logN, const double
     const double2 Ok = double2{0.5 * (Zk.y + Zkp.y), -0.5 * (Zk.x - Zkp.x)};
     const double ek = __ldg(&Ehalf[k]), ekp = __ldg(&Ehalf[kp]);
     {
-      const double2 W = __ldg(&twL[k]);
+      const double2 W = twiddle<-1>(q, k, logN + 1);
       const double2 WO = cmul(W, Ok);
       const double2 Y = cscale(cadd(Ek, WO), ek);    // Y_k
       const double2 YN = cscale(csub(Ek, WO), ekp);  // Y_{k+N}
@@ -49,7 +49,7 @@ __device__ __forceinline__ void r2c_mult_c2r(double2* sm, int logN, const double
     }
     if (kp != k) {
       const double2 Ekp = cconj(Ek), Okp = cconj(Ok);
-      const double2 W = __ldg(&twL[kp]);
+      const double2 W = twiddle<-1>(q, kp, logN + 1);
       const double2 WO = cmul(W, Okp);
       const double2 Y = cscale(cadd(Ekp, WO), ekp);
       const double2 YN = cscale(csub(Ekp, WO), ek);
@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(256) matvec_f64_kernel(const TIn* __restrict__
   __shared__ double red[32];
   const int N = 1 << logN;
   const int k = blockIdx.x;
+  double2* q = sm + padded_size(N);  // quarter twiddle table of the length-2N embedding
+  load_quarter(q, twL, N / 2);
   const TIn* vk = v + (size_t)k * M;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     const int i0 = 2 * j;
@@ -76,11 +78,9 @@ __global__ void __launch_bounds__(256) matvec_f64_kernel(const TIn* __restrict__
     const double x1 = (i0 + 1 < M) ? ld(vk + i0 + 1) : 0.0;
     sm[pad16(j)] = double2{x0, x1};
   }
-  __syncthreads();
-  fft_forward(sm, logN, 1, 0, twL, 1);
-  r2c_mult_c2r(sm, logN, Ehalf, twL);
-  __syncthreads();
-  fft_backward(sm, logN, 1, 0, twL, 1);
+  fft_forward(sm, logN, 1, 0, q, logN + 1);
+  r2c_mult_c2r(sm, logN, Ehalf, q);
+  fft_backward(sm, logN, 1, 0, q, logN + 1);
   const TIn* vk1 = vk - M;
   const TIn* vk2 = vk - 2 * M;
   double* wk = w + (size_t)k * M;
@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(256) matvec_f64_kernel(const TIn* __restrict__
   }
 }
 
-size_t matvec_smem_bytes(int logL) { return (size_t)padded_size(1 << (logL - 1)) * sizeof(double2); }
+size_t matvec_smem_bytes(int logL) {
+  return ((size_t)padded_size(1 << (logL - 1)) + (size_t)(1 << (logL - 2))) * sizeof(double2);
+}
 
 template <typename TIn>
 static cudaError_t launch_mv(const TIn* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,

@@ -335,8 +335,8 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   TRYP(upload_c(p, &p->twL32, t.tw_L));
   TRYP(upload_c(p, &p->twNt64, t.tw_Nt));
   TRYP(upload_c(p, &p->twNt32, t.tw_Nt));
-  TRYP(upload(p, &p->Ebr64, t.Ehat_br));
-  TRYP(upload(p, &p->Ebr32, t.Ehat_br));
+  TRYP(upload(p, &p->Ebr64, t.Ehat_f));
+  TRYP(upload(p, &p->Ebr32, t.Ehat_f));
   TRYP(upload_c(p, &p->lambda, t.lambda));
   TRYP(upload(p, &p->sfwd64, t.scale_fwd));
   TRYP(upload(p, &p->sinv64, t.scale_inv));
@@ -344,13 +344,13 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   TRYP(upload(p, &p->sinv32, t.scale_inv));
   TRYP(upload_c(p, &p->chirp64, t.chirp));
   TRYP(upload_c(p, &p->chirp32, t.chirp));
-  TRYP(upload_c(p, &p->chat64, t.chirp_hat_br));
-  TRYP(upload_c(p, &p->chat32, t.chirp_hat_br));
+  TRYP(upload_c(p, &p->chat64, t.chirp_hat_f));
+  TRYP(upload_c(p, &p->chat32, t.chirp_hat_f));
   TRYP(upload(p, &p->seig64, t.strang_eig));
   TRYP(upload(p, &p->seig32, t.strang_eig));
   if (t.tau_ok) {
-    TRYP(upload(p, &p->tau64, t.tau_eig_br));
-    TRYP(upload(p, &p->tau32, t.tau_eig_br));
+    TRYP(upload(p, &p->tau64, t.tau_eig_f));
+    TRYP(upload(p, &p->tau32, t.tau_eig_f));
   }
   const size_t n = p->n;
   const size_t csz = p->mixed ? sizeof(float2) : sizeof(double2);

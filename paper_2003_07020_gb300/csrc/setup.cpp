@@ -63,6 +63,14 @@ static int64_t bitrev64(int64_t k, int logn) {
   return r;
 }
 
+int64_t fused_to_freq(int64_t p, int logN) {
+  const int r = logN < 4 ? logN : 4;
+  const int64_t R = int64_t(1) << r;
+  const int64_t blk = p / R, m = p % R;
+  const int64_t pos = blk * R + bitrev64(m, r);  // bit-reversed position
+  return bitrev64(pos, logN);
+}
+
 bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, double eps,
                   HostTables& t, const char** err) {
   if (M < 1) { *err = "M must be >= 1"; return false; }
@@ -97,8 +105,8 @@ bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, d
   host_fft(e, -1);
   t.Ehat_half.resize((size_t)L / 2 + 1);
   for (int64_t m = 0; m <= L / 2; ++m) t.Ehat_half[m] = c * e[m].real() / (double)(L / 2);
-  t.Ehat_br.resize((size_t)L);
-  for (int64_t p = 0; p < L; ++p) t.Ehat_br[p] = c * e[bitrev64(p, t.logL)].real() / (double)L;
+  t.Ehat_f.resize((size_t)L);
+  for (int64_t p = 0; p < L; ++p) t.Ehat_f[p] = c * e[fused_to_freq(p, t.logL)].real() / (double)L;
 
   t.tw_L.resize((size_t)L / 2);
   for (int64_t m = 0; m < L / 2; ++m) t.tw_L[m] = unit_root(m, L, -1);
@@ -128,8 +136,8 @@ bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, d
     if (d > 0) b[L - d] = std::conj(t.chirp[d]);
   }
   host_fft(b, -1);  // DFT_L of the chirp filter
-  t.chirp_hat_br.resize((size_t)L);
-  for (int64_t p = 0; p < L; ++p) t.chirp_hat_br[p] = b[bitrev64(p, t.logL)] / (double)L;
+  t.chirp_hat_f.resize((size_t)L);
+  for (int64_t p = 0; p < L; ++p) t.chirp_hat_f[p] = b[fused_to_freq(p, t.logL)] / (double)L;
   std::vector<cd> a((size_t)L, cd(0, 0));
   for (int64_t k = 0; k < M; ++k) {
     const double s = (k <= M / 2) ? t.g[k] : t.g[M - k];
@@ -160,8 +168,11 @@ bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, d
       sig[j] = sq / unit_root(j, L, +1).imag();  // sin(pi j/(M+1)) = sin(2 pi j / L)
       sig[L - j] = sig[j];
     }
-    t.tau_eig_br.resize((size_t)L);
-    for (int64_t p = 0; p < L; ++p) t.tau_eig_br[p] = c * sig[bitrev64(p, t.logL)];
+    t.tau_eig_f.resize((size_t)L);
+    for (int64_t p = 0; p < L; ++p) {
+      const int64_t f = fused_to_freq(p, t.logL);
+      t.tau_eig_f[p] = (f == 0 || f == M + 1) ? 1e30 : c * sig[f];
+    }
   }
   return true;
 }

@@ -28,7 +28,7 @@ struct HostTables {
   double tau = 0, h = 0, c = 0, eps = 0;
   std::vector<double> g;            // g_0 .. g_{M+1}
   std::vector<double> Ehat_half;    // c * DFT_L(e)_m / (L/2), m = 0 .. L/2 (matvec, FP64 R2C form)
-  std::vector<double> Ehat_br;      // c * DFT_L(e)_m / L in bit-reversed order (complex-vector form)
+  std::vector<double> Ehat_f;       // c * DFT_L(e)_m / L in fused-pass order (complex-vector form)
   std::vector<cd> tw_L;             // exp(-2 pi i m / L), m < L/2
   std::vector<cd> tw_Nt;            // exp(-2 pi i m / Nt), m < Nt/2
   std::vector<cd> lambda;           // lambda_n of C_eps, n = 0 .. Nt/2
@@ -37,11 +37,17 @@ struct HostTables {
   // Strang circulant (Bluestein form)
   std::vector<double> strang_eig;   // c * DFT_M(s)_k, k < M
   std::vector<cd> chirp;            // exp(-pi i j^2 / M), j < M
-  std::vector<cd> chirp_hat_br;     // DFT_L(b)_m / L, bit-reversed, b_d = conj(chirp_|d|)
+  std::vector<cd> chirp_hat_f;      // DFT_L(b)_m / L in fused-pass order, b_d = conj(chirp_|d|)
   // natural tau matrix (DST form), valid when L == 2(M+1)
-  std::vector<double> tau_eig_br;   // c * sigma_j for frequency j = bitrev(position); 0 at j = 0, M+1
+  std::vector<double> tau_eig_f;    // c * sigma_f in fused-pass order; 1e30 at f = 0 and f = M+1
   bool tau_ok = false;
 };
+
+// Fused-pass order of a length-2^logN spectrum (see fft_convolve): entry
+// blk * R + m holds the value for bit-reversed position blk * R + bitrev_r(m)
+// of the natural frequency bitrev_logN(that position), R = 2^r,
+// r = min(4, logN).  Returns the natural frequency for fused index p.
+int64_t fused_to_freq(int64_t p, int logN);
 
 // Fills every table for the 1D problem.  Returns false with a message on bad input.
 bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, double eps,

@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const double* __restrict_
   const int Nt = 1 << logNt;
   const int bstride = padded_size(Nt);
   const int c0 = blockIdx.x * TW;
+  C* tq = sm + TWH * bstride;
+  load_quarter(tq, tw, Nt / 4);
   // load y_k = scale_k v_k (real) into position bitrev(k); column cc -> transform cc % TWH, part cc / TWH
   for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
     const int k = idx / TW, cc = idx - k * TW;
@@ -38,8 +40,7 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const double* __restrict_
     const int q = cc & (TWH - 1), part = cc / TWH;
     smr[2 * (q * bstride + pad16(bitrev(k, logNt))) + part] = val;
   }
-  __syncthreads();
-  fft_backward(sm, logNt, TWH, bstride, tw, 0);  // sum_k y_k exp(+2 pi i nk/Nt), natural order
+  fft_backward(sm, logNt, TWH, bstride, tq, logNt);  // sum_k y_k exp(+2 pi i nk/Nt), natural order
   const int half = Nt / 2;
   for (int idx = threadIdx.x; idx < (half + 1) * TW; idx += blockDim.x) {
     const int n = idx / TW, cc = idx - n * TW;
@@ -68,6 +69,8 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
   const int bstride = padded_size(Nt);
   const int c0 = blockIdx.x * TW;
   const int half = Nt / 2;
+  C* tq = sm + TWH * bstride;
+  load_quarter(tq, tw, Nt / 4);
   for (int idx = threadIdx.x; idx < (half + 1) * TWH; idx += blockDim.x) {
     const int n = idx / TWH, q = idx - n * TWH;
     const int ca = c0 + q, cb = c0 + q + TWH;
@@ -77,8 +80,7 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
     sm[q * bstride + pad16(n)] = C{Xa.x - Xb.y, Xa.y + Xb.x};                  // Xa + i Xb
     if (n != 0 && n != half) sm[q * bstride + pad16(Nt - n)] = C{Xa.x + Xb.y, Xb.x - Xa.y};  // conj Xa + i conj Xb
   }
-  __syncthreads();
-  fft_forward(sm, logNt, TWH, bstride, tw, 0);  // sum_n Z_n exp(-2 pi i nk/Nt), bit-reversed
+  fft_forward(sm, logNt, TWH, bstride, tq, logNt);  // sum_n Z_n exp(-2 pi i nk/Nt), bit-reversed
   for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
     const int k = idx / TW, cc = idx - k * TW;
     const int col = c0 + cc;
@@ -91,7 +93,9 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
 }
 
 template <typename R>
-static size_t tdft_smem(int Nt) { return (size_t)TWH * padded_size(Nt) * sizeof(typename cplx_t<R>::type); }
+static size_t tdft_smem(int Nt) {
+  return ((size_t)TWH * padded_size(Nt) + (size_t)(Nt / 4)) * sizeof(typename cplx_t<R>::type);
+}
 
 static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
