@@ -175,7 +175,26 @@ aao_status aao_gmres_solve_host(aao_plan* plan, const double* F_host, double* U_
 aao_status aao_plan_set_profiling(aao_plan* plan, int on);
 aao_status aao_plan_get_profile(aao_plan* plan, double* ms, int64_t* launches, int reset);
 
-/* Message for the last failing call on plan (or on plan creation if NULL). */
+/*
+ * The preconditioner apply of aao_bc_precond_apply (mixed precision only)
+ * without a plan and without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, e.g. code
+ * running inside another library's memory pool or a pipeline that must not
+ * synchronise the device through an allocation.  Scratch spectrum and tables
+ * live in one fixed 16 MiB device array of the library, held by every GPU
+ * that loads it until the process exits; problems whose scratch
+ * (nsys * M * 8 bytes plus tables, nsys = Nt/2 + 1) exceeds it are rejected
+ * with AAO_EINVAL.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Calls
+ * share the array, so calls that overlap on the GPU race.  opts.prec must be
+ * AAO_PREC_MIXED; v_dev, z_dev: double[Nt][M] on the device; cuda_stream as
+ * in aao_plan_create.  Errors: see aao_last_error(NULL).
+ */
+aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, const aao_opts* opts,
+                                        const double* v_dev, double* z_dev, void* cuda_stream);
+
+/* Message for the last failing call on plan (or on plan creation, or on a
+ * call without a plan, if NULL). */
 const char* aao_last_error(const aao_plan* plan);
 
 #ifdef __cplusplus

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4
 EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan_destroy",
             "aao_plan_workspace_bytes", "aao_build_rhs", "aao_matvec", "aao_bc_precond_apply",
             "aao_gmres_solve", "aao_gmres_solve_host", "aao_plan_set_profiling", "aao_plan_get_profile",
-            "aao_last_error")
+            "aao_bc_precond_apply_noalloc", "aao_last_error")
 STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector")
 
 
@@ -81,6 +81,7 @@ def load():
     lib.aao_gmres_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
     lib.aao_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.aao_plan_get_profile.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.aao_bc_precond_apply_noalloc.argtypes = [ctypes.POINTER(AaoProblem), ctypes.POINTER(AaoOpts), vp, vp, vp]
     lib.aao_last_error.argtypes = [vp]
     lib.aao_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:

@@ -45,6 +45,11 @@ __global__ void iter_stats_kernel(const int* __restrict__ iters, const int* __re
 
 }  // namespace
 
+namespace aao {
+// Error message for calls that have no plan (see aao_last_error(NULL)).
+void set_planless_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace aao
+
 struct aao_plan {
   aao_problem prob{};
   aao_opts opts{};
