@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 M_DEF, NT_DEF, ALPHAS = 8191, 1024, (1.2, 1.5, 1.8)
+ALPHAS_2D = (1.3, 1.7)
 METRIC = "unknowns·steps/s to rel. residual 1e-10; mixed+learned vs plain FP64, 1 GB300"
 UNIT = "unknowns*steps/s"
 
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--inner", default="strang", choices=["strang", "tau"])
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--Nt", type=int, default=NT_DEF)
+    ap.add_argument("--dim", type=int, default=1, choices=[1, 2],
+                    help="2: the 2D workload (255 x 255 interior points, Nt = 256, alphas (1.3, 1.7), tau inner)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -235,6 +238,33 @@ def cocg_flops(M, inner, inner_iters_sum, n_apply, nsys):
     return inner_iters_sum * per_it + n_apply * nsys * pre
 
 
+def _pow2_at_least(x):
+    L = 4
+    while L < x:
+        L *= 2
+    return L
+
+
+def matvec2d_flops(Mx, My, Nt):
+    """2D matvec (Eq. 4.2 Kronecker sum): per time level, c_x T_x on the My rows and c_y T_y on the
+    Mx columns, two real lines per complex FFT convolution (2 FFTs of the embedding length each),
+    plus the 5-flop band and 2 adds per point."""
+    Lx, Ly = _pow2_at_least(2 * Mx), _pow2_at_least(2 * My)
+    rows = (My + 1) // 2 * (2 * fft_flops(Lx) + 8.0 * Lx)
+    cols = (Mx + 1) // 2 * (2 * fft_flops(Ly) + 8.0 * Ly)
+    return Nt * (rows + cols + 7.0 * Mx * My)
+
+
+def cocg2d_flops(Mx, My, inner_iters_sum, n_apply, nsys):
+    """2D Step (b): per COCG iteration the Toeplitz product (My row and Mx column convolutions, 2 FFTs
+    each) and the tau preconditioner (a DST per row twice, two FFTs per column), ~50 flops per point of
+    updates and dots; the preconditioner is also applied once per system before the first iteration."""
+    Lx, Ly = 2 * (Mx + 1), 2 * (My + 1)
+    pre = 2 * My * fft_flops(Lx) + 2 * Mx * fft_flops(Ly)
+    per_it = 2 * My * fft_flops(Lx) + 2 * Mx * fft_flops(Ly) + pre + 50.0 * Mx * My
+    return inner_iters_sum * per_it + n_apply * nsys * pre
+
+
 def run_ours(args):
     import torch
     from paper_2003_07020_gb300 import aao, workloads
@@ -249,24 +279,37 @@ def run_ours(args):
     prec = aao.AAO_PREC_MIXED if args.prec == "mixed" else aao.AAO_PREC_FP64
     inner = aao.AAO_INNER_STRANG if args.inner == "strang" else aao.AAO_INNER_TAU
     plans, Fs = [], []
-    for i, a in enumerate(ALPHAS):
-        p = aao.Plan(M, Nt, a, kappa=1.0, T=1.0, prec=prec, inner=inner)
-        u0, f = workloads.make_inputs(M, Nt, seed=1000 * rank + i)
-        F = torch.empty((Nt, M), dtype=torch.float64, device=dev)
-        p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
-        plans.append(p)
-        Fs.append(F)
-    U = torch.zeros((Nt, M), dtype=torch.float64, device=dev)
+    if args.dim == 2:
+        M, My, Nt = 255, 255, 256
+        args.inner = "tau"
+        p = aao.Plan(M, Nt, ALPHAS_2D[0], My=My, alpha_y=ALPHAS_2D[1], kappa=1.0, T=1.0, prec=prec,
+                     inner=aao.AAO_INNER_TAU)
+        for i in range(3):
+            u0, f = workloads.make_inputs_2d(M, My, Nt, seed=1000 * rank + i)
+            F = torch.empty((Nt, My, M), dtype=torch.float64, device=dev)
+            p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
+            plans.append(p)
+            Fs.append(F)
+    else:
+        My = 1
+        for i, a in enumerate(ALPHAS):
+            p = aao.Plan(M, Nt, a, kappa=1.0, T=1.0, prec=prec, inner=inner)
+            u0, f = workloads.make_inputs(M, Nt, seed=1000 * rank + i)
+            F = torch.empty((Nt, M), dtype=torch.float64, device=dev)
+            p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
+            plans.append(p)
+            Fs.append(F)
+    U = torch.zeros(Fs[0].shape, dtype=torch.float64, device=dev)
     infos = []
 
     def step(s):
-        i = s % len(ALPHAS)
+        i = s % len(Fs)
         U.zero_()
         return plans[i].gmres_solve(Fs[i], U)
 
     for s in range(args.warmup):
         step(s)
-    for p in plans:
+    for p in {id(p): p for p in plans}.values():
         p.get_profile(reset=True)
         p.set_profiling(True)
     stream = torch.cuda.current_stream()
@@ -292,31 +335,31 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     prof = {}
-    for p in plans:
+    for p in {id(p): p for p in plans}.values():
         p.set_profiling(False)
         for k, (t_ms, nl) in p.get_profile(reset=True).items():
             a, b = prof.get(k, (0.0, 0))
             prof[k] = (a + t_ms, b + nl)
     clocks = clk.summary()
-    value = world * M * Nt * args.steps / (ms / 1e3)
+    value = world * M * My * Nt * args.steps / (ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory)
-    Fh = [torch.empty((Nt, M), dtype=torch.float64, pin_memory=True) for _ in ALPHAS]
-    for i in range(len(ALPHAS)):
+    Fh = [torch.empty(Fs[0].shape, dtype=torch.float64, pin_memory=True) for _ in Fs]
+    for i in range(len(Fs)):
         Fh[i].copy_(Fs[i].cpu())
-    Uh = torch.empty((Nt, M), dtype=torch.float64, pin_memory=True)
+    Uh = torch.empty(Fs[0].shape, dtype=torch.float64, pin_memory=True)
     barrier()
     t0 = time.perf_counter()
     for s in range(args.steps):
-        plans[s % len(ALPHAS)].gmres_solve_host(Fh[s % len(ALPHAS)], Uh)
+        plans[s % len(Fs)].gmres_solve_host(Fh[s % len(Fs)], Uh)
     barrier()
     t_e2e = time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_e2e = float(t.item())
-    e2e = {"value": world * M * Nt * args.steps / t_e2e, "unit": UNIT,
-           "h2d_bytes_per_step": M * Nt * 8, "d2h_bytes_per_step": M * Nt * 8}
+    e2e = {"value": world * M * My * Nt * args.steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": M * My * Nt * 8, "d2h_bytes_per_step": M * My * Nt * 8}
 
     if rank != 0:
         return
@@ -327,14 +370,17 @@ def run_ours(args):
     inner_sum = sum(i["inner_iters_sum"] for i in infos)
     nsys = Nt // 2 + 1
     if dom == "matvec":
-        t_launch = prof["matvec"][0] / max(prof["matvec"][1], 1)
-        achieved = matvec_flops(M, Nt) / (t_launch * 1e-3) / 1e12
+        n_mv = sum(i["matvecs"] for i in infos)
+        t_launch = prof["matvec"][0] / max(n_mv, 1)  # per matvec (2 kernels in 2D)
+        fl = matvec_flops(M, Nt) if args.dim == 1 else matvec2d_flops(M, My, Nt)
+        achieved = fl / (t_launch * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "matvec_f64_kernel",
                 "peak_source": "FP64 FMA issue rate x 152 SMs x 2.07 GHz (derived)"}
     elif dom == "cocg":
-        t_launch = prof["cocg"][0] / max(prof["cocg"][1], 1)
-        fl = cocg_flops(M, args.inner, inner_sum, n_apply, nsys) / max(prof["cocg"][1], 1)
+        t_launch = prof["cocg"][0] / max(n_apply, 1)  # per preconditioner apply
+        fl = (cocg_flops(M, args.inner, inner_sum, n_apply, nsys) if args.dim == 1 else
+              cocg2d_flops(M, My, inner_sum, n_apply, nsys)) / max(n_apply, 1)
         pkv = FP32_PEAK_TFLOPS if args.prec == "mixed" else FP64_PEAK_TFLOPS
         achieved = fl / (t_launch * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": pkv, "unit": "TFLOP/s", "frac": achieved / pkv,
@@ -343,7 +389,7 @@ def run_ours(args):
     else:
         t_launch = prof[dom][0] / max(prof[dom][1], 1)
         hb = pk.get("hbm_gbs", 6800.0)
-        bytes_ = {"tdft_fwd": 16.0, "tdft_inv": 16.0, "vector": 16.0}[dom] * M * Nt
+        bytes_ = {"tdft_fwd": 16.0, "tdft_inv": 16.0, "vector": 16.0}[dom] * M * My * Nt
         achieved = bytes_ / (t_launch * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hb, "unit": "GB/s", "frac": achieved / hb,
                 "traffic": None, "kernel": dom}
@@ -351,9 +397,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32" if args.prec == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": "1D Riesz FDE all-at-once BDF2 to TRR<=1e-10, M=%d, Nt=%d, alpha cycling %s, "
-                               "kappa=1, T=1, sine8_normal inputs" % (M, Nt, list(ALPHAS)),
-                   "M": M, "Nt": Nt, "precision": args.prec, "inner_precond": args.inner, "restart": 20,
+        "config": {"workload": ("1D Riesz FDE all-at-once BDF2 to TRR<=1e-10, M=%d, Nt=%d, alpha cycling %s, "
+                                "kappa=1, T=1, sine8_normal inputs" % (M, Nt, list(ALPHAS))) if args.dim == 1 else
+                               ("2D Riesz FDE all-at-once BDF2 to TRR<=1e-10, %dx%d, Nt=%d, alphas %s, kappa=(1,1), "
+                                "T=1, sine16_normal inputs (seeds 0-2)" % (M, My, Nt, list(ALPHAS_2D))),
+                   "M": M, "My": My, "Nt": Nt, "precision": args.prec, "inner_precond": args.inner, "restart": 20,
                    "l2": "no explicit flush: every solve streams a >2 GB Krylov working set through the "
                          "129 MB L2",
                    "outer_iters": [i["outer_iters"] for i in infos],
@@ -364,10 +412,10 @@ def run_ours(args):
         "gpu_launches": int(sum(v[1] for v in prof.values())),
         "clocks": clocks, "roofline": roof, "e2e": e2e,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.dim == 1:
         line["cpu_baseline"] = cpu_baseline(M, Nt)
     print(json.dumps(line), flush=True)
-    for p in plans:
+    for p in {id(p): p for p in plans}.values():
         p.close()
 
 

@@ -56,15 +56,24 @@ typedef enum {
   AAO_INNER_TAU = 1     /* natural tau-matrix T - H(T), applied by DST-I (Sec. 3.2) */
 } aao_inner_precond;
 
-/* Problem description (Sec. 2.1).  1D only: dim must be 1. */
+/*
+ * Problem description (Sec. 2.1; 2D: Eq. 4.1-4.2 on (0,1)^2).
+ * 1D: unknowns per time level M, vectors double[Nt][M].
+ * 2D: K = I (x) K_x + K_y (x) I with x fastest, unknowns per time level
+ *     M * My, vectors double[Nt][My][M]; M + 1 and My + 1 must be powers of
+ *     two (the 2D inner preconditioner is the tau matrix, applied by DSTs).
+ */
 typedef struct {
-  int dim;              /* 1 */
-  int64_t M;            /* interior points; h = 1/(M+1); M+1 a power of two for AAO_INNER_TAU */
+  int dim;              /* 1 or 2 */
+  int64_t M;            /* interior points (x direction in 2D); h = 1/(M+1); M+1 a power of two for AAO_INNER_TAU */
   int64_t Nt;           /* time steps, a power of two >= 4; tau = T/Nt */
   double T;             /* final time (> 0) */
-  double alpha;         /* fractional order, 1 < alpha <= 2 */
-  double kappa;         /* diffusion coefficient, > 0 */
+  double alpha;         /* fractional order (x direction in 2D), 1 < alpha <= 2 */
+  double kappa;         /* diffusion coefficient (x direction in 2D), > 0 */
   double eps;           /* circulant parameter in (0,1]; <= 0 selects min(0.5, 0.5 tau) (Sec. 4) */
+  int64_t My;           /* 2D: interior points in y, h_y = 1/(My+1); ignored in 1D */
+  double alpha_y;       /* 2D: fractional order in y */
+  double kappa_y;       /* 2D: diffusion coefficient in y */
 } aao_problem;
 
 /* Solver options.  aao_default_opts fills the defaults given in brackets. */

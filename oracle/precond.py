@@ -226,3 +226,35 @@ def P_eps_matvec(K, tau, eps, Z):
     Nt = Z.shape[0]
     Zf = Z.reshape(Nt, -1)
     return (C_eps(Nt, eps) @ Zf - tau * (Zf @ K.T)).reshape(Z.shape)
+
+
+def precond_apply_2d(Kx, Ky, tau, eps, V):
+    """z = P_eps^{-1} v for the 2D system K = I (x) Kx + Ky (x) I (x fastest), by the
+    three steps of Sec. 3.1 with Step (b) solved by fast diagonalisation:
+    Kx = Qx Lx Qx^T, Ky = Qy Ly Qy^T (symmetric eigendecompositions, library
+    routine), so (lambda_n I - tau K)^{-1} r = (Qy (x) Qx) [(Qy^T (x) Qx^T) r /
+    (lambda_n - tau (Ly_j + Lx_i))].  ``V`` has shape (Nt, My, Mx)."""
+    V = np.asarray(V, dtype=np.float64)
+    Nt, My, Mx = V.shape
+    F = dft_matrix(Nt)
+    scale = eps ** (np.arange(Nt) / Nt)
+    Z1 = F @ (scale[:, None] * V.reshape(Nt, -1))
+    lam = eigenvalues_C_eps(Nt, eps)
+    Lx, Qx = np.linalg.eigh(Kx)
+    Ly, Qy = np.linalg.eigh(Ky)
+    lam2 = Ly[:, None] + Lx[None, :]
+    Z2 = np.empty_like(Z1)
+    for n in range(Nt):
+        rt = Qy.T @ Z1[n].reshape(My, Mx) @ Qx
+        Z2[n] = (Qy @ (rt / (lam[n] - tau * lam2)) @ Qx.T).ravel()
+    Z = (1.0 / scale)[:, None] * (F.conj().T @ Z2)
+    return Z.real.reshape(V.shape)
+
+
+def P_eps_matvec_2d(Kx, Ky, tau, eps, Z):
+    """P_eps z for the 2D system: row k is sum_j C_eps[k, j] Z[j] - tau (Z[k] Kx^T + Ky Z[k])."""
+    Z = np.asarray(Z, dtype=np.float64)
+    Nt = Z.shape[0]
+    W = np.einsum("kj,jyx->kyx", C_eps(Nt, eps), Z)
+    W -= tau * (np.einsum("kyx,ix->kyi", Z, Kx) + np.einsum("jy,kyx->kjx", Ky, Z))
+    return W

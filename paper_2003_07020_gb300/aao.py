@@ -30,7 +30,8 @@ STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector")
 
 class AaoProblem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("M", ctypes.c_int64), ("Nt", ctypes.c_int64), ("T", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("kappa", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("kappa", ctypes.c_double), ("eps", ctypes.c_double),
+                ("My", ctypes.c_int64), ("alpha_y", ctypes.c_double), ("kappa_y", ctypes.c_double)]
 
 
 class AaoOpts(ctypes.Structure):
@@ -122,10 +123,19 @@ def _stream_ptr(stream):
 class Plan:
     """An ``aao_plan``: one 1D problem with its device workspace."""
 
-    def __init__(self, M, Nt, alpha, kappa=1.0, T=1.0, eps=0.0, opts=None, stream=None, **opt_kw):
+    def __init__(self, M, Nt, alpha, kappa=1.0, T=1.0, eps=0.0, opts=None, stream=None, My=None, alpha_y=None,
+                 kappa_y=None, **opt_kw):
+        """1D: M interior points.  2D (My given): M x My interior points, x fastest; alpha_y and kappa_y
+        default to alpha and kappa."""
         lib = load()
         self.M, self.Nt = int(M), int(Nt)
-        self.problem = AaoProblem(1, self.M, self.Nt, float(T), float(alpha), float(kappa), float(eps))
+        dim = 1 if My is None else 2
+        self.My = 1 if My is None else int(My)
+        self.problem = AaoProblem(dim, self.M, self.Nt, float(T), float(alpha), float(kappa), float(eps),
+                                  self.My if dim == 2 else 0, float(alpha if alpha_y is None else alpha_y),
+                                  float(kappa if kappa_y is None else kappa_y))
+        if dim == 2 and "inner" not in opt_kw and opts is None:
+            opt_kw["inner"] = AAO_INNER_TAU
         self.opts = opts if opts is not None else default_opts(**opt_kw)
         self._stream = stream
         h = ctypes.c_void_p()
@@ -157,8 +167,8 @@ class Plan:
     def _vec(self, t, name):
         if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
             raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
-        if t.numel() != self.M * self.Nt:
-            raise ValueError("%s must have Nt*M = %d elements" % (name, self.M * self.Nt))
+        if t.numel() != self.M * self.My * self.Nt:
+            raise ValueError("%s must have Nt*M*My = %d elements" % (name, self.M * self.My * self.Nt))
         return ctypes.c_void_p(t.data_ptr())
 
     def set_profiling(self, on=True):
@@ -174,8 +184,8 @@ class Plan:
         return {s: (float(ms[i]), int(ln[i])) for i, s in enumerate(STAGES)}
 
     def build_rhs(self, u0, f, F):
-        if not (u0.is_cuda and u0.numel() == self.M):
-            raise ValueError("u0 must be a CUDA tensor of M elements")
+        if not (u0.is_cuda and u0.numel() == self.M * self.My):
+            raise ValueError("u0 must be a CUDA tensor of M*My elements")
         _check(load().aao_build_rhs(self.handle, ctypes.c_void_p(u0.data_ptr()), self._vec(f, "f"),
                                     self._vec(F, "F")), self.handle)
 
@@ -195,7 +205,7 @@ class Plan:
     def gmres_solve_host(self, F_host, U_host, raise_on_noconv=True):
         """F_host, U_host: float64 host arrays/tensors of Nt*M elements (pinned preferred)."""
         def ptr(a, name):
-            n = self.M * self.Nt
+            n = self.M * self.My * self.Nt
             if hasattr(a, "data_ptr"):  # torch tensor
                 if a.is_cuda or a.element_size() != 8 or not a.is_contiguous() or a.numel() != n:
                     raise ValueError("%s must be a contiguous float64 host tensor of Nt*M elements" % name)

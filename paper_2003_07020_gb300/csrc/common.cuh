@@ -353,6 +353,64 @@ __device__ __forceinline__ void fused_mid_pass(T* buf, int logN, F factor) {
   }
 }
 
+// Batched form of fused_mid_pass: factor(b, pf) for transform b.
+template <typename T, int r, typename F>
+__device__ __forceinline__ void fused_mid_pass_b(T* buf, int logN, int batch, int bstride, F factor) {
+  constexpr int R = 1 << r;
+  const int per = 1 << (logN - r);
+  for (int gg = threadIdx.x; gg < batch * per; gg += blockDim.x) {
+    const int b = gg >> (logN - r);
+    const int start = (gg & (per - 1)) << r;
+    T* base = buf + b * bstride;
+    T v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = base[pad16(start + k)];
+    dft<-1, r>(v);
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = cmul(v[m], factor(b, start + m));
+    dft<+1, r>(v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) base[pad16(start + k)] = v[k];
+  }
+}
+
+// fft_convolve over `batch` transforms at buf + b * bstride; factor(b, pf).
+template <typename T, typename F>
+__device__ void fft_convolve_batched(T* buf, int logN, int batch, int bstride, const T* q, int logNq, F factor,
+                                     const T* pt = nullptr) {
+  __syncthreads();
+  const int r0 = first_pass_stages(logN);
+  int s0 = 0, r = r0, off = 0;
+  while (s0 + r < logN) {
+    if (s0 == 0) {
+      dif_pass_any<T>(r, buf, logN, 0, batch, bstride, q, logNq);
+    } else {
+      dif_pass<T, 4>(buf, logN, s0, batch, bstride, q, logNq, pt ? pt + off : nullptr);
+      off += 15 * (1 << (logN - s0 - 4));
+    }
+    __syncthreads();
+    s0 += r;
+    r = 4;
+  }
+  switch (logN - s0) {
+    case 1: fused_mid_pass_b<T, 1>(buf, logN, batch, bstride, factor); break;
+    case 2: fused_mid_pass_b<T, 2>(buf, logN, batch, bstride, factor); break;
+    case 3: fused_mid_pass_b<T, 3>(buf, logN, batch, bstride, factor); break;
+    default: fused_mid_pass_b<T, 4>(buf, logN, batch, bstride, factor); break;
+  }
+  __syncthreads();
+  if (s0 > 0) {
+    int t0 = s0 - 4;
+    while (t0 >= r0) {
+      dit_pass<T, 4>(buf, logN, t0, batch, bstride, q, logNq, pt ? pt + pass_table_offset(logN, t0) : nullptr);
+      __syncthreads();
+      t0 -= 4;
+    }
+    dit_pass_any<T>(r0, buf, logN, 0, batch, bstride, q, logNq);
+    __syncthreads();
+  }
+}
+
 template <typename T, typename F>
 __device__ void fft_convolve(T* buf, int logN, const T* q, int logNq, F factor, const T* pt = nullptr) {
   __syncthreads();

@@ -62,6 +62,42 @@ cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gb
                             int* iters, int* flags, int grid, cudaStream_t s);
 size_t cocg_gbuf_elems_f64(int logL, int grid);
 
+// ---- 2D problem, twod.cu ----------------------------------------------------------------
+// w = calA v (or rhs - calA v) for K = I (x) K_x + K_y (x) I (x fastest); tmp: n doubles of scratch;
+// sq (optional): per-CTA sums of squares of w, mv2d_partials(Mx, Nt, logLy) of them.
+cudaError_t launch_matvec2d_f64(const double* v, const double* rhs, double* w, double* tmp, double* sq, int Mx,
+                                int My, int Nt, int logLx, int logLy, const double2* twx, const double2* twy,
+                                const double* Exf, const double* Eyf, cudaStream_t s);
+cudaError_t launch_matvec2d_f64_fin(const float* v, const double* rhs, double* w, double* tmp, double* sq, int Mx,
+                                    int My, int Nt, int logLx, int logLy, const double2* twx, const double2* twy,
+                                    const double* Exf, const double* Eyf, cudaStream_t s);
+size_t mv2d_partials(int Mx, int Nt, int logLy);
+
+template <typename R> struct VecT;
+template <> struct VecT<float> { using c = float2; };
+template <> struct VecT<double> { using c = double2; };
+// Step (b) in 2D: all systems' COCG iterations with the 2D tau preconditioner.
+template <typename R> struct Cocg2dArgs {
+  using C = typename VecT<R>::c;
+  C *X, *Rr, *P, *Z, *Q, *Tm;  // [nsys][My][Mx]; X: rhs in, solution out
+  int Mx, My, nsys, logLx, logLy;
+  const C *twx, *twy;          // exp(-2 pi i m / L) tables
+  const R *Exf, *Eyf;          // c * DFT(embedding) / L, fused-pass order
+  const R *sxn, *syf;          // c_x sigma^x (natural), c_y sigma^y (fused, 1e30 where the DST multiplier vanishes)
+  const double2* lambda;
+  void* state;                 // cocg2d_state_bytes(nsys)
+  double2* part;               // nsys * cocg2d_max_partials(...) partial sums
+  int* active_count;           // device int
+  int* host_count;             // pinned host int
+  int *iters, *flags;          // per system
+  double tol;
+  int maxit;
+};
+size_t cocg2d_state_bytes(int nsys);
+int cocg2d_max_partials(int Mx, int My, int logLx, int logLy, int csize);
+cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* iters_run);
+cudaError_t launch_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, int* iters_run);
+
 // ---- vector kernels (FP64), blas.cu ----------------------------------------------------
 int blas_partial_blocks();
 // partial[b*nv + i] = sum over block b's elements of w[e] * V[i*vstride + e]

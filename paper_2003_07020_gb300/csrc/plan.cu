@@ -57,6 +57,19 @@ struct aao_plan {
   aao::HostTables ht;
   int M = 0, Nt = 0, logL = 0, nsys = 0, m = 0;
   size_t n = 0;
+  // 2D (dim == 2): M is M_x; Msp = spatial unknowns per time level (M in 1D, M * My in 2D)
+  int dim = 1, My = 1, logLy = 0;
+  size_t Msp = 0;
+  aao::HostTables hty;
+  double2 *twy64 = nullptr, *Px = nullptr, *Zx = nullptr, *Qx = nullptr, *Tx = nullptr;
+  float2* twy32 = nullptr;
+  double *Exf64 = nullptr, *Eyf64 = nullptr, *sxn64 = nullptr, *syf64 = nullptr, *tmp2d = nullptr;
+  float *Exf32 = nullptr, *Eyf32 = nullptr, *sxn32 = nullptr, *syf32 = nullptr;
+  void* state2d = nullptr;
+  double2* part2d = nullptr;
+  int* active2d = nullptr;
+  int* host_count = nullptr;
+  size_t nsq = 0;  // partial sums produced by the residual matvec
   bool mixed = true;
   std::vector<void*> allocs;
   size_t ws_bytes = 0;
@@ -210,6 +223,17 @@ aao_status reduce_to_host(aao_plan* p, const double* partials, int nblocks, int 
 }
 
 aao_status matvec_any(aao_plan* p, const void* v, bool v_is_f32, const double* rhs, double* w, double* sq) {
+  if (p->dim == 2) {
+    if (v_is_f32)
+      LAUNCH(ST_MATVEC, 2, aao::launch_matvec2d_f64_fin((const float*)v, rhs, w, p->tmp2d, sq, p->M, p->My, p->Nt,
+                                                        p->logL, p->logLy, p->twL64, p->twy64, p->Exf64, p->Eyf64,
+                                                        p->stream));
+    else
+      LAUNCH(ST_MATVEC, 2, aao::launch_matvec2d_f64((const double*)v, rhs, w, p->tmp2d, sq, p->M, p->My, p->Nt,
+                                                    p->logL, p->logLy, p->twL64, p->twy64, p->Exf64, p->Eyf64,
+                                                    p->stream));
+    return AAO_OK;
+  }
   if (v_is_f32)
     LAUNCH(ST_MATVEC, 1, aao::launch_matvec_f64_fin((const float*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->Ehalf,
                                                     p->twL64, p->stream));
@@ -220,28 +244,77 @@ aao_status matvec_any(aao_plan* p, const void* v, bool v_is_f32, const double* r
 }
 
 // out = P^{-1} v.  out_kind: 0 float (mixed Z basis), 1 double.
+// Step (b) in 2D: all shifted systems by the batched COCG of twod.cu
+template <typename R>
+aao_status cocg2d_any(aao_plan* p, void* spec) {
+  using C = typename aao::VecT<R>::c;
+  aao::Cocg2dArgs<R> a{};
+  a.X = (C*)spec;
+  a.Rr = (C*)p->rws;
+  a.P = (C*)p->Px;
+  a.Z = (C*)p->Zx;
+  a.Q = (C*)p->Qx;
+  a.Tm = (C*)p->Tx;
+  a.Mx = p->M;
+  a.My = p->My;
+  a.nsys = p->nsys;
+  a.logLx = p->logL;
+  a.logLy = p->logLy;
+  if constexpr (sizeof(R) == 4) {
+    a.twx = p->twL32; a.twy = p->twy32; a.Exf = p->Exf32; a.Eyf = p->Eyf32; a.sxn = p->sxn32; a.syf = p->syf32;
+  } else {
+    a.twx = p->twL64; a.twy = p->twy64; a.Exf = p->Exf64; a.Eyf = p->Eyf64; a.sxn = p->sxn64; a.syf = p->syf64;
+  }
+  a.lambda = p->lambda;
+  a.state = p->state2d;
+  a.part = p->part2d;
+  a.active_count = p->active2d;
+  a.host_count = p->host_count;
+  a.iters = p->iters;
+  a.flags = p->flags;
+  a.tol = p->opts.inner_tol;
+  a.maxit = p->opts.inner_maxit;
+  int its = 0;
+  prof_begin(p);
+  cudaError_t e = sizeof(R) == 4 ? aao::launch_cocg2d_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream, &its)
+                                 : aao::launch_cocg2d_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, p->stream, &its);
+  if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("cocg2d: ") + cudaGetErrorString(e));
+  prof_end(p, ST_COCG, 4 + its * 11);
+  return AAO_OK;
+}
+
+// out = P^{-1} v.  out_kind: 0 float (mixed Z basis), 1 double.
 aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
+  const int Ms = (int)p->Msp;
   if (p->mixed) {
     float2* spec = (float2*)p->spec;
-    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f32(v, spec, p->M, p->Nt, p->sfwd32, p->twNt32, p->stream));
-    aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
-    LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
-                                            (int)p->opts.inner, tb, (float)p->opts.inner_tol, p->opts.inner_maxit,
-                                            p->iters, p->flags, p->cocg_grid, p->stream));
+    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f32(v, spec, Ms, p->Nt, p->sfwd32, p->twNt32, p->stream));
+    if (p->dim == 2) {
+      TRY(cocg2d_any<float>(p, spec));
+    } else {
+      aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
+      LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
+                                              (int)p->opts.inner, tb, (float)p->opts.inner_tol, p->opts.inner_maxit,
+                                              p->iters, p->flags, p->cocg_grid, p->stream));
+    }
     if (out_kind == 0)
-      LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32(spec, (float*)out, p->M, p->Nt, p->sinv32, p->twNt32,
+      LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32(spec, (float*)out, Ms, p->Nt, p->sinv32, p->twNt32,
                                                       p->stream));
     else
-      LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32_to_f64(spec, (double*)out, p->M, p->Nt, p->sinv32,
+      LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32_to_f64(spec, (double*)out, Ms, p->Nt, p->sinv32,
                                                              p->twNt32, p->stream));
   } else {
     double2* spec = (double2*)p->spec;
-    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f64(v, spec, p->M, p->Nt, p->sfwd64, p->twNt64, p->stream));
-    aao::CocgTables64 tb{p->twL64, p->Ebr64, p->lambda, p->chirp64, p->chat64, p->seig64, p->tau64};
-    LAUNCH(ST_COCG, 1, aao::launch_cocg_f64(spec, (double2*)p->rws, (double2*)p->pws, p->gbuf, p->M, p->logL,
-                                            p->nsys, (int)p->opts.inner, tb, p->opts.inner_tol, p->opts.inner_maxit,
-                                            p->iters, p->flags, p->cocg_grid, p->stream));
-    LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f64(spec, (double*)out, p->M, p->Nt, p->sinv64, p->twNt64,
+    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f64(v, spec, Ms, p->Nt, p->sfwd64, p->twNt64, p->stream));
+    if (p->dim == 2) {
+      TRY(cocg2d_any<double>(p, spec));
+    } else {
+      aao::CocgTables64 tb{p->twL64, p->Ebr64, p->lambda, p->chirp64, p->chat64, p->seig64, p->tau64};
+      LAUNCH(ST_COCG, 1, aao::launch_cocg_f64(spec, (double2*)p->rws, (double2*)p->pws, p->gbuf, p->M, p->logL,
+                                              p->nsys, (int)p->opts.inner, tb, p->opts.inner_tol,
+                                              p->opts.inner_maxit, p->iters, p->flags, p->cocg_grid, p->stream));
+    }
+    LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f64(spec, (double*)out, Ms, p->Nt, p->sinv64, p->twNt64,
                                                     p->stream));
   }
   return AAO_OK;
@@ -249,8 +322,16 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
 
 aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (!prob || !o) return fail(nullptr, AAO_EINVAL, "null problem or options");
-  if (prob->dim != 1) return fail(nullptr, AAO_EINVAL, "only dim = 1 is supported");
+  if (prob->dim != 1 && prob->dim != 2) return fail(nullptr, AAO_EINVAL, "dim must be 1 or 2");
   if (prob->M < 1 || prob->M > 8191) return fail(nullptr, AAO_EINVAL, "M must be in [1, 8191]");
+  if (prob->dim == 2) {
+    if (prob->M > 2047 || prob->My < 1 || prob->My > 2047)
+      return fail(nullptr, AAO_EINVAL, "2D: M and My must be in [1, 2047]");
+    if (((prob->M + 1) & prob->M) || ((prob->My + 1) & prob->My))
+      return fail(nullptr, AAO_EINVAL, "2D: M+1 and My+1 must be powers of two");
+    if (o->inner != AAO_INNER_TAU)
+      return fail(nullptr, AAO_EINVAL, "2D: the inner preconditioner must be AAO_INNER_TAU (2D tau matrix)");
+  }
   if (prob->Nt < 4 || prob->Nt > 65536 || (prob->Nt & (prob->Nt - 1)))
     return fail(nullptr, AAO_EINVAL, "Nt must be a power of two in [4, 65536]");
   if (o->restart < 1 || o->restart > kMaxRestart) return fail(nullptr, AAO_EINVAL, "restart must be in [1, 64]");
@@ -300,6 +381,7 @@ aao_status aao_plan_destroy(aao_plan* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (void* q : p->allocs) cudaFree(q);
   if (p->pinned) cudaFreeHost(p->pinned);
+  if (p->host_count) cudaFreeHost(p->host_count);
   delete p;
   return AAO_OK;
 }
@@ -318,12 +400,21 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     delete p;
     return fail(nullptr, AAO_EINVAL, emsg);
   }
+  p->dim = prob->dim;
+  if (p->dim == 2 &&
+      !aao::build_tables(prob->My, prob->Nt, prob->T, prob->alpha_y, prob->kappa_y, prob->eps, p->hty, &emsg)) {
+    delete p;
+    return fail(nullptr, AAO_EINVAL, emsg);
+  }
   p->M = (int)prob->M;
+  p->My = p->dim == 2 ? (int)prob->My : 1;
+  p->Msp = (size_t)p->M * p->My;
   p->Nt = (int)prob->Nt;
   p->logL = p->ht.logL;
+  p->logLy = p->dim == 2 ? p->hty.logL : 0;
   p->nsys = p->Nt / 2 + 1;
   p->m = opts->restart;
-  p->n = (size_t)p->M * p->Nt;
+  p->n = p->Msp * p->Nt;
   auto bail = [&](aao_status st) {
     g_create_error = p->err;
     aao_plan_destroy(p);
@@ -367,12 +458,37 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   }
   {
     unsigned char* q;
-    TRYP(dalloc(p, &q, (size_t)p->nsys * p->M * csz));
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz));
     p->spec = q;
-    TRYP(dalloc(p, &q, (size_t)p->nsys * p->M * csz));
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz));
     p->rws = q;
-    TRYP(dalloc(p, &q, (size_t)p->nsys * p->M * csz));
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz));
     p->pws = q;
+  }
+  p->nsq = (size_t)p->Nt;
+  if (p->dim == 2) {
+    const aao::HostTables& ty = p->hty;
+    TRYP(upload_c(p, &p->twy64, ty.tw_L));
+    TRYP(upload_c(p, &p->twy32, ty.tw_L));
+    TRYP(upload(p, &p->Exf64, t.Ehat_f));
+    TRYP(upload(p, &p->Exf32, t.Ehat_f));
+    TRYP(upload(p, &p->Eyf64, ty.Ehat_f));
+    TRYP(upload(p, &p->Eyf32, ty.Ehat_f));
+    TRYP(upload(p, &p->sxn64, t.tau_eig_nat));
+    TRYP(upload(p, &p->sxn32, t.tau_eig_nat));
+    TRYP(upload(p, &p->syf64, ty.tau_eig_f));
+    TRYP(upload(p, &p->syf32, ty.tau_eig_f));
+    unsigned char* q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz)); p->Px = (double2*)q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz)); p->Zx = (double2*)q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz)); p->Qx = (double2*)q;
+    TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz)); p->Tx = (double2*)q;
+    TRYP(dalloc(p, &p->tmp2d, p->n));
+    TRYP(dalloc(p, &q, aao::cocg2d_state_bytes(p->nsys))); p->state2d = q;
+    const int np = aao::cocg2d_max_partials(p->M, p->My, p->logL, p->logLy, (int)csz);
+    TRYP(dalloc(p, &p->part2d, (size_t)p->nsys * np));
+    TRYP(dalloc(p, &p->active2d, 1));
+    p->nsq = aao::mv2d_partials(p->M, p->Nt, p->logLy);
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -390,9 +506,14 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   TRYP(dalloc(p, &p->stats, 4));
   TRYP(dalloc(p, &p->partial, (size_t)std::max(aao::blas_partial_blocks() * 65, p->Nt)));
   TRYP(dalloc(p, &p->hdev, 4 * 65));
-  TRYP(dalloc(p, &p->sq, (size_t)p->Nt));
+  TRYP(dalloc(p, &p->sq, p->nsq));
   if (cudaMallocHost(&p->pinned, 4 * 65 * sizeof(double)) != cudaSuccess) {
     p->pinned = nullptr;
+    p->err = "cudaMallocHost failed";
+    return bail(AAO_ENOMEM);
+  }
+  if (p->dim == 2 && cudaMallocHost(&p->host_count, sizeof(int)) != cudaSuccess) {
+    p->host_count = nullptr;
     p->err = "cudaMallocHost failed";
     return bail(AAO_ENOMEM);
   }
@@ -429,7 +550,7 @@ aao_status aao_plan_get_profile(aao_plan* p, double* ms, int64_t* launches, int 
 aao_status aao_build_rhs(aao_plan* p, const double* u0, const double* f, double* F) {
   if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
   if (!u0 || !f || !F) return fail(p, AAO_EINVAL, "null pointer");
-  LAUNCH(ST_VEC, 1, aao::launch_build_rhs(u0, f, F, p->ht.tau, p->M, p->Nt, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_build_rhs(u0, f, F, p->ht.tau, (int)p->Msp, p->Nt, p->stream));
   return AAO_OK;
 }
 
@@ -472,7 +593,7 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     TRY(matvec_any(p, U, false, F, p->V, p->sq));
     inf.matvecs++;
     double beta2 = 0;
-    TRY(reduce_to_host(p, p->sq, p->Nt, 1, &beta2));
+    TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));
     const double beta = std::sqrt(beta2);
     if (!std::isfinite(beta)) { result = AAO_ENONFINITE; p->err = "non-finite residual"; break; }
     inf.true_rel_res = beta / nF;

@@ -168,6 +168,8 @@ bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, d
       sig[j] = sq / unit_root(j, L, +1).imag();  // sin(pi j/(M+1)) = sin(2 pi j / L)
       sig[L - j] = sig[j];
     }
+    t.tau_eig_nat.resize((size_t)M);
+    for (int64_t j = 1; j <= M; ++j) t.tau_eig_nat[j - 1] = c * sig[j];
     t.tau_eig_f.resize((size_t)L);
     for (int64_t p = 0; p < L; ++p) {
       const int64_t f = fused_to_freq(p, t.logL);

@@ -40,6 +40,7 @@ struct HostTables {
   std::vector<cd> chirp_hat_f;      // DFT_L(b)_m / L in fused-pass order, b_d = conj(chirp_|d|)
   // natural tau matrix (DST form), valid when L == 2(M+1)
   std::vector<double> tau_eig_f;    // c * sigma_f in fused-pass order; 1e30 at f = 0 and f = M+1
+  std::vector<double> tau_eig_nat;  // c * sigma_j, j = 1..M, stored at j - 1
   bool tau_ok = false;
 };
 

@@ -1,0 +1,522 @@
+// The 2D all-at-once system: K = I (x) K_x + K_y (x) I (x fastest), the
+// Kronecker-sum Jacobian of Eq. 4.2, on (0,1)^2 with M_x x M_y interior
+// points.  A time level is a "slab" [My][Mx]; a system of Step (b) is a
+// complex slab.  Operators are separable, so every kernel here works on
+// batches of lines: rows (x direction, contiguous) or columns (y direction,
+// stride Mx, loaded as tiles of consecutive columns so that global accesses
+// stay coalesced), each line transformed with the shared-memory FFT engine.
+//
+//  * matvec (FP64): c_x T_x along rows and c_y T_y along columns by
+//    circulant-embedding convolutions; two real lines share one complex
+//    transform (the embedding spectrum is real and even); the BDF band of
+//    Eq. 1.7 is added in the column pass.
+//  * Step (b): preconditioned COCG on all systems at once, with the 2D tau
+//    matrix tau(T_x) (x) I + I (x) tau(T_y) (Sec. 4, Ex. 2) as preconditioner:
+//    P^{-1} = (2/(Mx+1)) S_x [ (2/(My+1)) S_y D S_y ] S_x with the DST-I
+//    matrices S and D = 1/(lambda_n + c_x sigma^x_i + c_y sigma^y_j).
+//    Per-system scalars (rho, a, beta) and convergence flags live on the
+//    device; kernels skip converged systems.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace aao {
+
+namespace {
+
+template <typename R> using Cx = typename cplx_t<R>::type;
+
+constexpr int kLineThreads = 256;
+constexpr int kElemThreads = 256;
+
+__host__ __device__ inline int lines_per_cta(int L, int csize) {
+  const int b = 73728 / (padded_size(L) * csize);
+  return b < 1 ? 1 : (b > 16 ? 16 : b);
+}
+
+template <typename TIn> __device__ __forceinline__ double ldd(const TIn* p) { return (double)__ldg(p); }
+
+// ---------------------------------------------------------------- matvec, FP64
+// tmp[k][j][i] = c_x (T_x v[k][j][:])_i, rows j = 2q, 2q+1 packed as one complex line
+template <typename TIn>
+__global__ void __launch_bounds__(kLineThreads) mv2d_rows(const TIn* __restrict__ v, double* __restrict__ tmp, int Mx,
+                                                          int My, int logLx, const double2* __restrict__ twx,
+                                                          const double* __restrict__ Exf, int B) {
+  extern __shared__ unsigned char smraw[];
+  double2* buf = reinterpret_cast<double2*>(smraw);
+  const int Lx = 1 << logLx, bs = padded_size(Lx);
+  double2* q = buf + B * bs;
+  load_quarter(q, twx, Lx / 4);
+  const size_t slab = (size_t)blockIdx.y * Mx * My;
+  const int pair0 = blockIdx.x * B, npairs = (My + 1) / 2;
+  for (int idx = threadIdx.x; idx < B * Lx; idx += blockDim.x) {
+    const int b = idx / Lx, i = idx - b * Lx, pr = pair0 + b;
+    double x0 = 0, x1 = 0;
+    if (pr < npairs && i < Mx) {
+      x0 = ldd(v + slab + (size_t)(2 * pr) * Mx + i);
+      if (2 * pr + 1 < My) x1 = ldd(v + slab + (size_t)(2 * pr + 1) * Mx + i);
+    }
+    buf[b * bs + pad16(i)] = double2{x0, x1};
+  }
+  fft_convolve_batched(buf, logLx, B, bs, q, logLx, [&](int, int pf) { return double2{__ldg(&Exf[pf]), 0.0}; });
+  for (int idx = threadIdx.x; idx < B * Mx; idx += blockDim.x) {
+    const int b = idx / Mx, i = idx - b * Mx, pr = pair0 + b;
+    if (pr >= npairs) continue;
+    const double2 t = buf[b * bs + pad16(i)];
+    tmp[slab + (size_t)(2 * pr) * Mx + i] = t.x;
+    if (2 * pr + 1 < My) tmp[slab + (size_t)(2 * pr + 1) * Mx + i] = t.y;
+  }
+}
+
+// w = band(v) + tmp + c_y T_y v (columns; 2B columns per CTA, packed in pairs), or rhs - that;
+// per-CTA sums of squares in sq_partial[k * gridDim.x + blockIdx.x]
+template <typename TIn>
+__global__ void __launch_bounds__(kLineThreads) mv2d_cols(const TIn* __restrict__ v, const double* __restrict__ tmp,
+                                                          const double* __restrict__ rhs, double* __restrict__ w,
+                                                          double* __restrict__ sq_partial, int Mx, int My, int logLy,
+                                                          const double2* __restrict__ twy,
+                                                          const double* __restrict__ Eyf, int B) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ double red[32];
+  double2* buf = reinterpret_cast<double2*>(smraw);
+  double* bufr = reinterpret_cast<double*>(smraw);
+  const int Ly = 1 << logLy, bs = padded_size(Ly);
+  double2* q = buf + B * bs;
+  load_quarter(q, twy, Ly / 4);
+  const int k = blockIdx.y;
+  const size_t Ms = (size_t)Mx * My, slab = (size_t)k * Ms;
+  const int i0 = blockIdx.x * 2 * B, W = 2 * B;
+  for (int idx = threadIdx.x; idx < Ly * W; idx += blockDim.x) {
+    const int j = idx / W, cc = idx - j * W, i = i0 + cc;
+    const double val = (j < My && i < Mx) ? ldd(v + slab + (size_t)j * Mx + i) : 0.0;
+    bufr[2 * ((cc >> 1) * bs + pad16(j)) + (cc & 1)] = val;
+  }
+  fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int, int pf) { return double2{__ldg(&Eyf[pf]), 0.0}; });
+  double sq = 0;
+  for (int idx = threadIdx.x; idx < My * W; idx += blockDim.x) {
+    const int j = idx / W, cc = idx - j * W, i = i0 + cc;
+    if (i >= Mx) continue;
+    const size_t e = slab + (size_t)j * Mx + i;
+    const double y = bufr[2 * ((cc >> 1) * bs + pad16(j)) + (cc & 1)];
+    double band;
+    if (k == 0) band = ldd(v + e);
+    else if (k == 1) band = 1.5 * ldd(v + e) - 2.0 * ldd(v + e - Ms);
+    else band = 1.5 * ldd(v + e) - 2.0 * ldd(v + e - Ms) + 0.5 * ldd(v + e - 2 * Ms);
+    double out = band + tmp[e] + y;
+    if (rhs) out = rhs[e] - out;
+    w[e] = out;
+    sq += out * out;
+  }
+  if (sq_partial) {
+    double a[1] = {sq};
+    block_sum<double, 1>(a, red);
+    if (threadIdx.x == 0) sq_partial[(size_t)k * gridDim.x + blockIdx.x] = a[0];
+  }
+}
+
+// ---------------------------------------------------------------- Step (b), 2D COCG
+struct SysState {  // per system, FP64 scalars
+  double2 rho, a, beta;
+  double nb2, thr;
+  int active, iters, flag, pad_;
+};
+
+__device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return double2{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> to_c(double2 v) { return Cx<R>{(R)v.x, (R)v.y}; }
+
+// partial sums of a complex value per CTA: part[n * P + blockIdx.x]
+template <typename R>
+__device__ __forceinline__ void write_partial(R re, R im, double2* part, int n, int P, R* red) {
+  R a[2] = {re, im};
+  block_sum<R, 2>(a, red);
+  if (threadIdx.x == 0) part[(size_t)n * P + blockIdx.x] = double2{(double)a[0], (double)a[1]};
+}
+
+// r = b (taken from X), X = 0, partial |b|^2
+template <typename R>
+__global__ void __launch_bounds__(kElemThreads) c2d_init(Cx<R>* __restrict__ X, Cx<R>* __restrict__ Rr, size_t Ms,
+                                                         double2* __restrict__ part) {
+  __shared__ R red[64];
+  const int n = blockIdx.y;
+  R s = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Ms; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)n * Ms + e;
+    const Cx<R> b = X[o];
+    Rr[o] = b;
+    X[o] = Cx<R>{0, 0};
+    s += b.x * b.x + b.y * b.y;
+  }
+  write_partial<R>(s, 0, part, n, gridDim.x, red);
+}
+
+// out = scale * S_x in (rows, odd extension of length Lx = 2 (Mx+1)); MODE 1 also accumulates
+// the bilinear partial sum_e r_e out_e (rho of COCG).
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kLineThreads) c2d_rows_dst(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
+                                                             const Cx<R>* __restrict__ rr, int Mx, int My, int logLx,
+                                                             const Cx<R>* __restrict__ twx, R scale, int B,
+                                                             const SysState* __restrict__ st,
+                                                             double2* __restrict__ part) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  __shared__ R red[64];
+  const int n = blockIdx.y;
+  if (!st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Lx = 1 << logLx, bs = padded_size(Lx);
+  C* q = buf + B * bs;
+  load_quarter(q, twx, Lx / 4);
+  const size_t slab = (size_t)n * Mx * My;
+  const int j0 = blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < B * Lx; idx += blockDim.x) {
+    const int b = idx / Lx, l = idx - b * Lx, j = j0 + b;
+    C y{0, 0};
+    if (j < My) {
+      if (l >= 1 && l <= Mx) y = in[slab + (size_t)j * Mx + (l - 1)];
+      else if (l > Mx + 1) { const C t = in[slab + (size_t)j * Mx + (Lx - l - 1)]; y = C{-t.x, -t.y}; }
+    }
+    buf[b * bs + pad16(l)] = y;
+  }
+  fft_forward(buf, logLx, B, bs, q, logLx);
+  R sre = 0, sim = 0;
+  const R h = scale * (R)0.5;
+  for (int idx = threadIdx.x; idx < B * Mx; idx += blockDim.x) {
+    const int b = idx / Mx, i = idx - b * Mx, j = j0 + b;
+    if (j >= My) continue;
+    const C Y = buf[b * bs + pad16(bitrev(i + 1, logLx))];
+    const C z = C{-h * Y.y, h * Y.x};  // scale * (i/2) * Y
+    const size_t e = slab + (size_t)j * Mx + i;
+    out[e] = z;
+    if (MODE == 1) {
+      const C r = rr[e];
+      sre += r.x * z.x - r.y * z.y;
+      sim += r.x * z.y + r.y * z.x;
+    }
+  }
+  if (MODE == 1) write_partial<R>(sre, sim, part, n, gridDim.x, red);
+}
+
+// out = (2/(My+1)) S_y D S_y in along columns (B complex columns per CTA), D from lambda_n,
+// c_x sigma^x_i (natural order) and c_y sigma^y (fused order, 1e30 where the DST multiplier vanishes)
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) c2d_cols_dst_div(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
+                                                                 int Mx, int My, int logLy,
+                                                                 const Cx<R>* __restrict__ twy,
+                                                                 const R* __restrict__ sxn, const R* __restrict__ syf,
+                                                                 const double2* __restrict__ lambda, int B,
+                                                                 const SysState* __restrict__ st) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  const int n = blockIdx.y;
+  if (!st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Ly = 1 << logLy, bs = padded_size(Ly);
+  C* q = buf + B * bs;
+  load_quarter(q, twy, Ly / 4);
+  const size_t slab = (size_t)n * Mx * My;
+  const int i0 = blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < Ly * B; idx += blockDim.x) {
+    const int l = idx / B, b = idx - l * B, i = i0 + b;
+    C y{0, 0};
+    if (i < Mx) {
+      if (l >= 1 && l <= My) y = in[slab + (size_t)(l - 1) * Mx + i];
+      else if (l > My + 1) { const C t = in[slab + (size_t)(Ly - l - 1) * Mx + i]; y = C{-t.x, -t.y}; }
+    }
+    buf[b * bs + pad16(l)] = y;
+  }
+  const C lam = to_c<R>(lambda[n]);
+  const R invL = (R)1 / (R)Ly;
+  fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int b, int pf) {
+    const int i = i0 + b;
+    C d = lam;
+    d.x += (i < Mx ? sxn[i] : (R)0) + __ldg(&syf[pf]);
+    const R den = d.x * d.x + d.y * d.y;
+    return C{invL * d.x / den, -invL * d.y / den};
+  });
+  for (int idx = threadIdx.x; idx < My * B; idx += blockDim.x) {
+    const int j = idx / B, b = idx - j * B, i = i0 + b;
+    if (i < Mx) out[slab + (size_t)j * Mx + i] = buf[b * bs + pad16(j + 1)];
+  }
+}
+
+// p = z + beta p (written back), then tmp = c_x T_x p along rows
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) c2d_rows_conv(const Cx<R>* __restrict__ Z, Cx<R>* __restrict__ P,
+                                                              Cx<R>* __restrict__ Tm, int Mx, int My, int logLx,
+                                                              const Cx<R>* __restrict__ twx,
+                                                              const R* __restrict__ Exf, int B,
+                                                              const SysState* __restrict__ st) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  const int n = blockIdx.y;
+  if (!st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Lx = 1 << logLx, bs = padded_size(Lx);
+  C* q = buf + B * bs;
+  load_quarter(q, twx, Lx / 4);
+  const C beta = to_c<R>(st[n].beta);
+  const size_t slab = (size_t)n * Mx * My;
+  const int j0 = blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < B * Lx; idx += blockDim.x) {
+    const int b = idx / Lx, i = idx - b * Lx, j = j0 + b;
+    C pv{0, 0};
+    if (j < My && i < Mx) {
+      const size_t e = slab + (size_t)j * Mx + i;
+      pv = cadd(Z[e], cmul(beta, P[e]));
+      P[e] = pv;
+    }
+    buf[b * bs + pad16(i)] = pv;
+  }
+  fft_convolve_batched(buf, logLx, B, bs, q, logLx, [&](int, int pf) { return C{__ldg(&Exf[pf]), (R)0}; });
+  for (int idx = threadIdx.x; idx < B * Mx; idx += blockDim.x) {
+    const int b = idx / Mx, i = idx - b * Mx, j = j0 + b;
+    if (j < My) Tm[slab + (size_t)j * Mx + i] = buf[b * bs + pad16(i)];
+  }
+}
+
+// q = tmp + lambda p + c_y T_y p along columns; partial p^T q
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) c2d_cols_conv(const Cx<R>* __restrict__ P, const Cx<R>* __restrict__ Tm,
+                                                              Cx<R>* __restrict__ Q, int Mx, int My, int logLy,
+                                                              const Cx<R>* __restrict__ twy,
+                                                              const R* __restrict__ Eyf,
+                                                              const double2* __restrict__ lambda, int B,
+                                                              const SysState* __restrict__ st,
+                                                              double2* __restrict__ part) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  __shared__ R red[64];
+  const int n = blockIdx.y;
+  if (!st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Ly = 1 << logLy, bs = padded_size(Ly);
+  C* q = buf + B * bs;
+  load_quarter(q, twy, Ly / 4);
+  const size_t slab = (size_t)n * Mx * My;
+  const int i0 = blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < Ly * B; idx += blockDim.x) {
+    const int j = idx / B, b = idx - j * B, i = i0 + b;
+    buf[b * bs + pad16(j)] = (j < My && i < Mx) ? P[slab + (size_t)j * Mx + i] : C{0, 0};
+  }
+  fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int, int pf) { return C{__ldg(&Eyf[pf]), (R)0}; });
+  const C lam = to_c<R>(lambda[n]);
+  R sre = 0, sim = 0;
+  for (int idx = threadIdx.x; idx < My * B; idx += blockDim.x) {
+    const int j = idx / B, b = idx - j * B, i = i0 + b;
+    if (i >= Mx) continue;
+    const size_t e = slab + (size_t)j * Mx + i;
+    const C p = P[e];
+    const C qv = cadd(cadd(buf[b * bs + pad16(j)], Tm[e]), cmul(lam, p));
+    Q[e] = qv;
+    sre += p.x * qv.x - p.y * qv.y;
+    sim += p.x * qv.y + p.y * qv.x;
+  }
+  write_partial<R>(sre, sim, part, n, gridDim.x, red);
+}
+
+// x += a p, r -= a q, partial |r|^2
+template <typename R>
+__global__ void __launch_bounds__(kElemThreads) c2d_update(Cx<R>* __restrict__ X, Cx<R>* __restrict__ Rr,
+                                                           const Cx<R>* __restrict__ P, const Cx<R>* __restrict__ Q,
+                                                           size_t Ms, const SysState* __restrict__ st,
+                                                           double2* __restrict__ part) {
+  __shared__ R red[64];
+  const int n = blockIdx.y;
+  if (!st[n].active) return;
+  const Cx<R> a = to_c<R>(st[n].a);
+  R s = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Ms; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)n * Ms + e;
+    X[o] = cadd(X[o], cmul(a, P[o]));
+    const Cx<R> r = csub(Rr[o], cmul(a, Q[o]));
+    Rr[o] = r;
+    s += r.x * r.x + r.y * r.y;
+  }
+  write_partial<R>(s, 0, part, n, gridDim.x, red);
+}
+
+enum { S_INIT = 0, S_RHO0 = 1, S_ALPHA = 2, S_CHECK = 3, S_BETA = 4 };
+
+// one block per system: reduce the partials of the last kernel and update the scalars
+__global__ void c2d_scalars(int step, SysState* __restrict__ st, const double2* __restrict__ part, int P, double tol,
+                            int* __restrict__ active_count, int* __restrict__ iters, int* __restrict__ flags) {
+  __shared__ double sr[256], si[256];
+  const int n = blockIdx.x;
+  SysState& s = st[n];
+  if (step != S_INIT && !s.active) return;
+  double a = 0, b = 0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    a += part[(size_t)n * P + i].x;
+    b += part[(size_t)n * P + i].y;
+  }
+  sr[threadIdx.x] = a;
+  si[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sr[threadIdx.x] += sr[threadIdx.x + o];
+      si[threadIdx.x] += si[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x) return;
+  const double2 v{sr[0], si[0]};
+  switch (step) {
+    case S_INIT:
+      s.nb2 = v.x;
+      s.thr = tol * tol * v.x;
+      s.active = v.x > 0;
+      s.iters = 0;
+      s.flag = v.x > 0 ? 1 : 0;
+      s.beta = double2{0, 0};
+      break;
+    case S_RHO0:
+      s.rho = v;
+      s.beta = double2{0, 0};
+      break;
+    case S_ALPHA:
+      if (!(v.x * v.x + v.y * v.y > 0)) { s.flag = 2; s.active = 0; break; }
+      s.a = cdivd(s.rho, v);
+      break;
+    case S_CHECK:
+      s.iters++;
+      if (!(v.x == v.x) || v.x > 1e30 * s.nb2) { s.flag = 3; s.active = 0; break; }
+      if (v.x <= s.thr) { s.flag = 0; s.active = 0; break; }
+      atomicAdd(active_count, 1);
+      break;
+    case S_BETA:
+      if (!(s.rho.x * s.rho.x + s.rho.y * s.rho.y > 0)) { s.flag = 2; s.active = 0; break; }
+      s.beta = cdivd(v, s.rho);
+      s.rho = v;
+      break;
+  }
+  if (step == S_CHECK || step == S_ALPHA || step == S_BETA) {
+    iters[n] = s.iters;
+    flags[n] = s.flag;
+  }
+}
+
+template <typename R>
+size_t line_smem(int L, int B) {
+  return ((size_t)B * padded_size(L) + (size_t)(L / 4)) * sizeof(Cx<R>);
+}
+
+template <typename K>
+cudaError_t allow_smem(K kern, size_t smem) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+size_t mv2d_partials(int Mx, int Nt, int logLy) {
+  const int B = lines_per_cta(1 << logLy, (int)sizeof(double2));
+  return (size_t)Nt * ((Mx + 2 * B - 1) / (2 * B));
+}
+
+template <typename TIn>
+static cudaError_t mv2d(const TIn* v, const double* rhs, double* w, double* tmp, double* sq, int Mx, int My, int Nt,
+                        int logLx, int logLy, const double2* twx, const double2* twy, const double* Exf,
+                        const double* Eyf, cudaStream_t s) {
+  const int Bx = lines_per_cta(1 << logLx, (int)sizeof(double2));
+  const int By = lines_per_cta(1 << logLy, (int)sizeof(double2));
+  const size_t smx = line_smem<double>(1 << logLx, Bx), smy = line_smem<double>(1 << logLy, By);
+  cudaError_t e = allow_smem(mv2d_rows<TIn>, smx);
+  if (e != cudaSuccess) return e;
+  e = allow_smem(mv2d_cols<TIn>, smy);
+  if (e != cudaSuccess) return e;
+  const int npairs = (My + 1) / 2;
+  mv2d_rows<TIn><<<dim3((npairs + Bx - 1) / Bx, Nt), kLineThreads, smx, s>>>(v, tmp, Mx, My, logLx, twx, Exf, Bx);
+  mv2d_cols<TIn><<<dim3((Mx + 2 * By - 1) / (2 * By), Nt), kLineThreads, smy, s>>>(v, tmp, rhs, w, sq, Mx, My,
+                                                                                    logLy, twy, Eyf, By);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec2d_f64(const double* v, const double* rhs, double* w, double* tmp, double* sq, int Mx,
+                                int My, int Nt, int logLx, int logLy, const double2* twx, const double2* twy,
+                                const double* Exf, const double* Eyf, cudaStream_t s) {
+  return mv2d<double>(v, rhs, w, tmp, sq, Mx, My, Nt, logLx, logLy, twx, twy, Exf, Eyf, s);
+}
+cudaError_t launch_matvec2d_f64_fin(const float* v, const double* rhs, double* w, double* tmp, double* sq, int Mx,
+                                    int My, int Nt, int logLx, int logLy, const double2* twx, const double2* twy,
+                                    const double* Exf, const double* Eyf, cudaStream_t s) {
+  return mv2d<float>(v, rhs, w, tmp, sq, Mx, My, Nt, logLx, logLy, twx, twy, Exf, Eyf, s);
+}
+
+size_t cocg2d_state_bytes(int nsys) { return (size_t)nsys * sizeof(SysState); }
+
+int cocg2d_max_partials(int Mx, int My, int logLx, int logLy, int csize) {
+  const int Bx = lines_per_cta(1 << logLx, csize), By = lines_per_cta(1 << logLy, csize);
+  const size_t Ms = (size_t)Mx * My;
+  const int ne = (int)std::min<size_t>((Ms + kElemThreads - 1) / kElemThreads, 64);
+  return std::max(ne, std::max((My + Bx - 1) / Bx, (Mx + By - 1) / By));
+}
+
+template <typename R>
+static cudaError_t cocg2d(const Cocg2dArgs<R>& A, cudaStream_t s, int* inner_iters_out) {
+  using C = Cx<R>;
+  const int Mx = A.Mx, My = A.My, nsys = A.nsys;
+  const size_t Ms = (size_t)Mx * My;
+  const int Lx = 1 << A.logLx, Ly = 1 << A.logLy;
+  const int Bx = lines_per_cta(Lx, (int)sizeof(C)), By = lines_per_cta(Ly, (int)sizeof(C));
+  const size_t smx = line_smem<R>(Lx, Bx), smy = line_smem<R>(Ly, By);
+  SysState* st = reinterpret_cast<SysState*>(A.state);
+  cudaError_t e;
+  if ((e = allow_smem(c2d_rows_dst<R, 0>, smx)) != cudaSuccess) return e;
+  if ((e = allow_smem(c2d_rows_dst<R, 1>, smx)) != cudaSuccess) return e;
+  if ((e = allow_smem(c2d_rows_conv<R>, smx)) != cudaSuccess) return e;
+  if ((e = allow_smem(c2d_cols_dst_div<R>, smy)) != cudaSuccess) return e;
+  if ((e = allow_smem(c2d_cols_conv<R>, smy)) != cudaSuccess) return e;
+  const dim3 g_rows((My + Bx - 1) / Bx, nsys), g_cols((Mx + By - 1) / By, nsys);
+  const int ne = (int)std::min<size_t>((Ms + kElemThreads - 1) / kElemThreads, 64);
+  const dim3 g_elem(ne, nsys);
+  C *X = A.X, *Rr = A.Rr, *P = A.P, *Z = A.Z, *Q = A.Q, *Tm = A.Tm;
+  const R sx = (R)(2.0 / (Mx + 1));
+  auto precond = [&](bool with_rho) {
+    c2d_rows_dst<R, 0><<<g_rows, kLineThreads, smx, s>>>(Rr, Tm, nullptr, Mx, My, A.logLx, A.twx, (R)1, Bx, st,
+                                                         A.part);
+    c2d_cols_dst_div<R><<<g_cols, kLineThreads, smy, s>>>(Tm, Q, Mx, My, A.logLy, A.twy, A.sxn, A.syf, A.lambda, By,
+                                                          st);
+    if (with_rho)
+      c2d_rows_dst<R, 1><<<g_rows, kLineThreads, smx, s>>>(Q, Z, Rr, Mx, My, A.logLx, A.twx, sx, Bx, st, A.part);
+    else
+      c2d_rows_dst<R, 0><<<g_rows, kLineThreads, smx, s>>>(Q, Z, Rr, Mx, My, A.logLx, A.twx, sx, Bx, st, A.part);
+  };
+  c2d_init<R><<<g_elem, kElemThreads, 0, s>>>(X, Rr, Ms, A.part);
+  c2d_scalars<<<nsys, 256, 0, s>>>(S_INIT, st, A.part, ne, A.tol, A.active_count, A.iters, A.flags);
+  precond(true);
+  c2d_scalars<<<nsys, 256, 0, s>>>(S_RHO0, st, A.part, g_rows.x, A.tol, A.active_count, A.iters, A.flags);
+  int it = 0;
+  for (; it < A.maxit; ++it) {
+    c2d_rows_conv<R><<<g_rows, kLineThreads, smx, s>>>(Z, P, Tm, Mx, My, A.logLx, A.twx, A.Exf, Bx, st);
+    c2d_cols_conv<R><<<g_cols, kLineThreads, smy, s>>>(P, Tm, Q, Mx, My, A.logLy, A.twy, A.Eyf, A.lambda, By, st,
+                                                       A.part);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_ALPHA, st, A.part, g_cols.x, A.tol, A.active_count, A.iters, A.flags);
+    c2d_update<R><<<g_elem, kElemThreads, 0, s>>>(X, Rr, P, Q, Ms, st, A.part);
+    if ((e = cudaMemsetAsync(A.active_count, 0, sizeof(int), s)) != cudaSuccess) return e;
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_CHECK, st, A.part, ne, A.tol, A.active_count, A.iters, A.flags);
+    if ((e = cudaMemcpyAsync(A.host_count, A.active_count, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (*A.host_count == 0) { ++it; break; }
+    precond(true);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_BETA, st, A.part, g_rows.x, A.tol, A.active_count, A.iters, A.flags);
+  }
+  if (inner_iters_out) *inner_iters_out = it;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* launches) {
+  return cocg2d<float>(a, s, launches);
+}
+cudaError_t launch_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, int* launches) {
+  return cocg2d<double>(a, s, launches);
+}
+
+}  // namespace aao

@@ -36,6 +36,21 @@ def make_inputs(M, Nt, seed=0, recipe="sine8_normal"):
     return np.ascontiguousarray(u0), np.ascontiguousarray(f)
 
 
+def make_inputs_2d(Mx, My, Nt, seed=0):
+    """2D recipe "sine16_normal": u^0(x, y) = sum_{k,l=1}^{4} a_kl sin(k pi x) sin(l pi y), a_kl ~ N(0, 1)
+    (16 modes, drawn first, row-major in (k, l)); f i.i.d. N(0, 1) of shape (Nt, My, Mx), x fastest.
+    Returns (u0 [My, Mx], f [Nt, My, Mx])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = rng.standard_normal((4, 4))
+    x = mesh(Mx)
+    y = mesh(My)
+    sx = np.stack([np.sin((k + 1) * np.pi * x) for k in range(4)])
+    sy = np.stack([np.sin((l + 1) * np.pi * y) for l in range(4)])
+    u0 = np.einsum("kl,ly,kx->yx", a, sy, sx)
+    f = rng.standard_normal((Nt, My, Mx))
+    return np.ascontiguousarray(u0), np.ascontiguousarray(f)
+
+
 def random_vector(Nt, M, seed=0):
     """A generic space-time vector with N(0, 1) entries (for operator tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))

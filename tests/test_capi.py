@@ -64,7 +64,7 @@ def test_default_opts(lib):
 
 
 @pytest.mark.parametrize("field,value,word", [
-    ("M", 0, "M must"), ("Nt", 48, "Nt must"), ("Nt", 2, "Nt must"), ("dim", 2, "dim")])
+    ("M", 0, "M must"), ("Nt", 48, "Nt must"), ("Nt", 2, "Nt must"), ("dim", 3, "dim"), ("dim", 2, "My")])
 def test_plan_create_validates_problem_without_gpu(lib, field, value, word):
     prob = aao.AaoProblem(1, 63, 64, 1.0, 1.5, 1.0, 0.0)
     setattr(prob, field, value)

@@ -131,3 +131,16 @@ def test_cocg_solves_shifted_system(kind):
     np.testing.assert_allclose(x1, np.linalg.solve(A, b), rtol=1e-10, atol=1e-10)
     # the shifted system is complex symmetric, not Hermitian
     assert np.allclose(A, A.T) and not np.allclose(A, A.conj().T)
+
+
+def test_2d_three_steps_by_fast_diagonalisation_equal_dense():
+    Mx, My, Nt, tau, eps = 5, 3, 8, 1 / 8, 1 / 16
+    Kx = fcd.jacobian_1d(1.3, 1.0, Mx, 1 / (Mx + 1))
+    Ky = fcd.jacobian_1d(1.7, 0.5, My, 1 / (My + 1))
+    K = fcd.jacobian_2d(1.3, 1.7, 1.0, 0.5, Mx, My, 1 / (Mx + 1), 1 / (My + 1))
+    V = np.random.default_rng(2).standard_normal((Nt, My, Mx))
+    z = precond.precond_apply_2d(Kx, Ky, tau, eps, V)
+    want = np.linalg.solve(precond.P_eps_dense(K, tau, Nt, eps), V.ravel())
+    np.testing.assert_allclose(z.ravel(), want, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(precond.P_eps_matvec_2d(Kx, Ky, tau, eps, z).ravel(),
+                               precond.P_eps_dense(K, tau, Nt, eps) @ z.ravel(), rtol=1e-12, atol=1e-12)
