@@ -70,7 +70,8 @@ typedef struct {
   double T;             /* final time (> 0) */
   double alpha;         /* fractional order (x direction in 2D), 1 < alpha <= 2 */
   double kappa;         /* diffusion coefficient (x direction in 2D), > 0 */
-  double eps;           /* circulant parameter in (0,1]; <= 0 selects min(0.5, 0.5 tau) (Sec. 4) */
+  double eps;           /* circulant parameter in (0,1]; <= 0 selects min(0.5, 0.5 tau) (Sec. 4) for
+                           AAO_PREC_FP64 and max(min(0.5, 0.5 tau), 1/16) for AAO_PREC_MIXED */
   int64_t My;           /* 2D: interior points in y, h_y = 1/(My+1); ignored in 1D */
   double alpha_y;       /* 2D: fractional order in y */
   double kappa_y;       /* 2D: diffusion coefficient in y */

@@ -104,7 +104,8 @@ extern "C" aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, cons
     return noalloc_fail(AAO_EINVAL, "the tau preconditioner needs M+1 to be a power of two");
   aao::HostTables t;
   const char* emsg = nullptr;
-  if (!aao::build_tables(prob->M, prob->Nt, prob->T, prob->alpha, prob->kappa, prob->eps, t, &emsg))
+  const double eps = prob->eps > 0 ? prob->eps : aao::default_eps(prob->T / (double)prob->Nt, true);
+  if (!aao::build_tables(prob->M, prob->Nt, prob->T, prob->alpha, prob->kappa, eps, t, &emsg))
     return noalloc_fail(AAO_EINVAL, emsg);
   const int M = (int)t.M, Nt = (int)t.Nt, L = (int)t.L, nsys = Nt / 2 + 1;
 

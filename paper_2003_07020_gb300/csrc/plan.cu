@@ -396,13 +396,14 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   p->stream = (cudaStream_t)cuda_stream;
   p->mixed = opts->prec == AAO_PREC_MIXED;
   const char* emsg = nullptr;
-  if (!aao::build_tables(prob->M, prob->Nt, prob->T, prob->alpha, prob->kappa, prob->eps, p->ht, &emsg)) {
+  const double eps = prob->eps > 0 ? prob->eps : aao::default_eps(prob->T / (double)prob->Nt, p->mixed);
+  if (!aao::build_tables(prob->M, prob->Nt, prob->T, prob->alpha, prob->kappa, eps, p->ht, &emsg)) {
     delete p;
     return fail(nullptr, AAO_EINVAL, emsg);
   }
   p->dim = prob->dim;
   if (p->dim == 2 &&
-      !aao::build_tables(prob->My, prob->Nt, prob->T, prob->alpha_y, prob->kappa_y, prob->eps, p->hty, &emsg)) {
+      !aao::build_tables(prob->My, prob->Nt, prob->T, prob->alpha_y, prob->kappa_y, eps, p->hty, &emsg)) {
     delete p;
     return fail(nullptr, AAO_EINVAL, emsg);
   }

@@ -63,6 +63,11 @@ static int64_t bitrev64(int64_t k, int logn) {
   return r;
 }
 
+double default_eps(double tau, bool mixed) {
+  const double e = std::min(0.5, 0.5 * tau);
+  return mixed ? std::max(e, 1.0 / 16.0) : e;
+}
+
 int64_t fused_to_freq(int64_t p, int logN) {
   const int r = logN < 4 ? logN : 4;
   const int64_t R = int64_t(1) << r;

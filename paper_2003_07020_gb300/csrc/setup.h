@@ -50,6 +50,12 @@ struct HostTables {
 // r = min(4, logN).  Returns the natural frequency for fused index p.
 int64_t fused_to_freq(int64_t p, int logN);
 
+// Default circulant parameter when the caller passes eps <= 0: the paper's
+// min(0.5, 0.5 tau) (Sec. 4) for the FP64 path; for the mixed path at least
+// 1/16, which bounds cond(V_eps) = 1/eps, the factor by which Step (c)
+// amplifies the FP32 errors of the shifted solves.
+double default_eps(double tau, bool mixed);
+
 // Fills every table for the 1D problem.  Returns false with a message on bad input.
 bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, double eps,
                   HostTables& out, const char** err);

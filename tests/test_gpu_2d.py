@@ -25,6 +25,11 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
+def mixed_eps(tau):
+    """The library's default circulant parameter for the mixed path: max(min(0.5, 0.5 tau), 1/16)."""
+    return max(min(0.5, 0.5 * tau), 1.0 / 16)
+
+
 def rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
@@ -66,7 +71,7 @@ def test_precond_2d_fp64(Mx, My, Nt, ax, ay):
 def test_precond_2d_mixed(Mx, My, Nt, ax, ay):
     v = np.random.default_rng(4).standard_normal((Nt, My, Mx))
     tau = 1.0 / Nt
-    eps = oprec.default_eps(tau)
+    eps = mixed_eps(tau)
     with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=aao.AAO_PREC_MIXED) as plan:
         z = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
         plan.bc_precond_apply(cu(v), z)

@@ -39,6 +39,11 @@ def jac(M, alpha, kappa=1.0):
     return fcd.jacobian_1d(alpha, kappa, M, 1.0 / (M + 1))
 
 
+def mixed_eps(tau):
+    """The library's default circulant parameter for the mixed path: max(min(0.5, 0.5 tau), 1/16)."""
+    return max(min(0.5, 0.5 * tau), 1.0 / 16)
+
+
 def rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
@@ -104,7 +109,7 @@ def test_precond_mixed_residual(M, Nt, alpha, inner):
         pytest.skip("tau preconditioner needs M+1 a power of two")
     v = workloads.random_vector(Nt, M, seed=4)
     tau = 1.0 / Nt
-    eps = oprec.default_eps(tau)
+    eps = mixed_eps(tau)
     with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED, inner=inner) as plan:
         z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
         plan.bc_precond_apply(cu(v), z)
@@ -139,7 +144,7 @@ def test_precond_full_size_mixed_residual():
     K = jac(M, alpha)
     # residual of the eps-circulant equation; the bound follows the z-error bound above
     # times ||P_eps|| ||z|| / ||v||, evaluated with ||P_eps|| <= 4 + c 2^alpha
-    eps = oprec.default_eps(tau)
+    eps = mixed_eps(tau)
     Z = host(z)
     res = rel(oprec.P_eps_matvec(K, tau, eps, Z), v)
     c = tau / (1.0 / (M + 1)) ** alpha
