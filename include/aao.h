@@ -173,6 +173,20 @@ aao_status aao_gmres_solve(aao_plan* plan, const double* F_dev, double* U_dev, a
 aao_status aao_gmres_solve_host(aao_plan* plan, const double* F_host, double* U_host, aao_info* info);
 
 /*
+ * Solves n independent problems (different M, Nt, alpha, kappa, precision)
+ * concurrently on the current device: each plan runs aao_gmres_solve on its
+ * own non-blocking stream (created for the call; the plan's stream is
+ * restored afterwards) from a pool of max_workers host threads (<= 0: 32),
+ * largest problems first, so that the kernels of small problems overlap and
+ * fill the GPU (the batched workload of many instances).  F[i], U[i]: device
+ * vectors of plans[i]'s shape; U[i] is the initial guess on entry.  infos
+ * (may be NULL) receives n results.  Returns AAO_OK if every solve did, else
+ * the first failing status (the other solves still complete).
+ */
+aao_status aao_solve_batched(int n, aao_plan* const* plans, const double* const* F, double* const* U,
+                             aao_info* infos, int max_workers);
+
+/*
  * Tracing.  When profiling is on, every kernel the plan launches is
  * bracketed by CUDA events recorded on the plan's stream, and the elapsed
  * times are accumulated per stage.  Stages: 0 matvec (Sec. 3.2), 1 Step (a)

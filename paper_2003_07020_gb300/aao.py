@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4
 EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan_destroy",
             "aao_plan_workspace_bytes", "aao_build_rhs", "aao_matvec", "aao_bc_precond_apply",
             "aao_gmres_solve", "aao_gmres_solve_host", "aao_plan_set_profiling", "aao_plan_get_profile",
-            "aao_bc_precond_apply_noalloc", "aao_last_error")
+            "aao_bc_precond_apply_noalloc", "aao_solve_batched", "aao_last_error")
 STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector")
 
 
@@ -82,6 +82,7 @@ def load():
     lib.aao_gmres_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
     lib.aao_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.aao_plan_get_profile.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.aao_solve_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int]
     lib.aao_bc_precond_apply_noalloc.argtypes = [ctypes.POINTER(AaoProblem), ctypes.POINTER(AaoOpts), vp, vp, vp]
     lib.aao_last_error.argtypes = [vp]
     lib.aao_last_error.restype = ctypes.c_char_p
@@ -219,6 +220,22 @@ class Plan:
         if st != AAO_OK and (raise_on_noconv or st != AAO_ENOCONV):
             _check(st, self.handle)
         return info.as_dict()
+
+
+def solve_batched(plans, Fs, Us, max_workers=0, raise_on_error=True):
+    """aao_solve_batched: all problems concurrently; returns the list of info dicts."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    Fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
+    Up = (ctypes.c_void_p * n)(*[U.data_ptr() for U in Us])
+    for p, F, U in zip(plans, Fs, Us):
+        p._vec(F, "F")
+        p._vec(U, "U")
+    infos = (AaoInfo * n)()
+    st = load().aao_solve_batched(n, P, Fp, Up, infos, int(max_workers))
+    if st != AAO_OK and raise_on_error:
+        _check(st, None)
+    return [i.as_dict() for i in infos]
 
 
 # Module-level aliases with the C names, for callers that prefer them.

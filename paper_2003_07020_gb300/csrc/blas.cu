@@ -2,10 +2,33 @@
 // with re-orthogonalisation (two passes) fused into three sweeps, the
 // solution update U += Z y, the right-hand side of Eq. 12, and deterministic
 // two-stage reductions (per-block partial sums, then a fixed-order sum).
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace aao {
+
+cudaError_t allow_max_dynamic_smem_impl(const void* kern) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({kern, dev})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({kern, dev});
+  return e;
+}
 
 constexpr int kBlasThreads = 256;
 constexpr int kBlasBlocks = 152 * 4;

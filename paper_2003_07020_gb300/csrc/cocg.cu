@@ -382,8 +382,7 @@ static cudaError_t launch_k(typename cplx_t<R>::type* xb, typename cplx_t<R>::ty
                             int nsys, const typename Tabs<R>::type& tb, R tol, int maxit, int* iters, int* flags,
                             int grid, cudaStream_t s) {
   const size_t smem = (GBUF ? 0 : cocg_smem<R>(logL)) + cocg_table_bytes<R>(logL);
-  cudaError_t e = cudaFuncSetAttribute(cocg_kernel<R, KIND, GBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_dynamic_smem(cocg_kernel<R, KIND, GBUF>);
   if (e != cudaSuccess) return e;
   cocg_kernel<R, KIND, GBUF><<<grid, 512, smem, s>>>(xb, rws, pws, gbuf, M, logL, nsys, tb, tol, maxit, iters,
                                                      flags);
@@ -397,7 +396,7 @@ cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int log
     const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
                         (size_t)pass_table_size(logL) * sizeof(float2);
     auto kern = inner == 0 ? cocg_reg_kernel<0> : cocg_reg_kernel<1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
     kern<<<grid, kRegThreads, smem, s>>>(xb, M, logL, nsys, tb, tol, maxit, iters, flags);
     return cudaGetLastError();

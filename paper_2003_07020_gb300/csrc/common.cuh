@@ -480,4 +480,15 @@ __device__ __forceinline__ void block_sum(R (&v)[NV], R* scratch) {
   __syncthreads();
 }
 
+// Lets `kern` use as much dynamic shared memory as the device allows.  The
+// attribute is global per kernel function, so every launcher sets the same
+// (maximal) value: a launch from one host thread can never see a smaller limit
+// set by a concurrent launch of another problem size.
+// Done once per (kernel, device); later calls only look the pair up.
+cudaError_t allow_max_dynamic_smem_impl(const void* kern);
+template <typename K>
+inline cudaError_t allow_max_dynamic_smem(K kern) {
+  return allow_max_dynamic_smem_impl(reinterpret_cast<const void*>(kern));
+}
+
 }  // namespace aao

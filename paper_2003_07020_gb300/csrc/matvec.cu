@@ -113,8 +113,7 @@ template <typename TIn>
 static cudaError_t launch_mv(const TIn* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                              int logL, const double* Ehalf, const double2* twL, cudaStream_t s) {
   const size_t smem = matvec_smem_bytes(logL);
-  cudaError_t e = cudaFuncSetAttribute(matvec_f64_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_dynamic_smem(matvec_f64_kernel<TIn>);
   if (e != cudaSuccess) return e;
   matvec_f64_kernel<TIn><<<Nt, 256, smem, s>>>(v, rhs, w, sq_partial, M, logL - 1, Ehalf, twL);
   return cudaGetLastError();

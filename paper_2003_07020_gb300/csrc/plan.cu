@@ -691,3 +691,61 @@ aao_status aao_gmres_solve_host(aao_plan* p, const double* F_host, double* U_hos
 }
 
 }  // extern "C"
+
+// ---- many independent problems at once --------------------------------------------------
+#include <atomic>
+#include <thread>
+
+extern "C" aao_status aao_solve_batched(int n, aao_plan* const* plans, const double* const* F, double* const* U,
+                                        aao_info* infos, int max_workers) {
+  if (n < 0 || (n > 0 && (!plans || !F || !U))) return fail(nullptr, AAO_EINVAL, "bad batched arguments");
+  if (n == 0) return AAO_OK;
+  for (int i = 0; i < n; ++i)
+    if (!plans[i] || !F[i] || !U[i]) return fail(nullptr, AAO_EINVAL, "null plan or vector in the batch");
+  // one non-blocking stream per instance so that the instances' kernels overlap on the GPU
+  std::vector<cudaStream_t> saved(n), own(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    saved[i] = plans[i]->stream;
+    if (cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaStreamDestroy(own[k]);
+      return fail(nullptr, AAO_ECUDA, "cudaStreamCreateWithFlags failed");
+    }
+    // the caller's pending work on the plan's own stream comes first
+    cudaStreamSynchronize(saved[i]);
+    plans[i]->stream = own[i];
+  }
+  // largest instances first
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return plans[a]->n > plans[b]->n; });
+  std::vector<aao_status> st(n, AAO_OK);
+  std::vector<aao_info> inf(n);
+  std::atomic<int> next(0);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      const int i = order[k];
+      st[i] = aao_gmres_solve(plans[i], F[i], U[i], &inf[i]);
+    }
+  };
+  const int nw = std::max(1, std::min(n, max_workers > 0 ? max_workers : 32));
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  aao_status result = AAO_OK;
+  for (int i = 0; i < n; ++i) {
+    cudaStreamSynchronize(own[i]);
+    plans[i]->stream = saved[i];
+    cudaStreamDestroy(own[i]);
+    if (infos) infos[i] = inf[i];
+    if (st[i] != AAO_OK && result == AAO_OK) {
+      result = st[i];
+      g_create_error = "instance " + std::to_string(i) + ": " + plans[i]->err;
+    }
+  }
+  return result;
+}

@@ -103,7 +103,7 @@ template <typename R>
 static cudaError_t fwd(const double* v, typename cplx_t<R>::type* out, int M, int Nt, const R* scale,
                        const typename cplx_t<R>::type* tw, cudaStream_t s) {
   const size_t smem = tdft_smem<R>(Nt);
-  cudaError_t e = cudaFuncSetAttribute(tdft_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem(tdft_fwd_kernel<R>);
   if (e != cudaSuccess) return e;
   tdft_fwd_kernel<R><<<(M + TW - 1) / TW, 256, smem, s>>>(v, out, M, ilog2i(Nt), scale, tw);
   return cudaGetLastError();
@@ -113,8 +113,7 @@ template <typename R, typename TOut>
 static cudaError_t inv(const typename cplx_t<R>::type* in, TOut* z, int M, int Nt, const R* scale_inv,
                        const typename cplx_t<R>::type* tw, cudaStream_t s) {
   const size_t smem = tdft_smem<R>(Nt);
-  cudaError_t e = cudaFuncSetAttribute(tdft_inv_kernel<R, TOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_dynamic_smem(tdft_inv_kernel<R, TOut>);
   if (e != cudaSuccess) return e;
   tdft_inv_kernel<R, TOut><<<(M + TW - 1) / TW, 256, smem, s>>>(in, z, M, ilog2i(Nt), scale_inv, tw);
   return cudaGetLastError();

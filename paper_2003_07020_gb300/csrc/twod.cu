@@ -410,7 +410,7 @@ size_t line_smem(int L, int B) {
 
 template <typename K>
 cudaError_t allow_smem(K kern, size_t smem) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return allow_max_dynamic_smem(kern);
 }
 
 }  // namespace

@@ -51,6 +51,19 @@ def make_inputs_2d(Mx, My, Nt, seed=0):
     return np.ascontiguousarray(u0), np.ascontiguousarray(f)
 
 
+def batched_instances(n=64, seed=0, Ms=(511, 1023, 2047, 4095), Nts=(128, 256, 512, 1024)):
+    """Parameters of n independent 1D instances (the batched workload): M and Nt uniform over the given
+    sets, alpha ~ U(1.1, 1.9), kappa ~ U(0.5, 2), inputs "sine8_normal" with seed 1000 + i.
+    Returns a list of dicts (M, Nt, alpha, kappa, seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M = rng.choice(np.asarray(Ms), n)
+    Nt = rng.choice(np.asarray(Nts), n)
+    alpha = rng.uniform(1.1, 1.9, n)
+    kappa = rng.uniform(0.5, 2.0, n)
+    return [dict(M=int(M[i]), Nt=int(Nt[i]), alpha=float(alpha[i]), kappa=float(kappa[i]), seed=1000 + i)
+            for i in range(n)]
+
+
 def random_vector(Nt, M, seed=0):
     """A generic space-time vector with N(0, 1) entries (for operator tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
