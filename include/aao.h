@@ -97,6 +97,8 @@ typedef struct {
   double true_rel_res;  /* final ||F - calA U||_2 / ||F||_2 computed in FP64 */
   int status_detail;    /* AAO_OK, or the inner failure code that was seen */
   int64_t inner_iters_sum; /* COCG iterations summed over all systems and applications */
+  int64_t warm_accepted;   /* shifted systems that started from the learned initial guess
+                              (aao_plan_set_warm_start), summed over applications */
 } aao_info;
 
 typedef struct aao_plan aao_plan;
@@ -191,11 +193,11 @@ aao_status aao_solve_batched(int n, aao_plan* const* plans, const double* const*
  * bracketed by CUDA events recorded on the plan's stream, and the elapsed
  * times are accumulated per stage.  Stages: 0 matvec (Sec. 3.2), 1 Step (a)
  * time DFT, 2 Step (b) shifted solves, 3 Step (c) inverse time DFT,
- * 4 Gram-Schmidt and other vector kernels.  aao_plan_get_profile
+ * 4 Gram-Schmidt and other vector kernels, 5 learned warm-start inference.  aao_plan_get_profile
  * synchronises the stream, fills ms[i] (milliseconds) and launches[i] for
  * i < AAO_NUM_STAGES, and resets the counters when reset != 0.
  */
-#define AAO_NUM_STAGES 5
+#define AAO_NUM_STAGES 6
 aao_status aao_plan_set_profiling(aao_plan* plan, int on);
 aao_status aao_plan_get_profile(aao_plan* plan, double* ms, int64_t* launches, int reset);
 
@@ -216,6 +218,93 @@ aao_status aao_plan_get_profile(aao_plan* plan, double* ms, int64_t* launches, i
  */
 aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, const aao_opts* opts,
                                         const double* v_dev, double* z_dev, void* cuda_stream);
+
+/*
+ * Learned warm start for Step (b).  The paper solves every shifted system
+ * (lambda_n I - tau K) x = zhat_n from x0 = 0; it has no learned component.
+ * An aao_fno is a Fourier neural operator that predicts x0 from
+ * (zhat_n, lambda_n, alpha) and is trained on the GPU on (zhat_n, x_n) pairs
+ * that the solver itself records (aao_plan_record_pairs).
+ *
+ * Architecture, per grid point i = 0..M-1 of one system with right-hand
+ * side b (channels last):
+ *   features [Re bh_i, Im bh_i, Re lambda, Im lambda, alpha, (i+1)/(M+1)],
+ *   bh = b / ||b||;  lift 6 -> 32;  4 Fourier layers, each: DFT of every
+ *   channel truncated to modes k < 16, a complex 32 x 32 matrix per mode,
+ *   inverse (real part, modes k >= 1 counted twice, divided by M), plus a
+ *   point-wise 32 x 32 matrix and bias, GELU (erf form) after all but the
+ *   last layer;  projection 32 -> 2 giving y;  x0 = ||b|| (y_0 + i y_1).
+ * Parameters: one flat float array of aao_fno_num_params() values in the
+ * order lift W (32 x 6, row-major), lift bias (32), then per layer the
+ * spectral weights (16 x 32 x 32 complex as [mode][out][in][re, im]), the
+ * point-wise W (32 x 32, [out][in]), the bias (32), then projection W
+ * (2 x 32) and bias (2).  Inference and training read the weights as BF16
+ * and accumulate in FP32; training keeps FP32 master weights and Adam
+ * moments.  The loss of one sample with target t = x / ||b|| is
+ * sum |y - t|^2 / sum |t|^2, averaged over the batch.
+ *
+ * Buffers: b, x: complex float [B][M] (re, im interleaved) on the device;
+ * lambda: complex double [B]; alpha: float [B]; all device pointers.
+ * cuda_stream as in aao_plan_create.  Calls on one model must not overlap
+ * (its activations are reused).  Errors: see aao_last_error(NULL).
+ */
+typedef struct aao_fno aao_fno;
+
+int64_t aao_fno_num_params(void);
+
+/* Model for grid size M (32 <= M <= 8191) and batches of up to max_batch
+ * systems; weights drawn from a seeded scaled Gaussian (fan-in), biases 0. */
+aao_status aao_fno_create(int64_t M, int max_batch, uint64_t seed, aao_fno** out);
+aao_status aao_fno_destroy(aao_fno* fno);
+
+/* Host float[aao_fno_num_params()] in the flat order above.  set_params
+ * also resets the optimiser.  get_params returns the FP32 master weights,
+ * or, if bf16_rounded != 0, the BF16 values the kernels read. */
+aao_status aao_fno_set_params(aao_fno* fno, const float* params_host);
+aao_status aao_fno_get_params(aao_fno* fno, float* params_host, int bf16_rounded);
+
+/* Save / load the FP32 weights: one line of JSON (format, version, sizes,
+ * number of parameters, Adam step count) followed by the parameters as
+ * little-endian float32.  load accepts a file written for any M. */
+aao_status aao_fno_save(aao_fno* fno, const char* path);
+aao_status aao_fno_load(aao_fno* fno, const char* path);
+
+/* x0 = prediction for B systems (1 <= B <= max_batch). */
+aao_status aao_fno_predict(aao_fno* fno, int B, const void* b_dev, const void* lambda_dev,
+                           const float* alpha_dev, void* x0_dev, void* cuda_stream);
+
+/* Mean loss over the batch and, if grad_host != NULL, its gradient in the
+ * flat order (host float[aao_fno_num_params()]); synchronises the stream. */
+aao_status aao_fno_loss_grad(aao_fno* fno, int B, const void* b_dev, const void* lambda_dev,
+                             const float* alpha_dev, const void* x_dev, double* loss, float* grad_host,
+                             void* cuda_stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * batch; *loss (may be NULL) receives the batch loss before the step. */
+aao_status aao_fno_train_step(aao_fno* fno, int B, const void* b_dev, const void* lambda_dev,
+                              const float* alpha_dev, const void* x_dev, float lr, double* loss,
+                              void* cuda_stream);
+
+/*
+ * Attaches fno (not owned; NULL detaches) to a 1D AAO_PREC_MIXED plan with
+ * M <= 8191 equal to the model's M and Nt/2 + 1 <= its max_batch.  Every
+ * Step (b) then predicts x0 for all shifted systems and COCG starts system n
+ * from its prediction only if the FP32 residual ||zhat_n - A_n x0|| is
+ * below ||zhat_n||, else from 0; the stopping test stays relative to
+ * ||zhat_n||.  The model must not be used by another call meanwhile.
+ */
+aao_status aao_plan_set_warm_start(aao_plan* plan, aao_fno* fno);
+
+/*
+ * Records training pairs from every later Step (b) of a 1D AAO_PREC_MIXED
+ * plan: system n's right-hand side zhat_n (b_dev), its COCG solution
+ * (x_dev, both complex float [capacity][M]) and lambda_n (lambda_dev,
+ * complex double [capacity]) are appended until capacity pairs are stored.
+ * capacity 0 (or NULL buffers) stops recording; a new call restarts the
+ * count.  aao_plan_recorded_pairs returns the number stored so far.
+ */
+aao_status aao_plan_record_pairs(aao_plan* plan, int64_t capacity, void* b_dev, void* x_dev, void* lambda_dev);
+aao_status aao_plan_recorded_pairs(const aao_plan* plan, int64_t* count);
 
 /* Message for the last failing call on plan (or on plan creation, or on a
  * call without a plan, if NULL). */

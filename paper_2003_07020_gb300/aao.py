@@ -24,8 +24,12 @@ STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4
 EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan_destroy",
             "aao_plan_workspace_bytes", "aao_build_rhs", "aao_matvec", "aao_bc_precond_apply",
             "aao_gmres_solve", "aao_gmres_solve_host", "aao_plan_set_profiling", "aao_plan_get_profile",
-            "aao_bc_precond_apply_noalloc", "aao_solve_batched", "aao_last_error")
-STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector")
+            "aao_bc_precond_apply_noalloc", "aao_solve_batched", "aao_last_error",
+            "aao_fno_num_params", "aao_fno_create", "aao_fno_destroy", "aao_fno_set_params",
+            "aao_fno_get_params", "aao_fno_save", "aao_fno_load", "aao_fno_predict", "aao_fno_loss_grad",
+            "aao_fno_train_step", "aao_plan_set_warm_start", "aao_plan_record_pairs",
+            "aao_plan_recorded_pairs")
+STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector", "fno")
 
 
 class AaoProblem(ctypes.Structure):
@@ -43,7 +47,7 @@ class AaoOpts(ctypes.Structure):
 class AaoInfo(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("cycles", ctypes.c_int), ("inner_iters_max", ctypes.c_int),
                 ("matvecs", ctypes.c_int), ("true_rel_res", ctypes.c_double), ("status_detail", ctypes.c_int),
-                ("inner_iters_sum", ctypes.c_int64)]
+                ("inner_iters_sum", ctypes.c_int64), ("warm_accepted", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,8 +90,22 @@ def load():
     lib.aao_bc_precond_apply_noalloc.argtypes = [ctypes.POINTER(AaoProblem), ctypes.POINTER(AaoOpts), vp, vp, vp]
     lib.aao_last_error.argtypes = [vp]
     lib.aao_last_error.restype = ctypes.c_char_p
+    lib.aao_fno_num_params.argtypes = []
+    lib.aao_fno_num_params.restype = i64
+    lib.aao_fno_create.argtypes = [i64, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(vp)]
+    lib.aao_fno_destroy.argtypes = [vp]
+    lib.aao_fno_set_params.argtypes = [vp, vp]
+    lib.aao_fno_get_params.argtypes = [vp, vp, ctypes.c_int]
+    lib.aao_fno_save.argtypes = [vp, ctypes.c_char_p]
+    lib.aao_fno_load.argtypes = [vp, ctypes.c_char_p]
+    lib.aao_fno_predict.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.aao_fno_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(dbl), vp, vp]
+    lib.aao_fno_train_step.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_float, ctypes.POINTER(dbl), vp]
+    lib.aao_plan_set_warm_start.argtypes = [vp, vp]
+    lib.aao_plan_record_pairs.argtypes = [vp, i64, vp, vp, vp]
+    lib.aao_plan_recorded_pairs.argtypes = [vp, ctypes.POINTER(i64)]
     for name in EXPORTED:
-        if name not in ("aao_default_opts", "aao_plan_workspace_bytes", "aao_last_error"):
+        if name not in ("aao_default_opts", "aao_plan_workspace_bytes", "aao_last_error", "aao_fno_num_params"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -220,6 +238,117 @@ class Plan:
         if st != AAO_OK and (raise_on_noconv or st != AAO_ENOCONV):
             _check(st, self.handle)
         return info.as_dict()
+
+    def set_warm_start(self, fno):
+        """Attach a learned warm-start model (an :class:`Fno`), or detach it with None."""
+        _check(load().aao_plan_set_warm_start(self.handle, None if fno is None else fno.handle), self.handle)
+        self._fno = fno  # keep the model alive while attached
+
+    def record_pairs(self, b, x, lam):
+        """Record (rhs, solution, lambda) of every later shifted solve into b, x (complex64 CUDA tensors
+        [capacity, M]) and lam (complex128 [capacity]); None stops recording."""
+        lib = load()
+        if b is None:
+            _check(lib.aao_plan_record_pairs(self.handle, 0, None, None, None), self.handle)
+            self._rec = None
+            return
+        cap = b.shape[0]
+        for t, dt, shape in ((b, "complex64", (cap, self.M)), (x, "complex64", (cap, self.M)),
+                             (lam, "complex128", (cap,))):
+            if not (t.is_cuda and t.is_contiguous() and str(t.dtype).endswith(dt) and tuple(t.shape) == shape):
+                raise ValueError("record buffers: b, x complex64 [capacity, M], lam complex128 [capacity]")
+        _check(lib.aao_plan_record_pairs(self.handle, cap, ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(lam.data_ptr())),
+               self.handle)
+        self._rec = (b, x, lam)
+
+    def recorded_pairs(self):
+        n = ctypes.c_int64()
+        _check(load().aao_plan_recorded_pairs(self.handle, ctypes.byref(n)), self.handle)
+        return n.value
+
+
+def fno_num_params():
+    return load().aao_fno_num_params()
+
+
+class Fno:
+    """An ``aao_fno``: the learned warm start (Fourier neural operator) for grid size M."""
+
+    def __init__(self, M, max_batch, seed=0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.aao_fno_create(int(M), int(max_batch), int(seed), ctypes.byref(h)))
+        self.handle, self.M, self.max_batch = h, int(M), int(max_batch)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().aao_fno_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != fno_num_params():
+            raise ValueError("need %d parameters" % fno_num_params())
+        _check(load().aao_fno_set_params(self.handle, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def get_params(self, bf16_rounded=False):
+        a = np.empty(fno_num_params(), dtype=np.float32)
+        _check(load().aao_fno_get_params(self.handle, a.ctypes.data_as(ctypes.c_void_p), int(bool(bf16_rounded))))
+        return a
+
+    def save(self, path):
+        _check(load().aao_fno_save(self.handle, os.fsencode(path)))
+
+    def load(self, path):
+        _check(load().aao_fno_load(self.handle, os.fsencode(path)))
+
+    def _args(self, b, lam, alpha):
+        B = b.shape[0]
+        if not (b.is_cuda and b.is_contiguous() and str(b.dtype).endswith("complex64") and tuple(b.shape) == (B, self.M)):
+            raise ValueError("b must be a contiguous complex64 CUDA tensor [B, M]")
+        if not (lam.is_cuda and lam.is_contiguous() and str(lam.dtype).endswith("complex128") and lam.numel() == B):
+            raise ValueError("lam must be a contiguous complex128 CUDA tensor [B]")
+        if not (alpha.is_cuda and alpha.is_contiguous() and str(alpha.dtype).endswith("float32") and alpha.numel() == B):
+            raise ValueError("alpha must be a contiguous float32 CUDA tensor [B]")
+        return B, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(alpha.data_ptr())
+
+    def predict(self, b, lam, alpha, x0, stream=None):
+        B, pb, pl, pa = self._args(b, lam, alpha)
+        if not (x0.is_cuda and x0.is_contiguous() and x0.shape == b.shape and x0.dtype == b.dtype):
+            raise ValueError("x0 must be like b")
+        _check(load().aao_fno_predict(self.handle, B, pb, pl, pa, ctypes.c_void_p(x0.data_ptr()), _stream_ptr(stream)))
+
+    def loss_grad(self, b, lam, alpha, x, want_grad=True, stream=None):
+        B, pb, pl, pa = self._args(b, lam, alpha)
+        if not (x.is_cuda and x.is_contiguous() and x.shape == b.shape and x.dtype == b.dtype):
+            raise ValueError("x must be like b")
+        loss = ctypes.c_double()
+        g = np.empty(fno_num_params(), dtype=np.float32) if want_grad else None
+        _check(load().aao_fno_loss_grad(self.handle, B, pb, pl, pa, ctypes.c_void_p(x.data_ptr()), ctypes.byref(loss),
+                                        None if g is None else g.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+        return loss.value, g
+
+    def train_step(self, b, lam, alpha, x, lr=1e-3, stream=None):
+        B, pb, pl, pa = self._args(b, lam, alpha)
+        if not (x.is_cuda and x.is_contiguous() and x.shape == b.shape and x.dtype == b.dtype):
+            raise ValueError("x must be like b")
+        loss = ctypes.c_double()
+        _check(load().aao_fno_train_step(self.handle, B, pb, pl, pa, ctypes.c_void_p(x.data_ptr()), float(lr),
+                                         ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value
 
 
 def solve_batched(plans, Fs, Us, max_workers=0, raise_on_error=True):

@@ -244,10 +244,10 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
   }
 }
 
-template <int KIND>
+template <int KIND, bool WARM>
 __global__ void __launch_bounds__(kRegThreads, 1)
-    cocg_reg_kernel(float2* __restrict__ xb, int M, int logL, int nsys, CocgTables32 tb, float tol, int maxit,
-                    int* __restrict__ iters, int* __restrict__ flags) {
+    cocg_reg_kernel(float2* __restrict__ xb, const float2* __restrict__ x0b, int M, int logL, int nsys,
+                    CocgTables32 tb, float tol, int maxit, int* __restrict__ iters, int* __restrict__ flags) {
   extern __shared__ unsigned char smraw[];
   __shared__ float red[4 * 32];
   float2* buf = reinterpret_cast<float2*>(smraw);
@@ -281,6 +281,47 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       continue;
     }
     const float thr = tol * tol * nb2[0];
+    int accepted = 0;
+    if constexpr (WARM) {
+      // warm start: r0 = b - (lambda I + c T) x0, kept only if ||r0|| < ||b||
+      const float2* x0 = x0b + (size_t)n * M;
+      float2 w[kRegElems];
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        w[j] = (i < M) ? x0[i] : float2{0, 0};
+        if (i < L) buf[pad16(i)] = w[j];
+      }
+      for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+      fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
+      float r02[1] = {0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + kRegThreads * j;
+        if (i < M) {
+          const float2 rj = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
+          r02[0] += rj.x * rj.x + rj.y * rj.y;
+        }
+      }
+      block_sum<float, 1>(r02, red);
+      if (r02[0] < nb2[0]) {  // uniform across the block
+        accepted = 1;
+#pragma unroll
+        for (int j = 0; j < kRegElems; ++j) {
+          const int i = t + kRegThreads * j;
+          if (i < M) {
+            r[j] = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
+            x[i] = w[j];
+          }
+        }
+        if (r02[0] <= thr) {
+          if (t == 0) { iters[n] = 0; flags[n] = 4; }
+          __syncthreads();
+          continue;
+        }
+      }
+      __syncthreads();
+    }
     // z = P^{-1} r, p = z, rho = r^T z
     precond_reg<KIND>(buf, r, M, logL, lam, tb, q, pt);
     float rho2[2] = {0, 0};
@@ -359,7 +400,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       }
       __syncthreads();
     }
-    if (t == 0) { iters[n] = it; flags[n] = flag; }
+    if (t == 0) { iters[n] = it; flags[n] = flag | (accepted << 2); }
     __syncthreads();
   }
 }
@@ -391,14 +432,16 @@ static cudaError_t launch_k(typename cplx_t<R>::type* xb, typename cplx_t<R>::ty
 
 cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys, int inner,
                             const CocgTables32& tb, float tol, int maxit, int* iters, int* flags, int grid,
-                            cudaStream_t s) {
+                            cudaStream_t s, const float2* x0) {
+  if (x0 && M > kRegThreads * kRegElems) return cudaErrorInvalidValue;
   if (M <= kRegThreads * kRegElems) {
     const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
                         (size_t)pass_table_size(logL) * sizeof(float2);
-    auto kern = inner == 0 ? cocg_reg_kernel<0> : cocg_reg_kernel<1>;
+    auto kern = x0 ? (inner == 0 ? cocg_reg_kernel<0, true> : cocg_reg_kernel<1, true>)
+                   : (inner == 0 ? cocg_reg_kernel<0, false> : cocg_reg_kernel<1, false>);
     cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kRegThreads, smem, s>>>(xb, M, logL, nsys, tb, tol, maxit, iters, flags);
+    kern<<<grid, kRegThreads, smem, s>>>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags);
     return cudaGetLastError();
   }
   if (inner == 0)

@@ -4,6 +4,10 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
+struct aao_fno;
+
 namespace aao {
 
 // ---- all-at-once matvec (FP64), matvec.cu -------------------------------------------
@@ -53,10 +57,12 @@ struct CocgTables64 {
 // xb: [nsys][M] complex, right-hand sides on entry, solutions on exit.
 // rws, pws: [nsys][M] complex workspace.  gbuf: global FFT scratch used when
 // the transform does not fit in shared memory (may be null otherwise).
-// iters[n]: iterations used; flags[n]: 0 ok, 1 not converged, 2 breakdown, 3 non-finite.
+// iters[n]: iterations used; flags[n] & 3: 0 ok, 1 not converged, 2 breakdown, 3 non-finite.
+// x0 (optional, [nsys][M] complex, M <= 8192): learned initial guesses; system n
+// starts from x0[n] only if ||b - A x0[n]|| < ||b||, and then flags[n] |= 4.
 cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys,
                             int inner, const CocgTables32& tb, float tol, int maxit, int* iters,
-                            int* flags, int grid, cudaStream_t s);
+                            int* flags, int grid, cudaStream_t s, const float2* x0 = nullptr);
 cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gbuf, int M, int logL,
                             int nsys, int inner, const CocgTables64& tb, double tol, int maxit,
                             int* iters, int* flags, int grid, cudaStream_t s);
@@ -122,4 +128,9 @@ cudaError_t launch_build_rhs(const double* u0, const double* f, double* F, doubl
                              cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
 
+// Message reported by aao_last_error(NULL) (calls without a plan).
+void set_planless_error(const std::string& msg);
+// Shape of a learned warm-start model (fno.cu).
+int fno_grid_size(const aao_fno* f);
+int fno_max_batch(const aao_fno* f);
 }  // namespace aao

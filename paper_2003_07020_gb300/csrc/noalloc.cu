@@ -31,10 +31,6 @@
 #include "kernels.h"
 #include "setup.h"
 
-namespace aao {
-void set_planless_error(const std::string& msg);  // plan.cu
-}
-
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;

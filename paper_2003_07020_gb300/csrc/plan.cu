@@ -25,22 +25,29 @@ constexpr int kMaxRestart = 64;
 
 __global__ void iter_stats_kernel(const int* __restrict__ iters, const int* __restrict__ flags, int n,
                                   int* __restrict__ out) {
-  __shared__ int smax[256], fmax_[256], ssum[256];
-  int a = 0, b = 0, c = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { a = max(a, iters[i]); b = max(b, flags[i]); c += iters[i]; }
+  __shared__ int smax[256], fmax_[256], ssum[256], sacc[256];
+  int a = 0, b = 0, c = 0, d = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a = max(a, iters[i]);
+    b = max(b, flags[i] & 3);
+    c += iters[i];
+    d += (flags[i] >> 2) & 1;  // warm start accepted
+  }
   smax[threadIdx.x] = a;
   fmax_[threadIdx.x] = b;
   ssum[threadIdx.x] = c;
+  sacc[threadIdx.x] = d;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
       smax[threadIdx.x] = max(smax[threadIdx.x], smax[threadIdx.x + o]);
       fmax_[threadIdx.x] = max(fmax_[threadIdx.x], fmax_[threadIdx.x + o]);
       ssum[threadIdx.x] += ssum[threadIdx.x + o];
+      sacc[threadIdx.x] += sacc[threadIdx.x + o];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { out[0] = smax[0]; out[1] = fmax_[0]; out[2] = ssum[0]; }
+  if (threadIdx.x == 0) { out[0] = smax[0]; out[1] = fmax_[0]; out[2] = ssum[0]; out[3] = sacc[0]; }
 }
 
 }  // namespace
@@ -119,6 +126,13 @@ struct aao_plan {
   cudaEvent_t ev_open = nullptr;
   double prof_ms[AAO_NUM_STAGES] = {0};
   int64_t prof_launches[AAO_NUM_STAGES] = {0};
+  // learned warm start (aao_plan_set_warm_start) and training-pair recording
+  aao_fno* fno = nullptr;
+  float2* x0buf = nullptr;
+  float* fno_alpha = nullptr;
+  float2 *rec_b = nullptr, *rec_x = nullptr;
+  double2* rec_lam = nullptr;
+  int64_t rec_cap = 0, rec_count = 0;
 };
 
 namespace {
@@ -136,7 +150,8 @@ aao_status fail(aao_plan* p, aao_status st, const std::string& msg) {
       return fail(p, AAO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
   } while (0)
 
-enum { ST_MATVEC = 0, ST_TDFT_FWD = 1, ST_COCG = 2, ST_TDFT_INV = 3, ST_VEC = 4 };
+enum { ST_MATVEC = 0, ST_TDFT_FWD = 1, ST_COCG = 2, ST_TDFT_INV = 3, ST_VEC = 4, ST_FNO = 5 };
+constexpr int kFnoLaunches = 17;  // kernels of one aao_fno_predict
 
 cudaEvent_t take_event(aao_plan* p) {
   if (!p->ev_pool.empty()) {
@@ -293,9 +308,28 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
       TRY(cocg2d_any<float>(p, spec));
     } else {
       aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
+      const int64_t nrec = std::min<int64_t>(p->nsys, p->rec_cap - p->rec_count);
+      if (nrec > 0) {
+        CK(cudaMemcpyAsync(p->rec_b + p->rec_count * p->M, spec, nrec * p->M * sizeof(float2),
+                           cudaMemcpyDeviceToDevice, p->stream));
+        CK(cudaMemcpyAsync(p->rec_lam + p->rec_count, p->lambda, nrec * sizeof(double2), cudaMemcpyDeviceToDevice,
+                           p->stream));
+      }
+      if (p->fno) {
+        prof_begin(p);
+        const aao_status fs = aao_fno_predict(p->fno, p->nsys, spec, p->lambda, p->fno_alpha, p->x0buf, p->stream);
+        if (fs != AAO_OK) return fail(p, fs, std::string("warm start: ") + aao_last_error(nullptr));
+        prof_end(p, ST_FNO, kFnoLaunches);
+      }
       LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
                                               (int)p->opts.inner, tb, (float)p->opts.inner_tol, p->opts.inner_maxit,
-                                              p->iters, p->flags, p->cocg_grid, p->stream));
+                                              p->iters, p->flags, p->cocg_grid, p->stream,
+                                              p->fno ? p->x0buf : nullptr));
+      if (nrec > 0) {
+        CK(cudaMemcpyAsync(p->rec_x + p->rec_count * p->M, spec, nrec * p->M * sizeof(float2),
+                           cudaMemcpyDeviceToDevice, p->stream));
+        p->rec_count += nrec;
+      }
     }
     if (out_kind == 0)
       LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f32(spec, (float*)out, Ms, p->Nt, p->sinv32, p->twNt32,
@@ -505,6 +539,10 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   TRYP(dalloc(p, &p->iters, (size_t)p->nsys));
   TRYP(dalloc(p, &p->flags, (size_t)p->nsys));
   TRYP(dalloc(p, &p->stats, 4));
+  if (cudaMemset(p->stats, 0, 4 * sizeof(int)) != cudaSuccess) {
+    p->err = "cudaMemset failed";
+    return bail(AAO_ECUDA);
+  }
   TRYP(dalloc(p, &p->partial, (size_t)std::max(aao::blas_partial_blocks() * 65, p->Nt)));
   TRYP(dalloc(p, &p->hdev, 4 * 65));
   TRYP(dalloc(p, &p->sq, p->nsq));
@@ -545,6 +583,46 @@ aao_status aao_plan_get_profile(aao_plan* p, double* ms, int64_t* launches, int 
     if (launches) launches[i] = p->prof_launches[i];
     if (reset) { p->prof_ms[i] = 0; p->prof_launches[i] = 0; }
   }
+  return AAO_OK;
+}
+
+aao_status aao_plan_set_warm_start(aao_plan* p, aao_fno* fno) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!fno) {
+    p->fno = nullptr;
+    return AAO_OK;
+  }
+  if (p->dim != 1 || !p->mixed || p->M > 8191)
+    return fail(p, AAO_EINVAL, "the warm start needs a 1D AAO_PREC_MIXED plan");
+  if (aao::fno_grid_size(fno) != p->M || aao::fno_max_batch(fno) < p->nsys)
+    return fail(p, AAO_EINVAL, "the model's M must equal the plan's and its max_batch must be >= Nt/2 + 1");
+  if (!p->x0buf) {
+    TRY(dalloc(p, &p->x0buf, (size_t)p->nsys * p->M));
+    TRY(dalloc(p, &p->fno_alpha, (size_t)p->nsys));
+    std::vector<float> a(p->nsys, (float)p->prob.alpha);
+    CK(cudaMemcpy(p->fno_alpha, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  p->fno = fno;
+  return AAO_OK;
+}
+
+aao_status aao_plan_record_pairs(aao_plan* p, int64_t capacity, void* b, void* x, void* lam) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (capacity < 0) return fail(p, AAO_EINVAL, "negative capacity");
+  if (capacity > 0 && b && x && lam && (p->dim != 1 || !p->mixed))
+    return fail(p, AAO_EINVAL, "pair recording needs a 1D AAO_PREC_MIXED plan");
+  const bool on = capacity > 0 && b && x && lam;
+  p->rec_b = on ? (float2*)b : nullptr;
+  p->rec_x = on ? (float2*)x : nullptr;
+  p->rec_lam = on ? (double2*)lam : nullptr;
+  p->rec_cap = on ? capacity : 0;
+  p->rec_count = 0;
+  return AAO_OK;
+}
+
+aao_status aao_plan_recorded_pairs(const aao_plan* p, int64_t* count) {
+  if (!p || !count) return fail(nullptr, AAO_EINVAL, "null argument");
+  *count = p->rec_count;
   return AAO_OK;
 }
 
@@ -625,12 +703,13 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
       LAUNCH(ST_VEC, 1, aao::launch_update_norm(w, p->V, n, nv, n, p->hdev + 65, p->partial, p->stream));
       LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, 1, p->hdev + 130, p->stream));
       CK(cudaMemcpyAsync(p->pinned, p->hdev, 131 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-      int st[3] = {0, 0, 0};
-      CK(cudaMemcpyAsync(p->pinned + 200, p->stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+      int st[4] = {0, 0, 0, 0};
+      CK(cudaMemcpyAsync(p->pinned + 200, p->stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
       CK(cudaStreamSynchronize(p->stream));
-      std::memcpy(st, p->pinned + 200, 3 * sizeof(int));
+      std::memcpy(st, p->pinned + 200, 4 * sizeof(int));
       inf.inner_iters_max = std::max(inf.inner_iters_max, st[0]);
       inf.inner_iters_sum += st[2];
+      inf.warm_accepted += st[3];
       if (st[1] != 0 && inf.status_detail == 0)
         inf.status_detail = st[1] == 1 ? AAO_ENOCONV : (st[1] == 2 ? AAO_EBREAKDOWN : AAO_ENONFINITE);
       for (int i = 0; i <= j; ++i) Hij(i, j) = p->pinned[i] + p->pinned[65 + i];

@@ -64,6 +64,15 @@ def batched_instances(n=64, seed=0, Ms=(511, 1023, 2047, 4095), Nts=(128, 256, 5
             for i in range(n)]
 
 
+def learned_instances(n, seed=0, M=1023, Nt=256, first_seed=0):
+    """Parameters of n 1D instances of the learned warm-start workload: fixed M and Nt, alpha ~ U(1.1, 1.9),
+    kappa = 1, inputs "sine8_normal" with seeds first_seed, first_seed + 1, ...  Training and held-out sets
+    use disjoint seed ranges.  Returns a list of dicts (M, Nt, alpha, kappa, seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    alpha = rng.uniform(1.1, 1.9, n)
+    return [dict(M=int(M), Nt=int(Nt), alpha=float(alpha[i]), kappa=1.0, seed=first_seed + i) for i in range(n)]
+
+
 def random_vector(Nt, M, seed=0):
     """A generic space-time vector with N(0, 1) entries (for operator tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -89,3 +89,22 @@ def test_null_plan_calls_fail_cleanly(lib):
     assert lib.aao_matvec(None, None, None) == aao.AAO_EINVAL
     assert lib.aao_plan_destroy(None) == aao.AAO_OK
     assert lib.aao_plan_workspace_bytes(None) == 0
+
+
+def test_fno_parameter_count_matches_oracle_layout(lib):
+    from oracle import fno
+    assert lib.aao_fno_num_params() == fno.num_params(32, 16, 4)
+
+
+def test_fno_and_warm_start_calls_validate_without_gpu(lib):
+    h = ctypes.c_void_p()
+    # grid too small for 16 modes, and a null output handle
+    assert lib.aao_fno_create(16, 4, 0, ctypes.byref(h)) == aao.AAO_EINVAL
+    assert lib.aao_fno_create(63, 4, 0, None) == aao.AAO_EINVAL
+    assert lib.aao_fno_destroy(None) == aao.AAO_OK
+    assert lib.aao_fno_predict(None, 1, None, None, None, None, None) == aao.AAO_EINVAL
+    assert lib.aao_fno_save(None, b"x") == aao.AAO_EINVAL
+    assert lib.aao_plan_set_warm_start(None, None) == aao.AAO_EINVAL
+    assert lib.aao_plan_record_pairs(None, 0, None, None, None) == aao.AAO_EINVAL
+    n = ctypes.c_int64(-1)
+    assert lib.aao_plan_recorded_pairs(None, ctypes.byref(n)) == aao.AAO_EINVAL
