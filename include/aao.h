@@ -86,6 +86,10 @@ typedef struct {
   int inner_maxit;      /* COCG iteration cap per system [200] */
   aao_precision prec;   /* [AAO_PREC_MIXED] */
   aao_inner_precond inner; /* [AAO_INNER_STRANG] */
+  int use_graphs;       /* [1] 1D: run each restart cycle as one CUDA graph (the Arnoldi steps as
+                           conditional nodes, Givens rotations on the device, one host synchronisation
+                           per cycle instead of one per step); ignored in 2D, while profiling, or
+                           while recording pairs.  0: host-driven steps. */
 } aao_opts;
 
 /* Result of a solve. */
@@ -291,7 +295,8 @@ aao_status aao_fno_train_step(aao_fno* fno, int B, const void* b_dev, const void
  * Step (b) then predicts x0 for all shifted systems and COCG starts system n
  * from its prediction only if the FP32 residual ||zhat_n - A_n x0|| is
  * below ||zhat_n||, else from 0; the stopping test stays relative to
- * ||zhat_n||.  The model must not be used by another call meanwhile.
+ * ||zhat_n||.  The model must stay alive while attached and must not be
+ * used by another call meanwhile.
  */
 aao_status aao_plan_set_warm_start(aao_plan* plan, aao_fno* fno);
 

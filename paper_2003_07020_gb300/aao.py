@@ -41,7 +41,7 @@ class AaoProblem(ctypes.Structure):
 class AaoOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner", ctypes.c_int)]
+                ("inner", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class AaoInfo(ctypes.Structure):

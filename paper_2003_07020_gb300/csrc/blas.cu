@@ -143,6 +143,13 @@ __global__ void scale_kernel(double* __restrict__ out, const double* __restrict_
     out[e] = a * in[e];
 }
 
+__global__ void scale_dev_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                 const double* __restrict__ a_dev, size_t n) {
+  const double a = *a_dev;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = a * in[e];
+}
+
 template <typename TZ, int NZMAX>
 __global__ void __launch_bounds__(kBlasThreads) zy_kernel(double* __restrict__ U, const TZ* __restrict__ Z,
                                                           size_t zstride, int nz, size_t n,
@@ -206,6 +213,10 @@ cudaError_t launch_reduce_partials(const double* partial, int nblocks, int nv, d
 }
 cudaError_t launch_scale(double* out, const double* in, double a, size_t n, cudaStream_t s) {
   scale_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(out, in, a, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_dev(double* out, const double* in, const double* a_dev, size_t n, cudaStream_t s) {
+  scale_dev_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(out, in, a_dev, n);
   return cudaGetLastError();
 }
 cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,

@@ -119,6 +119,8 @@ cudaError_t launch_update_norm(double* w, const double* V, size_t vstride, int n
 cudaError_t launch_reduce_partials(const double* partial, int nblocks, int nv, double* out,
                                    cudaStream_t s);
 cudaError_t launch_scale(double* out, const double* in, double a, size_t n, cudaStream_t s);
+// out = (*a_dev) * in, the factor read from device memory
+cudaError_t launch_scale_dev(double* out, const double* in, const double* a_dev, size_t n, cudaStream_t s);
 // U += sum_j y[j] Z_j  (Z float or double)
 cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n,
                                  const double* y, cudaStream_t s);

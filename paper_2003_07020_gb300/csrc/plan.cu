@@ -50,6 +50,119 @@ __global__ void iter_stats_kernel(const int* __restrict__ iters, const int* __re
   if (threadIdx.x == 0) { out[0] = smax[0]; out[1] = fmax_[0]; out[2] = ssum[0]; out[3] = sacc[0]; }
 }
 
+// ---- graph-captured restart cycles ---------------------------------------------------------
+// Device copy of the FGMRES recurrences of one restart cycle (Givens rotations,
+// residual estimate, least-squares solution), so that a whole cycle runs as one
+// CUDA graph whose Arnoldi steps are conditional nodes.
+struct GmresDevState {
+  double H[(kMaxRestart + 1) * kMaxRestart];  // H[i * kMaxRestart + j]
+  double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+  double thr;                                 // 0.5 * tol * ||F||: stop when |g[j+1]| <= thr
+  double inv_beta, inv_hn;
+  int jdone, active, status, outer_total;
+  int inner_max, flag_max;
+  long long inner_sum, accepted;
+};
+
+// Start of a cycle: g = (beta, 0, ...), beta^2 = *beta2 from the residual reduction; enables step 0.
+__global__ void cycle_init_kernel(GmresDevState* d, const double* beta2, int m, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(*beta2);
+  for (int i = 0; i <= m; ++i) d->g[i] = 0.0;
+  d->g[0] = beta;
+  d->inv_beta = 1.0 / beta;
+  d->jdone = 0;
+  d->active = 1;
+  d->status = 0;
+  cudaGraphSetConditional(h, 1u);
+}
+
+// Column j of H from the two Gram-Schmidt passes (hd[i] + hd[65 + i], norm^2 in hd[130]),
+// the previous rotations, a new rotation and the residual estimate |g[j+1]|; enables step
+// j + 1 (its conditional handle h_next, when has_next) unless the cycle stops here.
+__global__ void givens_kernel(GmresDevState* d, const double* hd, int j, int m, cudaGraphConditionalHandle h_next,
+                              int has_next) {
+  if (threadIdx.x != 0) return;
+  double* H = d->H;
+  auto at = [&](int i, int k) -> double& { return H[i * kMaxRestart + k]; };
+  for (int i = 0; i <= j; ++i) at(i, j) = hd[i] + hd[65 + i];
+  const double hn = sqrt(hd[130]);
+  at(j + 1, j) = hn;
+  bool stop = false;
+  if (!isfinite(hn)) {
+    d->status = AAO_ENONFINITE;
+    stop = true;
+  } else {
+    d->inv_hn = hn > 0 ? 1.0 / hn : 0.0;
+    for (int i = 0; i < j; ++i) {
+      const double t = d->cs[i] * at(i, j) + d->sn[i] * at(i + 1, j);
+      at(i + 1, j) = -d->sn[i] * at(i, j) + d->cs[i] * at(i + 1, j);
+      at(i, j) = t;
+    }
+    const double dd = hypot(at(j, j), at(j + 1, j));
+    if (dd == 0.0) {
+      d->status = AAO_EBREAKDOWN;
+      stop = true;
+    } else {
+      d->cs[j] = at(j, j) / dd;
+      d->sn[j] = at(j + 1, j) / dd;
+      at(j, j) = dd;
+      at(j + 1, j) = 0.0;
+      d->g[j + 1] = -d->sn[j] * d->g[j];
+      d->g[j] = d->cs[j] * d->g[j];
+      d->outer_total++;
+      d->jdone = j + 1;
+      if (fabs(d->g[j + 1]) <= d->thr || hn == 0.0 || j + 1 == m) stop = true;
+    }
+  }
+  if (stop) d->active = 0;
+  if (has_next) cudaGraphSetConditional(h_next, stop ? 0u : 1u);
+}
+
+// y = H(0:jdone, 0:jdone)^{-1} g by back substitution (upper triangular after the rotations)
+__global__ void lsq_kernel(GmresDevState* d) {
+  if (threadIdx.x != 0 || d->status != 0) return;
+  const int jd = d->jdone;
+  for (int i = jd - 1; i >= 0; --i) {
+    double s = d->g[i];
+    for (int k = i + 1; k < jd; ++k) s -= d->H[i * kMaxRestart + k] * d->y[k];
+    d->y[i] = s / d->H[i * kMaxRestart + i];
+  }
+}
+
+// COCG iteration statistics of one preconditioner application, accumulated on the device
+__global__ void iter_stats_accum_kernel(const int* __restrict__ iters, const int* __restrict__ flags, int n,
+                                        GmresDevState* d) {
+  __shared__ int smax[256], fmax_[256], ssum[256], sacc[256];
+  int a = 0, b = 0, c = 0, e = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a = max(a, iters[i]);
+    b = max(b, flags[i] & 3);
+    c += iters[i];
+    e += (flags[i] >> 2) & 1;
+  }
+  smax[threadIdx.x] = a;
+  fmax_[threadIdx.x] = b;
+  ssum[threadIdx.x] = c;
+  sacc[threadIdx.x] = e;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smax[threadIdx.x] = max(smax[threadIdx.x], smax[threadIdx.x + o]);
+      fmax_[threadIdx.x] = max(fmax_[threadIdx.x], fmax_[threadIdx.x + o]);
+      ssum[threadIdx.x] += ssum[threadIdx.x + o];
+      sacc[threadIdx.x] += sacc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d->inner_max = max(d->inner_max, smax[0]);
+    if (d->flag_max == 0) d->flag_max = fmax_[0];
+    d->inner_sum += ssum[0];
+    d->accepted += sacc[0];
+  }
+}
+
 }  // namespace
 
 namespace aao {
@@ -133,6 +246,13 @@ struct aao_plan {
   float2 *rec_b = nullptr, *rec_x = nullptr;
   double2* rec_lam = nullptr;
   int64_t rec_cap = 0, rec_count = 0;
+  // graph-captured restart cycles (opts.use_graphs)
+  GmresDevState* gd = nullptr;
+  GmresDevState* gd_host = nullptr;  // pinned mirror for the per-cycle readback
+  cudaGraphExec_t cycle_exec = nullptr;
+  cudaStream_t cap1 = nullptr, cap2 = nullptr;
+  aao_fno* graph_fno = nullptr;      // warm-start model baked into cycle_exec
+  int64_t step_launches[AAO_NUM_STAGES] = {0};
 };
 
 namespace {
@@ -354,6 +474,140 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
   return AAO_OK;
 }
 
+// One Arnoldi step j of FGMRES (Sec. 4): z_j = P^{-1} v_j (Steps (a)-(c)), COCG statistics
+// (into p->stats, or accumulated into acc), w = calA z_j, and CGS2 against v_0..v_j:
+// h1 = V^T w (p->hdev), w -= V h1, h2 = V^T w (p->hdev + 65), w -= V h2, ||w||^2 (p->hdev[130]).
+aao_status arnoldi_step(aao_plan* p, int j, GmresDevState* acc) {
+  const size_t n = p->n;
+  const int nb = aao::blas_partial_blocks();
+  double* vj = p->V + (size_t)j * n;
+  double* w = p->V + (size_t)(j + 1) * n;
+  void* zj = p->mixed ? (void*)((float*)p->Z + (size_t)j * n) : (void*)((double*)p->Z + (size_t)j * n);
+  TRY(precond_any(p, vj, zj, p->mixed ? 0 : 1));
+  if (acc)
+    LAUNCH(ST_VEC, 1, (iter_stats_accum_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, acc),
+                       cudaGetLastError()));
+  else
+    LAUNCH(ST_VEC, 1, (iter_stats_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->stats),
+                       cudaGetLastError()));
+  TRY(matvec_any(p, zj, p->mixed, nullptr, w, nullptr));
+  const int nv = j + 1;
+  LAUNCH(ST_VEC, 1, aao::launch_dots(w, p->V, n, nv, n, p->partial, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_update_dots(w, p->V, n, nv, n, p->hdev, p->partial, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev + 65, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_update_norm(w, p->V, n, nv, n, p->hdev + 65, p->partial, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, 1, p->hdev + 130, p->stream));
+  return AAO_OK;
+}
+
+void release_cycle_graph(aao_plan* p) {
+  if (p->cycle_exec) cudaGraphExecDestroy(p->cycle_exec);
+  p->cycle_exec = nullptr;
+  p->graph_fno = nullptr;
+}
+
+// Captures one restart cycle as a graph: init (g = beta e_1, v_0 /= beta), then for j < m a
+// conditional IF node whose body is Arnoldi step j + the device Givens update + v_{j+1} /= h,
+// then the least-squares solve.  Each IF node has its own handle, reset to 0 at every launch;
+// the init kernel enables step 0 and step j's Givens kernel enables step j + 1.  Kernels are
+// recorded on plan-owned capture streams.
+aao_status build_cycle_graph(aao_plan* p) {
+  release_cycle_graph(p);
+  if (!p->gd) {
+    TRY(dalloc(p, &p->gd, 1));
+    if (cudaMallocHost(&p->gd_host, sizeof(GmresDevState)) != cudaSuccess) {
+      p->gd_host = nullptr;
+      return fail(p, AAO_ENOMEM, "cudaMallocHost failed");
+    }
+  }
+  if (!p->cap1) {
+    CK(cudaStreamCreateWithFlags(&p->cap1, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking));
+  }
+  const int m = p->m;
+  const size_t n = p->n;
+  cudaStream_t user = p->stream;
+  int64_t saved[AAO_NUM_STAGES];
+  std::memcpy(saved, p->prof_launches, sizeof saved);
+  cudaGraph_t g = nullptr;
+  std::string err;
+  auto check = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && err.empty()) err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaSuccess;
+  };
+  p->stream = p->cap1;
+  if (check(cudaStreamBeginCapture(p->cap1, cudaStreamCaptureModeRelaxed), "begin capture")) {
+    cudaStreamCaptureStatus cst;
+    std::vector<cudaGraphConditionalHandle> hs(m, 0);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    bool ok = check(cudaStreamGetCaptureInfo(p->cap1, &cst, nullptr, &g), "capture info");
+    for (int j = 0; ok && j < m; ++j)
+      ok = check(cudaGraphConditionalHandleCreate(&hs[j], g, 0, cudaGraphCondAssignDefault), "conditional handle");
+    if (ok) {
+      cycle_init_kernel<<<1, 1, 0, p->cap1>>>(p->gd, p->hdev, m, hs[0]);
+      ok = check(cudaGetLastError(), "cycle init") &&
+           check(aao::launch_scale_dev(p->V, p->V, &p->gd->inv_beta, n, p->cap1), "scale v0");
+    }
+    for (int j = 0; ok && j < m; ++j) {
+      ok = check(cudaStreamGetCaptureInfo(p->cap1, &cst, nullptr, nullptr, &deps, nullptr, &ndeps), "capture info");
+      if (!ok) break;
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hs[j];
+      np.conditional.type = cudaGraphCondTypeIf;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      ok = check(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np), "conditional node") &&
+           check(cudaStreamUpdateCaptureDependencies(p->cap1, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+                 "capture dependencies");
+      if (!ok) break;
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      p->stream = p->cap2;
+      if (!check(cudaStreamBeginCaptureToGraph(p->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+                 "begin body capture")) {
+        ok = false;
+        break;
+      }
+      int64_t before[AAO_NUM_STAGES];
+      std::memcpy(before, p->prof_launches, sizeof before);
+      const aao_status st = arnoldi_step(p, j, p->gd);
+      if (st == AAO_OK) {
+        givens_kernel<<<1, 1, 0, p->cap2>>>(p->gd, p->hdev, j, m, j + 1 < m ? hs[j + 1] : hs[j], j + 1 < m);
+        double* w = p->V + (size_t)(j + 1) * n;
+        if (check(cudaGetLastError(), "givens")) check(aao::launch_scale_dev(w, w, &p->gd->inv_hn, n, p->cap2), "scale");
+        if (j == 0)
+          for (int q = 0; q < AAO_NUM_STAGES; ++q) p->step_launches[q] = p->prof_launches[q] - before[q];
+      } else if (err.empty()) {
+        err = p->err;
+      }
+      cudaGraph_t body_out = nullptr;
+      check(cudaStreamEndCapture(p->cap2, &body_out), "end body capture");
+      p->stream = p->cap1;
+      ok = err.empty();
+    }
+    if (ok) {
+      lsq_kernel<<<1, 1, 0, p->cap1>>>(p->gd);
+      check(cudaGetLastError(), "lsq");
+    }
+    cudaGraph_t g_out = nullptr;
+    check(cudaStreamEndCapture(p->cap1, &g_out), "end capture");
+    if (err.empty()) check(cudaGraphInstantiate(&p->cycle_exec, g_out, 0), "instantiate");
+    if (g_out) cudaGraphDestroy(g_out);
+  }
+  p->stream = user;
+  std::memcpy(p->prof_launches, saved, sizeof saved);
+  // givens + scale per step on top of the step's own kernels
+  p->step_launches[ST_VEC] += 2;
+  if (!err.empty()) {
+    release_cycle_graph(p);
+    return fail(p, AAO_ECUDA, "cycle graph: " + err);
+  }
+  p->graph_fno = p->fno;
+  return AAO_OK;
+}
+
 aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (!prob || !o) return fail(nullptr, AAO_EINVAL, "null problem or options");
   if (prob->dim != 1 && prob->dim != 2) return fail(nullptr, AAO_EINVAL, "dim must be 1 or 2");
@@ -376,7 +630,63 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (o->inner != AAO_INNER_STRANG && o->inner != AAO_INNER_TAU) return fail(nullptr, AAO_EINVAL, "bad inner");
   if (o->inner == AAO_INNER_TAU && ((prob->M + 1) & prob->M))
     return fail(nullptr, AAO_EINVAL, "the tau preconditioner needs M+1 to be a power of two");
+  if (o->use_graphs != 0 && o->use_graphs != 1) return fail(nullptr, AAO_EINVAL, "use_graphs must be 0 or 1");
   return AAO_OK;
+}
+
+// aao_gmres_solve with each restart cycle replayed as one CUDA graph (1D); nF = ||F|| > 0.
+aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* info, double nF) {
+  if (!p->cycle_exec || p->graph_fno != p->fno) TRY(build_cycle_graph(p));
+  const size_t n = p->n;
+  const size_t tail = sizeof(GmresDevState) - offsetof(GmresDevState, thr);
+  GmresDevState& hs = *p->gd_host;
+  std::memset(&hs.thr, 0, tail);
+  hs.thr = 0.5 * p->opts.tol * nF;
+  CK(cudaMemcpyAsync(&p->gd->thr, &hs.thr, tail, cudaMemcpyHostToDevice, p->stream));
+  aao_info inf{};
+  aao_status result = AAO_ENOCONV;
+  int outer_prev = 0;
+  for (int cycle = 0; cycle <= p->opts.max_cycles; ++cycle) {
+    TRY(matvec_any(p, U, false, F, p->V, p->sq));  // r = F - calA U into v_0, row sums of squares
+    inf.matvecs++;
+    double beta2 = 0;
+    TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));  // leaves beta^2 in p->hdev[0]
+    const double beta = std::sqrt(beta2);
+    if (!std::isfinite(beta)) { result = AAO_ENONFINITE; p->err = "non-finite residual"; break; }
+    inf.true_rel_res = beta / nF;
+    inf.cycles = cycle;
+    if (inf.true_rel_res <= p->opts.tol) { result = AAO_OK; break; }
+    if (cycle == p->opts.max_cycles) break;
+    CK(cudaGraphLaunch(p->cycle_exec, p->stream));
+    CK(cudaMemcpyAsync(&hs.thr, &p->gd->thr, tail, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    const int steps = hs.outer_total - outer_prev + (hs.status != 0 ? 1 : 0);
+    outer_prev = hs.outer_total;
+    inf.matvecs += steps;
+    for (int q = 0; q < AAO_NUM_STAGES; ++q) p->prof_launches[q] += steps * p->step_launches[q];
+    p->prof_launches[ST_VEC] += 3;  // cycle init, v_0 scaling, least squares
+    if (hs.status != 0) {
+      result = (aao_status)hs.status;
+      p->err = result == AAO_EBREAKDOWN ? "GMRES breakdown" : "non-finite Arnoldi vector";
+      break;
+    }
+    if (hs.jdone > 0) {
+      if (p->mixed)
+        LAUNCH(ST_VEC, 1, aao::launch_zy_update_f32(U, (const float*)p->Z, n, hs.jdone, n, p->gd->y, p->stream));
+      else
+        LAUNCH(ST_VEC, 1, aao::launch_zy_update_f64(U, (const double*)p->Z, n, hs.jdone, n, p->gd->y, p->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  inf.outer_iters = hs.outer_total;
+  inf.inner_iters_max = hs.inner_max;
+  inf.inner_iters_sum = hs.inner_sum;
+  inf.warm_accepted = hs.accepted;
+  if (hs.flag_max != 0)
+    inf.status_detail = hs.flag_max == 1 ? AAO_ENOCONV : (hs.flag_max == 2 ? AAO_EBREAKDOWN : AAO_ENONFINITE);
+  if (info) *info = inf;
+  if (result == AAO_ENOCONV) p->err = "FGMRES did not reach the tolerance within max_cycles";
+  return result;
 }
 
 }  // namespace
@@ -392,6 +702,7 @@ void aao_default_opts(aao_opts* o, aao_precision prec) {
   o->inner_maxit = 200;
   o->prec = prec;
   o->inner = AAO_INNER_STRANG;
+  o->use_graphs = 1;
 }
 
 aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host) {
@@ -413,6 +724,10 @@ aao_status aao_plan_destroy(aao_plan* p) {
     cudaEventDestroy(pr.second.second);
   }
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  release_cycle_graph(p);
+  if (p->cap1) cudaStreamDestroy(p->cap1);
+  if (p->cap2) cudaStreamDestroy(p->cap2);
+  if (p->gd_host) cudaFreeHost(p->gd_host);
   for (void* q : p->allocs) cudaFree(q);
   if (p->pinned) cudaFreeHost(p->pinned);
   if (p->host_count) cudaFreeHost(p->host_count);
@@ -588,6 +903,7 @@ aao_status aao_plan_get_profile(aao_plan* p, double* ms, int64_t* launches, int 
 
 aao_status aao_plan_set_warm_start(aao_plan* p, aao_fno* fno) {
   if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  release_cycle_graph(p);  // a captured cycle holds the previous model's buffers
   if (!fno) {
     p->fno = nullptr;
     return AAO_OK;
@@ -663,6 +979,8 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     if (info) *info = inf;
     return AAO_OK;
   }
+  if (p->opts.use_graphs && p->dim == 1 && !p->prof_on && p->rec_cap <= p->rec_count)
+    return gmres_solve_graph(p, F, U, info, nF);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   const double tol = p->opts.tol;
@@ -686,22 +1004,9 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     int jdone = 0;
     bool stop = false;
     for (int j = 0; j < m && !stop; ++j) {
-      double* vj = p->V + (size_t)j * n;
       double* w = p->V + (size_t)(j + 1) * n;
-      void* zj = p->mixed ? (void*)((float*)p->Z + (size_t)j * n) : (void*)((double*)p->Z + (size_t)j * n);
-      TRY(precond_any(p, vj, zj, p->mixed ? 0 : 1));
-      LAUNCH(ST_VEC, 1, (iter_stats_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->stats),
-                         cudaGetLastError()));
-      TRY(matvec_any(p, zj, p->mixed, nullptr, w, nullptr));
+      TRY(arnoldi_step(p, j, nullptr));
       inf.matvecs++;
-      // CGS2: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2; ||w||
-      const int nv = j + 1;
-      LAUNCH(ST_VEC, 1, aao::launch_dots(w, p->V, n, nv, n, p->partial, p->stream));
-      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
-      LAUNCH(ST_VEC, 1, aao::launch_update_dots(w, p->V, n, nv, n, p->hdev, p->partial, p->stream));
-      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev + 65, p->stream));
-      LAUNCH(ST_VEC, 1, aao::launch_update_norm(w, p->V, n, nv, n, p->hdev + 65, p->partial, p->stream));
-      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, 1, p->hdev + 130, p->stream));
       CK(cudaMemcpyAsync(p->pinned, p->hdev, 131 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
       int st[4] = {0, 0, 0, 0};
       CK(cudaMemcpyAsync(p->pinned + 200, p->stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
