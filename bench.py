@@ -424,6 +424,7 @@ def run_ours(args):
                    "inner_iters_max": max(i["inner_iters_max"] for i in infos),
                    "true_rel_res_max": max(i["true_rel_res"] for i in infos),
                    "fgmres_cycles": "CUDA graph per restart cycle" if args.dim == 1 else "host-driven steps",
+                   "cocg_threads": plans[0].cocg_threads,
                    "stage_ms_profiled_pass": {k: round(v[0], 3) for k, v in prof.items()},
                    "stage_launches_profiled_pass": {k: v[1] for k, v in prof.items()}},
         "gpu_launches": int(launches_timed),
@@ -548,6 +549,7 @@ def run_learned(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     launches_timed = sum(n for p in plans for _, n in p.get_profile(reset=True).values())
+    cocg_threads = plans[0].cocg_threads
     for p in plans:  # stage breakdown from one more pass with every launch bracketed by events
         p.set_profiling(True)
     prof_infos = pass_over(plans)
@@ -648,6 +650,7 @@ def run_learned(args):
                        "l2": "no explicit flush: each solve streams a ~100 MB Krylov basis; consecutive "
                              "instances use different plans and vectors",
                        "fgmres_cycles": "CUDA graph per restart cycle",
+                       "cocg_threads": cocg_threads,
                        "stage_ms_profiled_pass": {k: round(v[0], 3) for k, v in prof.items()},
                        "stage_launches_profiled_pass": {k: v[1] for k, v in prof.items()}},
             "gpu_launches": int(launches_timed),
@@ -753,6 +756,7 @@ def run_batched(args):
                        "outer_iters_max": max(i["outer_iters"] for i in infos),
                        "true_rel_res_max": max(i["true_rel_res"] for i in infos),
                        "fgmres_cycles": "CUDA graph per restart cycle",
+                       "cocg_threads_by_M": {str(m): t for m, t in sorted({(p.M, p.cocg_threads) for p in plans})},
                        "stage_ms_sum_over_streams_profiled_step": {k: round(v[0], 3) for k, v in prof.items()}},
             "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

@@ -90,6 +90,10 @@ typedef struct {
                            conditional nodes, Givens rotations on the device, one host synchronisation
                            per cycle instead of one per step); ignored in 2D, while profiling, or
                            while recording pairs.  0: host-driven steps. */
+  int cocg_threads;     /* [0] mixed 1D, M <= 8192: CTA size of the register-resident COCG kernel
+                           (64, 128, 256 or 512, at least M / 16); 0 lets plan creation time the
+                           admissible sizes on the plan's own systems and keep the fastest (cached
+                           per problem shape for the process) */
 } aao_opts;
 
 /* Result of a solve. */
@@ -134,6 +138,10 @@ aao_status aao_plan_destroy(aao_plan* plan);
 
 /* Bytes of device workspace the plan holds. */
 size_t aao_plan_workspace_bytes(const aao_plan* plan);
+
+/* Launch shapes the plan uses: *cocg_threads = CTA size of the Step (b) kernel
+ * (0 where the shared-memory kernel serves: FP64, M > 8192 or 2D). */
+aao_status aao_plan_get_tuning(const aao_plan* plan, int* cocg_threads);
 
 /*
  * Right-hand side of Eq. 12: F_1 = tau f^1 + u^0, F_2 = tau f^2 - u^0/2,

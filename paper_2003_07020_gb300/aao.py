@@ -28,7 +28,7 @@ EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan
             "aao_fno_num_params", "aao_fno_create", "aao_fno_destroy", "aao_fno_set_params",
             "aao_fno_get_params", "aao_fno_save", "aao_fno_load", "aao_fno_predict", "aao_fno_loss_grad",
             "aao_fno_train_step", "aao_plan_set_warm_start", "aao_plan_record_pairs",
-            "aao_plan_recorded_pairs")
+            "aao_plan_recorded_pairs", "aao_plan_get_tuning")
 STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector", "fno")
 
 
@@ -41,7 +41,7 @@ class AaoProblem(ctypes.Structure):
 class AaoOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("inner", ctypes.c_int), ("use_graphs", ctypes.c_int), ("cocg_threads", ctypes.c_int)]
 
 
 class AaoInfo(ctypes.Structure):
@@ -104,6 +104,7 @@ def load():
     lib.aao_plan_set_warm_start.argtypes = [vp, vp]
     lib.aao_plan_record_pairs.argtypes = [vp, i64, vp, vp, vp]
     lib.aao_plan_recorded_pairs.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.aao_plan_get_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     for name in EXPORTED:
         if name not in ("aao_default_opts", "aao_plan_workspace_bytes", "aao_last_error", "aao_fno_num_params"):
             getattr(lib, name).restype = ctypes.c_int
@@ -182,6 +183,13 @@ class Plan:
     @property
     def workspace_bytes(self):
         return load().aao_plan_workspace_bytes(self.handle)
+
+    @property
+    def cocg_threads(self):
+        """CTA size of the Step (b) kernel chosen at plan creation (0: shared-memory kernel)."""
+        v = ctypes.c_int()
+        _check(load().aao_plan_get_tuning(self.handle, ctypes.byref(v)), self.handle)
+        return v.value
 
     def _vec(self, t, name):
         if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):

@@ -188,12 +188,14 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
 }
 
 // ---- FP32 path with register-resident vectors -------------------------------------------
-// 512 threads; thread t owns elements i = t + 512 j, j < 16 (M <= 8192), so r and p live in
-// registers for the whole solve and only x is updated in global memory.
-constexpr int kRegThreads = 512;
+// NT threads (64 .. 512, chosen per problem by the autotuner of plan creation); thread t owns
+// elements i = t + NT j, j < 16 (M <= 16 NT), so r and p live in registers for the whole solve
+// and only x is updated in global memory.  Every variant keeps <= 128 registers per thread so
+// that 512 / NT CTAs fit on an SM.
+constexpr int kRegMaxThreads = 512;
 constexpr int kRegElems = 16;
 
-template <int KIND>
+template <int KIND, int NT>
 __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegElems], int M, int logL, float2 lam,
                                             const CocgTables32& tb, const float2* q, const float2* pt) {
   const int L = 1 << logL;
@@ -201,15 +203,15 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
   if (KIND == 0) {
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + kRegThreads * j;
+      const int i = t + NT * j;
       if (i < L) buf[pad16(i)] = (i < M) ? cmul(r[j], __ldg(&tb.chirp[i])) : float2{0, 0};
     }
-    for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+    for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
     fft_convolve(buf, logL, q, logL, [&](int p) { return __ldg(&tb.chat_br[p]); }, pt);
     const float invM = 1.0f / (float)M;
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
-      const int k = t + kRegThreads * j;
+      const int k = t + NT * j;
       if (k < M) {
         float2 d = lam;
         d.x += __ldg(&tb.seig[k]);
@@ -218,7 +220,7 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
         buf[pad16(k)] = float2{0, 0};
       }
     }
-    for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+    for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
     fft_convolve(buf, logL, q, logL, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); }, pt);
   } else {
     if (t == 0) {
@@ -227,7 +229,7 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
     }
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + kRegThreads * j;
+      const int i = t + NT * j;
       if (i < M) {
         buf[pad16(i + 1)] = r[j];
         buf[pad16(L - 1 - i)] = float2{-r[j].x, -r[j].y};
@@ -244,8 +246,8 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
   }
 }
 
-template <int KIND, bool WARM>
-__global__ void __launch_bounds__(kRegThreads, 1)
+template <int KIND, bool WARM, int NT>
+__global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     cocg_reg_kernel(float2* __restrict__ xb, const float2* __restrict__ x0b, int M, int logL, int nsys,
                     CocgTables32 tb, float tol, int maxit, int* __restrict__ iters, int* __restrict__ flags) {
   extern __shared__ unsigned char smraw[];
@@ -266,14 +268,14 @@ __global__ void __launch_bounds__(kRegThreads, 1)
     float nb2[1] = {0};
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + kRegThreads * j;
+      const int i = t + NT * j;
       r[j] = (i < M) ? x[i] : float2{0, 0};
       nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
     }
     block_sum<float, 1>(nb2, red);
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + kRegThreads * j;
+      const int i = t + NT * j;
       if (i < M) x[i] = float2{0, 0};
     }
     if (nb2[0] == 0.0f) {
@@ -288,16 +290,16 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       float2 w[kRegElems];
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         w[j] = (i < M) ? x0[i] : float2{0, 0};
         if (i < L) buf[pad16(i)] = w[j];
       }
-      for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+      for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
       fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
       float r02[1] = {0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         if (i < M) {
           const float2 rj = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
           r02[0] += rj.x * rj.x + rj.y * rj.y;
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         accepted = 1;
 #pragma unroll
         for (int j = 0; j < kRegElems; ++j) {
-          const int i = t + kRegThreads * j;
+          const int i = t + NT * j;
           if (i < M) {
             r[j] = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
             x[i] = w[j];
@@ -323,11 +325,11 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       __syncthreads();
     }
     // z = P^{-1} r, p = z, rho = r^T z
-    precond_reg<KIND>(buf, r, M, logL, lam, tb, q, pt);
+    precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt);
     float rho2[2] = {0, 0};
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + kRegThreads * j;
+      const int i = t + NT * j;
       float2 z{0, 0};
       if (i < M) z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
       p[j] = z;
@@ -341,15 +343,15 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       // q = (lambda I + c T) p
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         if (i < L) buf[pad16(i)] = (i < M) ? p[j] : float2{0, 0};
       }
-      for (int i = t + kRegThreads * kRegElems; i < L; i += kRegThreads) buf[pad16(i)] = float2{0, 0};
+      for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
       fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
       float pq2[2] = {0, 0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         if (i < M) {
           const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
           pq2[0] += p[j].x * qq.x - p[j].y * qq.y;
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       float rr[1] = {0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         if (i < M) {
           const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
           x[i] = cadd(x[i], cmul(a, p[j]));
@@ -375,11 +377,11 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       ++it;
       if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
       if (rr[0] <= thr) { flag = 0; break; }
-      precond_reg<KIND>(buf, r, M, logL, lam, tb, q, pt);
+      precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt);
       float rn2[2] = {0, 0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         if (i < M) {
           const float2 z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
           rn2[0] += r[j].x * z.x - r[j].y * z.y;
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
       rho = rho_new;
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + kRegThreads * j;
+        const int i = t + NT * j;
         float2 z{0, 0};
         if (i < M) z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
         p[j] = cadd(z, cmul(beta, p[j]));
@@ -430,20 +432,58 @@ static cudaError_t launch_k(typename cplx_t<R>::type* xb, typename cplx_t<R>::ty
   return cudaGetLastError();
 }
 
+template <int NT>
+static cudaError_t launch_reg(float2* xb, int M, int logL, int nsys, int inner, const CocgTables32& tb, float tol,
+                              int maxit, int* iters, int* flags, int grid, cudaStream_t s, const float2* x0) {
+  const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
+                      (size_t)pass_table_size(logL) * sizeof(float2);
+  auto kern = x0 ? (inner == 0 ? cocg_reg_kernel<0, true, NT> : cocg_reg_kernel<1, true, NT>)
+                 : (inner == 0 ? cocg_reg_kernel<0, false, NT> : cocg_reg_kernel<1, false, NT>);
+  cudaError_t e = allow_max_dynamic_smem(kern);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, NT, smem, s>>>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags);
+  return cudaGetLastError();
+}
+
+// Deterministic test right-hand sides in [-1, 1)^2 for the autotuner (a 32-bit integer hash).
+__global__ void fill_test_rhs_kernel(float2* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    unsigned h = (unsigned)i * 2654435761u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const float a = (float)(h & 0xffffu) / 32768.0f - 1.0f, b = (float)(h >> 16) / 32768.0f - 1.0f;
+    x[i] = float2{a, b};
+  }
+}
+
+cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s) {
+  fill_test_rhs_kernel<<<152 * 4, 256, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+int cocg_reg_min_threads(int M) {
+  int nt = 64;
+  while (nt * kRegElems < M) nt *= 2;
+  return nt <= kRegMaxThreads ? nt : 0;
+}
+
 cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys, int inner,
                             const CocgTables32& tb, float tol, int maxit, int* iters, int* flags, int grid,
-                            cudaStream_t s, const float2* x0) {
-  if (x0 && M > kRegThreads * kRegElems) return cudaErrorInvalidValue;
-  if (M <= kRegThreads * kRegElems) {
-    const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
-                        (size_t)pass_table_size(logL) * sizeof(float2);
-    auto kern = x0 ? (inner == 0 ? cocg_reg_kernel<0, true> : cocg_reg_kernel<1, true>)
-                   : (inner == 0 ? cocg_reg_kernel<0, false> : cocg_reg_kernel<1, false>);
-    cudaError_t e = allow_max_dynamic_smem(kern);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kRegThreads, smem, s>>>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags);
-    return cudaGetLastError();
+                            cudaStream_t s, const float2* x0, int threads) {
+  const int nt_min = cocg_reg_min_threads(M);
+  if (nt_min) {
+    const int nt = threads ? threads : kRegMaxThreads;
+    if (nt < nt_min || nt > kRegMaxThreads) return cudaErrorInvalidValue;
+    switch (nt) {
+      case 64: return launch_reg<64>(xb, M, logL, nsys, inner, tb, tol, maxit, iters, flags, grid, s, x0);
+      case 128: return launch_reg<128>(xb, M, logL, nsys, inner, tb, tol, maxit, iters, flags, grid, s, x0);
+      case 256: return launch_reg<256>(xb, M, logL, nsys, inner, tb, tol, maxit, iters, flags, grid, s, x0);
+      case 512: return launch_reg<512>(xb, M, logL, nsys, inner, tb, tol, maxit, iters, flags, grid, s, x0);
+      default: return cudaErrorInvalidValue;
+    }
   }
+  if (x0) return cudaErrorInvalidValue;
   if (inner == 0)
     return launch_k<float, 0, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
   return launch_k<float, 1, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);

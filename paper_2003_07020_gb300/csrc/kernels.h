@@ -62,11 +62,18 @@ struct CocgTables64 {
 // starts from x0[n] only if ||b - A x0[n]|| < ||b||, and then flags[n] |= 4.
 cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int logL, int nsys,
                             int inner, const CocgTables32& tb, float tol, int maxit, int* iters,
-                            int* flags, int grid, cudaStream_t s, const float2* x0 = nullptr);
+                            int* flags, int grid, cudaStream_t s, const float2* x0 = nullptr,
+                            int threads = 0);
+// Smallest CTA size (64 .. 512) of the register-resident FP32 COCG kernel for M, or 0 when
+// M > 8192 (the shared-memory kernel is used); `threads` of launch_cocg_f32 may be any power
+// of two from this value to 512 (0: 512).
 cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gbuf, int M, int logL,
                             int nsys, int inner, const CocgTables64& tb, double tol, int maxit,
                             int* iters, int* flags, int grid, cudaStream_t s);
 size_t cocg_gbuf_elems_f64(int logL, int grid);
+int cocg_reg_min_threads(int M);
+// x[i] = deterministic pseudo-random values in [-1, 1)^2 (autotuner inputs)
+cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s);
 
 // ---- 2D problem, twod.cu ----------------------------------------------------------------
 // w = calA v (or rhs - calA v) for K = I (x) K_x + K_y (x) I (x fastest); tmp: n doubles of scratch;

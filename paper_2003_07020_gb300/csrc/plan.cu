@@ -6,6 +6,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -223,6 +227,7 @@ struct aao_plan {
   void* pws = nullptr;
   double2* gbuf = nullptr;
   int cocg_grid = 0;
+  int cocg_threads = 0;  // CTA size of the register-resident FP32 COCG kernel (0: not used)
   int* iters = nullptr;
   int* flags = nullptr;
   int* stats = nullptr;
@@ -444,7 +449,7 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
       LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
                                               (int)p->opts.inner, tb, (float)p->opts.inner_tol, p->opts.inner_maxit,
                                               p->iters, p->flags, p->cocg_grid, p->stream,
-                                              p->fno ? p->x0buf : nullptr));
+                                              p->fno ? p->x0buf : nullptr, p->cocg_threads));
       if (nrec > 0) {
         CK(cudaMemcpyAsync(p->rec_x + p->rec_count * p->M, spec, nrec * p->M * sizeof(float2),
                            cudaMemcpyDeviceToDevice, p->stream));
@@ -608,6 +613,67 @@ aao_status build_cycle_graph(aao_plan* p) {
   return AAO_OK;
 }
 
+// Autotuner of the Step (b) launch shape: times every admissible CTA size of the
+// register-resident COCG kernel on the plan's own shifted systems (deterministic test
+// right-hand sides, tol 0, a fixed 4 iterations, so every candidate does the same work)
+// and keeps the fastest.  Results are cached per (device, M, L, inner, systems).
+aao_status autotune_cocg_threads(aao_plan* p) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, int> cache;
+  const int nt_min = aao::cocg_reg_min_threads(p->M);
+  if (nt_min == 0) return AAO_OK;
+  if (nt_min == 512) {
+    p->cocg_threads = 512;
+    return AAO_OK;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, p->M, p->logL, (int)p->opts.inner, p->nsys);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      p->cocg_threads = it->second;
+      return AAO_OK;
+    }
+  }
+  aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
+  float2* spec = (float2*)p->spec;
+  const size_t ns = (size_t)p->nsys * p->M;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(p, AAO_ECUDA, "cudaEventCreate failed");
+  }
+  int best = 512;
+  float best_ms = 1e30f;
+  cudaError_t e = cudaSuccess;
+  for (int nt = nt_min; nt <= 512 && e == cudaSuccess; nt *= 2) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // rep 0 warms up
+      e = aao::launch_fill_test_rhs(spec, ns, p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+      if (e == cudaSuccess)
+        e = aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys, (int)p->opts.inner,
+                                 tb, 0.0f, 4, p->iters, p->flags, p->cocg_grid, p->stream, nullptr, nt);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess && rep == 1 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = nt;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("COCG autotuning: ") + cudaGetErrorString(e));
+  p->cocg_threads = best;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = best;
+  return AAO_OK;
+}
+
 aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (!prob || !o) return fail(nullptr, AAO_EINVAL, "null problem or options");
   if (prob->dim != 1 && prob->dim != 2) return fail(nullptr, AAO_EINVAL, "dim must be 1 or 2");
@@ -631,6 +697,12 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (o->inner == AAO_INNER_TAU && ((prob->M + 1) & prob->M))
     return fail(nullptr, AAO_EINVAL, "the tau preconditioner needs M+1 to be a power of two");
   if (o->use_graphs != 0 && o->use_graphs != 1) return fail(nullptr, AAO_EINVAL, "use_graphs must be 0 or 1");
+  if (o->cocg_threads != 0 && o->cocg_threads != 64 && o->cocg_threads != 128 && o->cocg_threads != 256 &&
+      o->cocg_threads != 512)
+    return fail(nullptr, AAO_EINVAL, "cocg_threads must be 0, 64, 128, 256 or 512");
+  if (o->cocg_threads != 0 && o->prec == AAO_PREC_MIXED && prob->dim == 1 &&
+      o->cocg_threads < aao::cocg_reg_min_threads((int)prob->M))
+    return fail(nullptr, AAO_EINVAL, "cocg_threads must be at least M / 16");
   return AAO_OK;
 }
 
@@ -703,6 +775,7 @@ void aao_default_opts(aao_opts* o, aao_precision prec) {
   o->prec = prec;
   o->inner = AAO_INNER_STRANG;
   o->use_graphs = 1;
+  o->cocg_threads = 0;
 }
 
 aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host) {
@@ -871,8 +944,20 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->err = "cudaMallocHost failed";
     return bail(AAO_ENOMEM);
   }
+  if (p->mixed && p->dim == 1 && aao::cocg_reg_min_threads(p->M) > 0) {
+    if (opts->cocg_threads)
+      p->cocg_threads = opts->cocg_threads;
+    else
+      TRYP(autotune_cocg_threads(p));
+  }
 #undef TRYP
   *out = p;
+  return AAO_OK;
+}
+
+aao_status aao_plan_get_tuning(const aao_plan* p, int* cocg_threads) {
+  if (!p || !cocg_threads) return fail(nullptr, AAO_EINVAL, "null argument");
+  *cocg_threads = p->cocg_threads;
   return AAO_OK;
 }
 

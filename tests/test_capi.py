@@ -108,3 +108,12 @@ def test_fno_and_warm_start_calls_validate_without_gpu(lib):
     assert lib.aao_plan_record_pairs(None, 0, None, None, None) == aao.AAO_EINVAL
     n = ctypes.c_int64(-1)
     assert lib.aao_plan_recorded_pairs(None, ctypes.byref(n)) == aao.AAO_EINVAL
+
+
+def test_plan_create_validates_launch_options_without_gpu(lib):
+    prob = aao.AaoProblem(1, 2047, 64, 1.0, 1.5, 1.0, 0.0, 0, 1.5, 1.0)
+    h = ctypes.c_void_p()
+    for kw in (dict(cocg_threads=100), dict(cocg_threads=64), dict(use_graphs=2)):
+        o = aao.default_opts(**kw)
+        assert lib.aao_plan_create(ctypes.byref(prob), ctypes.byref(o), None, ctypes.byref(h)) == aao.AAO_EINVAL, kw
+    assert lib.aao_plan_get_tuning(None, None) == aao.AAO_EINVAL
