@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libaao.so")
 AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOCONV, AAO_EBREAKDOWN, AAO_ENONFINITE = range(7)
 AAO_PREC_FP64, AAO_PREC_MIXED = 0, 1
 AAO_INNER_STRANG, AAO_INNER_TAU = 0, 1
+AAO_MATVEC_FFT64, AAO_MATVEC_NTT = 0, 1
 STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4: "AAO_ENOCONV",
                 5: "AAO_EBREAKDOWN", 6: "AAO_ENONFINITE"}
 
@@ -41,7 +42,8 @@ class AaoProblem(ctypes.Structure):
 class AaoOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner", ctypes.c_int), ("use_graphs", ctypes.c_int), ("cocg_threads", ctypes.c_int)]
+                ("inner", ctypes.c_int), ("use_graphs", ctypes.c_int), ("matvec", ctypes.c_int),
+                ("cocg_threads", ctypes.c_int)]
 
 
 class AaoInfo(ctypes.Structure):

@@ -195,12 +195,23 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
 constexpr int kRegMaxThreads = 512;
 constexpr int kRegElems = 16;
 
+// KIND 0: Strang by Bluestein (4 FFTs of L); 1: natural tau matrix by DST-I (2 FFTs); 2: Strang by
+// the precomputed per-system circulant spectrum sc (2 FFTs).  The result is read by zval().
 template <int KIND, int NT>
 __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegElems], int M, int logL, float2 lam,
-                                            const CocgTables32& tb, const float2* q, const float2* pt) {
+                                            const CocgTables32& tb, const float2* q, const float2* pt,
+                                            const float2* __restrict__ sc) {
   const int L = 1 << logL;
   const int t = threadIdx.x;
-  if (KIND == 0) {
+  if constexpr (KIND == 2) {
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < L) buf[pad16(i)] = (i < M) ? r[j] : float2{0, 0};
+    }
+    for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+    fft_convolve(buf, logL, q, logL, [&](int p) { return __ldg(&sc[p]); }, pt);
+  } else if constexpr (KIND == 0) {
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
@@ -223,6 +234,7 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
     for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
     fft_convolve(buf, logL, q, logL, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); }, pt);
   } else {
+    (void)sc;
     if (t == 0) {
       buf[pad16(0)] = float2{0, 0};
       buf[pad16(M + 1)] = float2{0, 0};
@@ -246,6 +258,14 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
   }
 }
 
+// Element i of the preconditioned residual left in buf by precond_reg<KIND>.
+template <int KIND>
+__device__ __forceinline__ float2 zval(const float2* buf, const CocgTables32& tb, int i) {
+  if constexpr (KIND == 0) return cmulc(buf[pad16(i)], __ldg(&tb.chirp[i]));
+  else if constexpr (KIND == 1) return buf[pad16(i + 1)];
+  else return buf[pad16(i)];
+}
+
 template <int KIND, bool WARM, int NT>
 __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     cocg_reg_kernel(float2* __restrict__ xb, const float2* __restrict__ x0b, int M, int logL, int nsys,
@@ -264,6 +284,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     const double2 lamd = tb.lambda[n];
     const float2 lam{(float)lamd.x, (float)lamd.y};
     float2* x = xb + (size_t)n * M;
+    const float2* sc = KIND == 2 ? tb.sconv + ((size_t)n << logL) : nullptr;
     float2 r[kRegElems], p[kRegElems];
     float nb2[1] = {0};
 #pragma unroll
@@ -325,13 +346,13 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       __syncthreads();
     }
     // z = P^{-1} r, p = z, rho = r^T z
-    precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt);
+    precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
     float rho2[2] = {0, 0};
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
       float2 z{0, 0};
-      if (i < M) z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
+      if (i < M) z = zval<KIND>(buf, tb, i);
       p[j] = z;
       rho2[0] += r[j].x * z.x - r[j].y * z.y;
       rho2[1] += r[j].x * z.y + r[j].y * z.x;
@@ -377,13 +398,13 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       ++it;
       if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
       if (rr[0] <= thr) { flag = 0; break; }
-      precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt);
+      precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
       float rn2[2] = {0, 0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
         const int i = t + NT * j;
         if (i < M) {
-          const float2 z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
+          const float2 z = zval<KIND>(buf, tb, i);
           rn2[0] += r[j].x * z.x - r[j].y * z.y;
           rn2[1] += r[j].x * z.y + r[j].y * z.x;
         }
@@ -397,7 +418,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       for (int j = 0; j < kRegElems; ++j) {
         const int i = t + NT * j;
         float2 z{0, 0};
-        if (i < M) z = KIND == 0 ? cmulc(buf[pad16(i)], __ldg(&tb.chirp[i])) : buf[pad16(i + 1)];
+        if (i < M) z = zval<KIND>(buf, tb, i);
         p[j] = cadd(z, cmul(beta, p[j]));
       }
       __syncthreads();
@@ -437,11 +458,70 @@ static cudaError_t launch_reg(float2* xb, int M, int logL, int nsys, int inner, 
                               int maxit, int* iters, int* flags, int grid, cudaStream_t s, const float2* x0) {
   const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
                       (size_t)pass_table_size(logL) * sizeof(float2);
-  auto kern = x0 ? (inner == 0 ? cocg_reg_kernel<0, true, NT> : cocg_reg_kernel<1, true, NT>)
-                 : (inner == 0 ? cocg_reg_kernel<0, false, NT> : cocg_reg_kernel<1, false, NT>);
+  const int kind = inner == 1 ? 1 : (tb.sconv ? 2 : 0);
+  auto kern = x0 ? (kind == 0 ? cocg_reg_kernel<0, true, NT>
+                              : (kind == 1 ? cocg_reg_kernel<1, true, NT> : cocg_reg_kernel<2, true, NT>))
+                 : (kind == 0 ? cocg_reg_kernel<0, false, NT>
+                              : (kind == 1 ? cocg_reg_kernel<1, false, NT> : cocg_reg_kernel<2, false, NT>));
   cudaError_t e = allow_max_dynamic_smem(kern);
   if (e != cudaSuccess) return e;
   kern<<<grid, NT, smem, s>>>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags);
+  return cudaGetLastError();
+}
+
+// Per-system spectra of the Strang inverse as an L-point circulant (see launch_strang_conv_setup).
+__global__ void __launch_bounds__(kRegMaxThreads, 1)
+    strang_conv_kernel(int M, int logL, int nsys, CocgTables32 tb, float2* __restrict__ out) {
+  constexpr int NT = kRegMaxThreads;
+  extern __shared__ unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* q = buf + padded_size(1 << logL);
+  float2* pt = q + (1 << logL) / 4;
+  const int L = 1 << logL;
+  const int t = threadIdx.x;
+  load_quarter(q, tb.twL, L / 4);
+  __syncthreads();
+  build_pass_tables(pt, q, logL, logL);
+  const float invL = 1.0f / (float)L;
+  for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
+    const double2 lamd = tb.lambda[n];
+    const float2 lam{(float)lamd.x, (float)lamd.y};
+    float2 r[kRegElems];
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) r[j] = (t == 0 && j == 0) ? float2{1, 0} : float2{0, 0};
+    precond_reg<0, NT>(buf, r, M, logL, lam, tb, q, pt, nullptr);  // h = (lambda I + c S)^{-1} e_0
+    float2 h[kRegElems];
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      h[j] = i < M ? zval<0>(buf, tb, i) : float2{0, 0};
+    }
+    __syncthreads();
+    for (int i = t; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) {
+        buf[pad16(i)] = h[j];                          // g_i = h_i
+        if (i >= 1) buf[pad16(L - M + i)] = h[j];      // g_{L-d} = h_{M-d}, d = M - i
+      }
+    }
+    fft_forward_fused(buf, logL, q, logL, pt);
+    float2* o = out + ((size_t)n << logL);
+    for (int p = t; p < L; p += NT) o[p] = cscale(buf[pad16(p)], invL);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_strang_conv_setup(int M, int logL, int nsys, const CocgTables32& tb, float2* out,
+                                     cudaStream_t s) {
+  if (M > kRegMaxThreads * kRegElems) return cudaErrorInvalidValue;
+  const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) +
+                      (size_t)pass_table_size(logL) * sizeof(float2);
+  cudaError_t e = allow_max_dynamic_smem(strang_conv_kernel);
+  if (e != cudaSuccess) return e;
+  strang_conv_kernel<<<nsys, kRegMaxThreads, smem, s>>>(M, logL, nsys, tb, out);
   return cudaGetLastError();
 }
 

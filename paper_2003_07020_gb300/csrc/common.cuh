@@ -449,6 +449,50 @@ __device__ void fft_convolve(T* buf, int logN, const T* q, int logNq, F factor, 
   }
 }
 
+// Last forward pass of fft_forward_fused: the 2^r-point DFT of each group, stored in fused order.
+template <typename T, int r>
+__device__ __forceinline__ void fused_last_pass(T* buf, int logN) {
+  constexpr int R = 1 << r;
+  const int per = 1 << (logN - r);
+  for (int g = threadIdx.x; g < per; g += blockDim.x) {
+    const int start = g << r;
+    T v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = buf[pad16(start + k)];
+    dft<-1, r>(v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) buf[pad16(start + k)] = v[k];
+  }
+}
+
+// Forward DFT (sign -1) of one transform with the output left in the fused order that
+// fft_convolve's factor(pf) uses: buf[pad16(pf)] = spectrum at fused index pf.  Starts and
+// ends with __syncthreads().
+template <typename T>
+__device__ void fft_forward_fused(T* buf, int logN, const T* q, int logNq, const T* pt = nullptr) {
+  __syncthreads();
+  const int r0 = first_pass_stages(logN);
+  int s0 = 0, r = r0, off = 0;
+  while (s0 + r < logN) {
+    if (s0 == 0) {
+      dif_pass_any<T>(r, buf, logN, 0, 1, 0, q, logNq);
+    } else {
+      dif_pass<T, 4>(buf, logN, s0, 1, 0, q, logNq, pt ? pt + off : nullptr);
+      off += 15 * (1 << (logN - s0 - 4));
+    }
+    __syncthreads();
+    s0 += r;
+    r = 4;
+  }
+  switch (logN - s0) {
+    case 1: fused_last_pass<T, 1>(buf, logN); break;
+    case 2: fused_last_pass<T, 2>(buf, logN); break;
+    case 3: fused_last_pass<T, 3>(buf, logN); break;
+    default: fused_last_pass<T, 4>(buf, logN); break;
+  }
+  __syncthreads();
+}
+
 // Copies the quarter twiddle table (n4 entries) from global to shared memory.
 template <typename T>
 __device__ __forceinline__ void load_quarter(T* dst, const T* __restrict__ src, int n4) {

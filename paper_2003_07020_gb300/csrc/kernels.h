@@ -44,6 +44,9 @@ struct CocgTables32 {
   const float2* chat_br;  // Strang: DFT_L(conj chirp filter)/L, fused-pass order
   const float* seig;      // Strang: c * eigenvalues of S
   const float* taueig_br; // tau: c * sigma_f, fused-pass order (1e30 where the DST multiplier vanishes)
+  // Strang, optional: per system n, the fused-order spectrum (/L) of the length-L circulant whose
+  // first M outputs apply (lambda_n I + c S)^{-1} exactly ([nsys][L]); null: Bluestein at run time
+  const float2* sconv;
 };
 struct CocgTables64 {
   const double2* twL;
@@ -64,6 +67,11 @@ cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int log
                             int inner, const CocgTables32& tb, float tol, int maxit, int* iters,
                             int* flags, int grid, cudaStream_t s, const float2* x0 = nullptr,
                             int threads = 0);
+// Builds CocgTables32::sconv (out: [nsys][L] complex) for M <= 8192: the first column h of
+// (lambda_n I + c S)^{-1} by the Bluestein preconditioner applied to e_0, wrapped into the
+// length-L circulant g (g_d = h_d, g_{L-d} = h_{M-d}), transformed to fused order and divided by L.
+cudaError_t launch_strang_conv_setup(int M, int logL, int nsys, const CocgTables32& tb, float2* out,
+                                     cudaStream_t s);
 // Smallest CTA size (64 .. 512) of the register-resident FP32 COCG kernel for M, or 0 when
 // M > 8192 (the shared-memory kernel is used); `threads` of launch_cocg_f32 may be any power
 // of two from this value to 512 (0: 512).
@@ -74,6 +82,24 @@ size_t cocg_gbuf_elems_f64(int logL, int grid);
 int cocg_reg_min_threads(int M);
 // x[i] = deterministic pseudo-random values in [-1, 1)^2 (autotuner inputs)
 cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s);
+
+// ---- exact-integer matvec (NTT), ntt.cu ---------------------------------------------
+// Four primes p < 2^30 with 2^21 | p - 1 (product ~2^119.5) and a primitive root of each.
+constexpr uint32_t kNttPrime[4] = {1004535809u, 998244353u, 985661441u, 943718401u};
+constexpr uint32_t kNttGen[4] = {3u, 3u, 3u, 7u};
+struct NttTables {
+  const uint2* twf;     // [4][L/2] (w^e, floor(w^e 2^32 / p))
+  const uint2* twi;     // [4][L/2] inverse roots
+  const uint2* ghat;    // [4][L] stencil spectrum, bit-reversed, times L^-1
+  uint32_t crt[6];      // p0^-1 mod p1, p0^-1 mod p2, p1^-1 mod p2, p0^-1 mod p3, p1^-1 mod p3, p2^-1 mod p3
+  double c_gscale;      // c 2^(e_g - 51)
+};
+// w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the quantised row
+// (same contract as launch_matvec_f64).  res: 4 n uint32 scratch; rowscale: Nt doubles.
+cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
+                              int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
+cudaError_t launch_matvec_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
+                                  int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
 
 // ---- 2D problem, twod.cu ----------------------------------------------------------------
 // w = calA v (or rhs - calA v) for K = I (x) K_x + K_y (x) I (x fastest); tmp: n doubles of scratch;

@@ -228,6 +228,12 @@ struct aao_plan {
   double2* gbuf = nullptr;
   int cocg_grid = 0;
   int cocg_threads = 0;  // CTA size of the register-resident FP32 COCG kernel (0: not used)
+  float2* sconv = nullptr;  // mixed Strang: per-system spectra of (lambda_n I + c S)^{-1} as L-point circulants
+  // exact-integer matvec (opts.matvec == AAO_MATVEC_NTT, 1D)
+  bool ntt = false;
+  aao::NttTables ntt_tab{};
+  uint32_t* ntt_res = nullptr;  // 4 n residues
+  double* ntt_rowscale = nullptr;
   int* iters = nullptr;
   int* flags = nullptr;
   int* stats = nullptr;
@@ -374,6 +380,15 @@ aao_status matvec_any(aao_plan* p, const void* v, bool v_is_f32, const double* r
                                                     p->stream));
     return AAO_OK;
   }
+  if (p->ntt) {
+    if (v_is_f32)
+      LAUNCH(ST_MATVEC, 2, aao::launch_matvec_ntt_fin((const float*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->ntt_tab,
+                                                      p->ntt_res, p->ntt_rowscale, p->stream));
+    else
+      LAUNCH(ST_MATVEC, 2, aao::launch_matvec_ntt((const double*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->ntt_tab,
+                                                  p->ntt_res, p->ntt_rowscale, p->stream));
+    return AAO_OK;
+  }
   if (v_is_f32)
     LAUNCH(ST_MATVEC, 1, aao::launch_matvec_f64_fin((const float*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->Ehalf,
                                                     p->twL64, p->stream));
@@ -432,7 +447,7 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
     if (p->dim == 2) {
       TRY(cocg2d_any<float>(p, spec));
     } else {
-      aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
+      aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32, p->sconv};
       const int64_t nrec = std::min<int64_t>(p->nsys, p->rec_cap - p->rec_count);
       if (nrec > 0) {
         CK(cudaMemcpyAsync(p->rec_b + p->rec_count * p->M, spec, nrec * p->M * sizeof(float2),
@@ -637,7 +652,7 @@ aao_status autotune_cocg_threads(aao_plan* p) {
       return AAO_OK;
     }
   }
-  aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32};
+  aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32, p->sconv};
   float2* spec = (float2*)p->spec;
   const size_t ns = (size_t)p->nsys * p->M;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -697,6 +712,7 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (o->inner == AAO_INNER_TAU && ((prob->M + 1) & prob->M))
     return fail(nullptr, AAO_EINVAL, "the tau preconditioner needs M+1 to be a power of two");
   if (o->use_graphs != 0 && o->use_graphs != 1) return fail(nullptr, AAO_EINVAL, "use_graphs must be 0 or 1");
+  if (o->matvec != AAO_MATVEC_FFT64 && o->matvec != AAO_MATVEC_NTT) return fail(nullptr, AAO_EINVAL, "bad matvec");
   if (o->cocg_threads != 0 && o->cocg_threads != 64 && o->cocg_threads != 128 && o->cocg_threads != 256 &&
       o->cocg_threads != 512)
     return fail(nullptr, AAO_EINVAL, "cocg_threads must be 0, 64, 128, 256 or 512");
@@ -775,6 +791,7 @@ void aao_default_opts(aao_opts* o, aao_precision prec) {
   o->prec = prec;
   o->inner = AAO_INNER_STRANG;
   o->use_graphs = 1;
+  o->matvec = AAO_MATVEC_FFT64;
   o->cocg_threads = 0;
 }
 
@@ -873,6 +890,21 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   }
   const size_t n = p->n;
   const size_t csz = p->mixed ? sizeof(float2) : sizeof(double2);
+  if (p->dim == 1 && opts->matvec == AAO_MATVEC_NTT) {
+    aao::build_ntt_tables(p->ht);
+    uint32_t* q32;
+    TRYP(upload(p, &q32, p->ht.ntt_twf));
+    p->ntt_tab.twf = (const uint2*)q32;
+    TRYP(upload(p, &q32, p->ht.ntt_twi));
+    p->ntt_tab.twi = (const uint2*)q32;
+    TRYP(upload(p, &q32, p->ht.ntt_ghat));
+    p->ntt_tab.ghat = (const uint2*)q32;
+    for (int i = 0; i < 6; ++i) p->ntt_tab.crt[i] = p->ht.ntt_crt[i];
+    p->ntt_tab.c_gscale = p->ht.ntt_c_gscale;
+    TRYP(dalloc(p, &p->ntt_res, 4 * n));
+    TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));
+    p->ntt = true;
+  }
   TRYP(dalloc(p, &p->V, (size_t)(p->m + 1) * n));
   {
     void* z = nullptr;
@@ -943,6 +975,18 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->host_count = nullptr;
     p->err = "cudaMallocHost failed";
     return bail(AAO_ENOMEM);
+  }
+  if (p->mixed && p->dim == 1 && opts->inner == AAO_INNER_STRANG && aao::cocg_reg_min_threads(p->M) > 0) {
+    // the Strang preconditioner of every shifted system as one L-point circulant (2 FFTs per
+    // application instead of Bluestein's 4), built once by the Bluestein form itself
+    TRYP(dalloc(p, &p->sconv, (size_t)p->nsys << p->logL));
+    aao::CocgTables32 tb{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32, nullptr};
+    cudaError_t e = aao::launch_strang_conv_setup(p->M, p->logL, p->nsys, tb, p->sconv, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+      p->err = std::string("Strang spectra: ") + cudaGetErrorString(e);
+      return bail(AAO_ECUDA);
+    }
   }
   if (p->mixed && p->dim == 1 && aao::cocg_reg_min_threads(p->M) > 0) {
     if (opts->cocg_threads)

@@ -6,6 +6,10 @@
 // and the tau-matrix of Sec. 3.2 (here in its natural T - H(T) form).
 #include "setup.h"
 
+#include <utility>
+
+#include "kernels.h"
+
 #include <cmath>
 
 namespace aao {
@@ -191,3 +195,97 @@ extern "C" int aao_setup_coeffs_impl(double alpha, int64_t n, double* g) {
   aao::fcd_weights_recurrence(alpha, n, g);
   return 0;
 }
+
+// ---- exact-integer matvec tables -------------------------------------------------------------
+namespace aao {
+namespace {
+
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p) { return (a * b) % p; }  // a, b < 2^30
+uint64_t powmod(uint64_t b, uint64_t e, uint64_t p) {
+  uint64_t r = 1;
+  b %= p;
+  while (e) {
+    if (e & 1) r = mulmod(r, b, p);
+    b = mulmod(b, b, p);
+    e >>= 1;
+  }
+  return r;
+}
+uint32_t shoup(uint64_t w, uint64_t p) { return (uint32_t)((w << 32) / p); }
+
+// In-place cyclic NTT A_k = sum_j a_j w^{jk} (natural order in and out), radix 2.
+void host_ntt(std::vector<uint64_t>& a, uint64_t p, uint64_t w) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const uint64_t wl = powmod(w, n / len, p);
+    for (size_t i = 0; i < n; i += len) {
+      uint64_t wj = 1;
+      for (size_t j = 0; j < len / 2; ++j) {
+        const uint64_t u = a[i + j], v = mulmod(a[i + j + len / 2], wj, p);
+        a[i + j] = (u + v) % p;
+        a[i + j + len / 2] = (u + p - v) % p;
+        wj = mulmod(wj, wl, p);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void build_ntt_tables(HostTables& t) {
+  const int64_t L = t.L, M = t.M;
+  const int logL = t.logL;
+  // quantised stencil: G_j = round(g_j 2^(51 - e_g)), g_0 = max |g_j| < 2^e_g
+  int eg = 0;
+  std::frexp(t.g[0], &eg);
+  std::vector<int64_t> G((size_t)M);
+  for (int64_t j = 0; j < M; ++j) G[j] = std::llround(std::ldexp(t.g[j], 51 - eg));
+  t.ntt_c_gscale = t.c * std::ldexp(1.0, eg - 51);
+  t.ntt_twf.assign((size_t)4 * (L / 2) * 2, 0);
+  t.ntt_twi.assign((size_t)4 * (L / 2) * 2, 0);
+  t.ntt_ghat.assign((size_t)4 * L * 2, 0);
+  for (int q = 0; q < 4; ++q) {
+    const uint64_t p = kNttPrime[q];
+    const uint64_t w = powmod(kNttGen[q], (p - 1) / (uint64_t)L, p), wi = powmod(w, p - 2, p);
+    uint64_t a = 1, b = 1;
+    for (int64_t e = 0; e < L / 2; ++e) {
+      const size_t o = ((size_t)q * (L / 2) + e) * 2;
+      t.ntt_twf[o] = (uint32_t)a;
+      t.ntt_twf[o + 1] = shoup(a, p);
+      t.ntt_twi[o] = (uint32_t)b;
+      t.ntt_twi[o + 1] = shoup(b, p);
+      a = mulmod(a, w, p);
+      b = mulmod(b, wi, p);
+    }
+    // circulant embedding of the stencil: c_0 = G_0, c_j = c_{L-j} = G_j (1 <= j < M)
+    std::vector<uint64_t> c((size_t)L, 0);
+    auto res = [&](int64_t x) { int64_t m = x % (int64_t)p; return (uint64_t)(m < 0 ? m + (int64_t)p : m); };
+    c[0] = res(G[0]);
+    for (int64_t j = 1; j < M; ++j) c[j] = c[L - j] = res(G[j]);
+    host_ntt(c, p, w);
+    const uint64_t Linv = powmod((uint64_t)L % p, p - 2, p);
+    for (int64_t k = 0; k < L; ++k) {
+      int64_t r = 0;  // bit reversal of k over logL bits
+      for (int bit = 0; bit < logL; ++bit)
+        if (k & ((int64_t)1 << bit)) r |= (int64_t)1 << (logL - 1 - bit);
+      const uint64_t v = mulmod(c[r], Linv, p);
+      t.ntt_ghat[((size_t)q * L + k) * 2] = (uint32_t)v;
+      t.ntt_ghat[((size_t)q * L + k) * 2 + 1] = shoup(v, p);
+    }
+  }
+  const uint64_t p0 = kNttPrime[0], p1 = kNttPrime[1], p2 = kNttPrime[2], p3 = kNttPrime[3];
+  t.ntt_crt[0] = (uint32_t)powmod(p0 % p1, p1 - 2, p1);
+  t.ntt_crt[1] = (uint32_t)powmod(p0 % p2, p2 - 2, p2);
+  t.ntt_crt[2] = (uint32_t)powmod(p1 % p2, p2 - 2, p2);
+  t.ntt_crt[3] = (uint32_t)powmod(p0 % p3, p3 - 2, p3);
+  t.ntt_crt[4] = (uint32_t)powmod(p1 % p3, p3 - 2, p3);
+  t.ntt_crt[5] = (uint32_t)powmod(p2 % p3, p3 - 2, p3);
+}
+
+}  // namespace aao

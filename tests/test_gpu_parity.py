@@ -51,9 +51,10 @@ def rel(a, b):
 # ---------------------------------------------------------------- matvec
 @pytest.mark.parametrize("M,Nt,alpha", [(63, 64, 1.5), (100, 16, 1.2), (1, 4, 1.5), (2, 8, 1.9),
                                         (1023, 32, 1.8), (4095, 8, 1.3)])
-def test_matvec_matches_dense_oracle(M, Nt, alpha):
+@pytest.mark.parametrize("kind", [aao.AAO_MATVEC_NTT, aao.AAO_MATVEC_FFT64])
+def test_matvec_matches_dense_oracle(M, Nt, alpha, kind):
     v = workloads.random_vector(Nt, M, seed=M + Nt)
-    with aao.Plan(M, Nt, alpha) as plan:
+    with aao.Plan(M, Nt, alpha, matvec=kind) as plan:
         w = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
         plan.matvec(cu(v), w)
         torch.cuda.synchronize()
@@ -61,10 +62,11 @@ def test_matvec_matches_dense_oracle(M, Nt, alpha):
     assert rel(host(w), ref) <= 1e-13
 
 
-def test_matvec_full_size_sampled():
+@pytest.mark.parametrize("kind", [aao.AAO_MATVEC_NTT, aao.AAO_MATVEC_FFT64])
+def test_matvec_full_size_sampled(kind):
     M, Nt, alpha = 8191, 1024, 1.8
     v = workloads.random_vector(Nt, M, seed=7)
-    with aao.Plan(M, Nt, alpha) as plan:
+    with aao.Plan(M, Nt, alpha, matvec=kind) as plan:
         w = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
         plan.matvec(cu(v), w)
         torch.cuda.synchronize()
@@ -236,3 +238,32 @@ def test_iteration_cap_reports_noconv():
         with pytest.raises(aao.AaoError) as e:
             plan.gmres_solve(F, U)
         assert e.value.status == aao.AAO_ENOCONV
+
+
+def test_ntt_matvec_edge_rows():
+    """Exact-integer matvec: zero rows, rows of very different scale (per-row quantisation), a single
+    huge entry, FP32 input (the Z basis), and a non-finite entry that must reach the output."""
+    M, Nt, alpha = 255, 8, 1.7
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((Nt, M))
+    v[1] = 0.0
+    v[2] *= 1e-150
+    v[3] *= 1e100
+    v[4] = 0.0
+    v[4, 17] = 3.0
+    with aao.Plan(M, Nt, alpha, matvec=aao.AAO_MATVEC_NTT) as plan:
+        w = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.matvec(cu(v), w)
+        torch.cuda.synchronize()
+        W = host(w)
+        K = jac(M, alpha)
+        ref = oaao.matvec(K, 1.0 / Nt, v)
+        for k in range(Nt):  # row-wise relative accuracy (the time band mixes rows of different scale)
+            nr = np.linalg.norm(ref[k])
+            assert np.linalg.norm(W[k] - ref[k]) <= 1e-13 * nr + 1e-300, k
+        vbad = v.copy()
+        vbad[5, 3] = np.nan
+        plan.matvec(cu(vbad), w)
+        torch.cuda.synchronize()
+        W = host(w)
+        assert np.isnan(W[5]).all() and np.isfinite(W[:5]).all()
