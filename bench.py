@@ -216,6 +216,12 @@ def peaks():
 # FP64 and FP32 issue rates measured on GB300 by a throughput probe (DFMA and
 # FFMA chains, 152 SMs): ~1.60 DFMA and ~114 FFMA per SM per 2.07 GHz clock.
 FP64_PEAK_TFLOPS = 2 * 1.60 * 152 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) per time row of matvec_f64_kernel at M = 8191 from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, 4 launches of 128 rows each, 17.02 MB per
+# launch; profiles/cocg_reg_matvec_small_full.md); traffic grows with the rows, so a full launch of
+# Nt rows moves Nt times this.
+MATVEC_DRAM_BYTES_PER_ROW_M8191 = 17.018e6 / 128
 FP32_PEAK_TFLOPS = 2 * 114.0 * 152 * 2.07e9 / 1e12
 
 
@@ -390,9 +396,11 @@ def run_ours(args):
         t_launch = prof["matvec"][0] / max(n_mv, 1)  # per matvec (2 kernels in 2D)
         fl = matvec_flops(M, Nt) if args.dim == 1 else matvec2d_flops(M, My, Nt)
         achieved = fl / (t_launch * 1e-3) / 1e12
+        traffic = MATVEC_DRAM_BYTES_PER_ROW_M8191 * Nt if (args.dim == 1 and M == 8191) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "matvec_f64_kernel",
-                "peak_source": "FP64 FMA issue rate x 152 SMs x 2.07 GHz (derived)"}
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "matvec_f64_kernel",
+                "peak_source": "FP64 FMA issue rate x 152 SMs x 2.07 GHz (derived)",
+                "traffic_source": "ncu dram bytes of a 128-row launch scaled to Nt rows" if traffic else None}
     elif dom == "cocg":
         t_launch = prof["cocg"][0] / max(n_apply, 1)  # per preconditioner apply
         fl = (cocg_flops(M, args.inner, inner_sum, n_apply, nsys) if args.dim == 1 else
@@ -613,7 +621,7 @@ def run_learned(args):
         t_launch = prof["fno"][0] / max(n_apply, 1)
         achieved = fno_flops(M, nsys) / (t_launch * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "fno forward (17 kernels)",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "fno forward (12 kernels)",
                 "peak_source": "FFMA issue rate x 152 SMs x 2.07 GHz (derived)"}
     elif pk_dom == "matvec":
         n_mv = sum(i["matvecs"] for i in prof_infos)

@@ -64,81 +64,38 @@ __global__ void k_norms(const float2* __restrict__ b, int M, float* __restrict__
   if (threadIdx.x == 0) norms[s] = sqrtf(red[0]);
 }
 
-__global__ void k_features(const float2* __restrict__ b, const double2* __restrict__ lam,
-                           const float* __restrict__ alpha, const float* __restrict__ norms, int M, int B,
-                           float* __restrict__ feat) {
-  const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= (size_t)B * M) return;
-  const int s = (int)(n / M), i = (int)(n % M);
-  const float inv = norms[s] > 0 ? 1.0f / norms[s] : 0.0f;
-  const float2 v = b[n];
-  float* f = feat + n * FF;
-  f[0] = v.x * inv;
-  f[1] = v.y * inv;
-  f[2] = (float)lam[s].x;
-  f[3] = (float)lam[s].y;
-  f[4] = alpha[s];
-  f[5] = (float)(i + 1) / (float)(M + 1);
-}
-
-// h0[n] = W_lift f[n] + b_lift, one thread per point (32 outputs written as float4)
-__global__ void __launch_bounds__(256) k_lift(const float* __restrict__ feat, const bf16* __restrict__ P, size_t N,
-                                              float* __restrict__ h) {
-  __shared__ float Wl[FC * FF + FC];  // lift W [32][6] then bias
-  for (int q = threadIdx.x; q < FC * FF + FC; q += blockDim.x) Wl[q] = wv(P, OFF_LW + q);
-  __syncthreads();
-  const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  float fv[FF];
-#pragma unroll
-  for (int q = 0; q < FF; ++q) fv[q] = feat[n * FF + q];
-  float4* out = reinterpret_cast<float4*>(h + n * FC);
-#pragma unroll
-  for (int c4 = 0; c4 < FC / 4; ++c4) {
-    float v[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = 4 * c4 + j;
-      float a = Wl[FC * FF + c];
-#pragma unroll
-      for (int q = 0; q < FF; ++q) a = fmaf(Wl[c * FF + q], fv[q], a);
-      v[j] = a;
-    }
-    out[c4] = float4{v[0], v[1], v[2], v[3]};
-  }
-}
-
-// Truncated DFT, the first step of a Fourier layer: per chunk of DT points,
+// Truncated DFT, the first step of a Fourier layer, over tiles of TP = 64 points:
 // part[s][chunk][k][c] = sum_{i in chunk} h[s][i][c] tw[i][k]  (tw[i][k] = e^{-2 pi i ik/M});
-// the chunk partials are summed (in a fixed order) by k_mix.  Warp w takes the
-// points r = w (mod 8) of the chunk for all 16 modes (twiddles read as broadcast
-// float4), then the 8 warp partials are added in shared memory.
-constexpr int DT = 64;
-__global__ void __launch_bounds__(256) k_dft(const float* __restrict__ h, int M, const float2* __restrict__ tw,
-                                             float2* __restrict__ part, int nch) {
-  __shared__ __align__(16) float smem[8 * FK * FC * 2];  // 32 KB: staging, then the warp partials
-  float(*hs)[FC + 1] = reinterpret_cast<float(*)[FC + 1]>(smem);
-  float2(*ts)[FK] = reinterpret_cast<float2(*)[FK]>(smem + DT * (FC + 1));
-  const int s = blockIdx.y, ch = blockIdx.x, i0 = ch * DT, t = threadIdx.x;
-  for (int q = t; q < DT * FC; q += blockDim.x) {
-    const int r = q >> 5, c = q & 31, i = i0 + r;
-    hs[r][c] = i < M ? h[((size_t)s * M + i) * FC + c] : 0.0f;
-  }
-  for (int q = t; q < DT * FK / 2; q += blockDim.x) {  // 8 float4 (16 twiddles) per point
+// the chunk partials are summed (in a fixed order) by k_mix.
+constexpr int TP = 64;
+constexpr int DT = TP;
+constexpr int TILE_SMEM_FLOATS = 8 * FK * FC * 2;  // 32 KB: activation + twiddle tiles, then warp partials
+
+// Loads the twiddles of the tile starting at point i0 (8 float4 = 16 complex per point, zero past M).
+__device__ __forceinline__ void load_tile_twiddles(float2* ts, const float2* __restrict__ tw, int i0, int M) {
+  for (int q = threadIdx.x; q < TP * FK / 2; q += blockDim.x) {
     const int r = q >> 3, i = i0 + r;
     float4 v{0, 0, 0, 0};
     if (i < M) v = __ldg(reinterpret_cast<const float4*>(tw) + (size_t)i * (FK / 2) + (q & 7));
-    reinterpret_cast<float4*>(ts[r])[q & 7] = v;
+    reinterpret_cast<float4*>(ts + r * FK)[q & 7] = v;
   }
+}
+
+// DFT partials of one tile: hs [TP][FC] activations, ts [TP][FK] twiddles (both in `raw`), 256
+// threads; warp w takes the points r = w (mod 8) for all 16 modes, then the 8 warp partials are
+// added in shared memory (overwriting the tiles).  Writes FK * FC values to out.
+__device__ __forceinline__ void tile_dft(float* raw, float2* __restrict__ out) {
+  const float* hs = raw;
+  const float2* ts = reinterpret_cast<const float2*>(raw + TP * FC);
+  const int t = threadIdx.x, w = t >> 5, c = t & 31;
   __syncthreads();
-  const int w = t >> 5, c = t & 31;
   float2 acc[FK];
 #pragma unroll
   for (int k = 0; k < FK; ++k) acc[k] = float2{0, 0};
 #pragma unroll 2
-  for (int r = w; r < DT; r += 8) {
-    const float v = hs[r][c];
-    const float4* t4 = reinterpret_cast<const float4*>(ts[r]);
+  for (int r = w; r < TP; r += 8) {
+    const float v = hs[r * FC + c];
+    const float4* t4 = reinterpret_cast<const float4*>(ts + r * FK);
 #pragma unroll
     for (int k4 = 0; k4 < FK / 2; ++k4) {
       const float4 q = t4[k4];
@@ -149,11 +106,10 @@ __global__ void __launch_bounds__(256) k_dft(const float* __restrict__ h, int M,
     }
   }
   __syncthreads();
-  float2* red = reinterpret_cast<float2*>(smem);  // [8 warps][FK][FC]
+  float2* red = reinterpret_cast<float2*>(raw);  // [8 warps][FK][FC]
 #pragma unroll
   for (int k = 0; k < FK; ++k) red[(w * FK + k) * FC + c] = acc[k];
   __syncthreads();
-  float2* o = part + ((size_t)s * nch + ch) * FK * FC;
   for (int q = t; q < FK * FC; q += blockDim.x) {
     float2 a{0, 0};
 #pragma unroll
@@ -162,8 +118,58 @@ __global__ void __launch_bounds__(256) k_dft(const float* __restrict__ h, int M,
       a.x += v.x;
       a.y += v.y;
     }
-    o[q] = a;
+    out[q] = a;
   }
+}
+
+// grid (chunks, B), 256 threads: DFT partials of h (the backward's gradient transforms)
+__global__ void __launch_bounds__(256) k_dft(const float* __restrict__ h, int M, const float2* __restrict__ tw,
+                                             float2* __restrict__ part, int nch) {
+  __shared__ __align__(16) float raw[TILE_SMEM_FLOATS];
+  const int s = blockIdx.y, ch = blockIdx.x, i0 = ch * TP, t = threadIdx.x;
+  for (int q = t; q < TP * FC / 4; q += blockDim.x) {
+    const int r = q >> 3, c4 = q & 7, i = i0 + r;
+    float4 v{0, 0, 0, 0};
+    if (i < M) v = reinterpret_cast<const float4*>(h + ((size_t)s * M + i) * FC)[c4];
+    reinterpret_cast<float4*>(raw + r * FC)[c4] = v;
+  }
+  load_tile_twiddles(reinterpret_cast<float2*>(raw + TP * FC), tw, i0, M);
+  tile_dft(raw, part + ((size_t)s * nch + ch) * FK * FC);
+}
+
+// Features, lift and the first layer's DFT partials in one pass over a tile of points:
+// f_i = [Re b_i / ||b||, Im b_i / ||b||, Re lambda, Im lambda, alpha, (i+1)/(M+1)],
+// h0_i = W_lift f_i + b_lift (feat and h0 are kept for the backward).
+__global__ void __launch_bounds__(256) k_lift_dft(const float2* __restrict__ b, const double2* __restrict__ lam,
+                                                  const float* __restrict__ alpha, const float* __restrict__ norms,
+                                                  const bf16* __restrict__ P, int M, const float2* __restrict__ tw,
+                                                  float* __restrict__ feat, float* __restrict__ h0,
+                                                  float2* __restrict__ part, int nch) {
+  __shared__ __align__(16) float raw[TILE_SMEM_FLOATS];
+  __shared__ float Wl[FC * FF + FC];  // lift W [32][6] then bias
+  const int s = blockIdx.y, ch = blockIdx.x, i0 = ch * TP, t = threadIdx.x;
+  for (int q = t; q < FC * FF + FC; q += blockDim.x) Wl[q] = wv(P, OFF_LW + q);
+  load_tile_twiddles(reinterpret_cast<float2*>(raw + TP * FC), tw, i0, M);
+  __syncthreads();
+  const int o = t & 31, w = t >> 5;
+  const float inv = norms[s] > 0 ? 1.0f / norms[s] : 0.0f;
+  const float l0 = (float)lam[s].x, l1 = (float)lam[s].y, al = alpha[s];
+  for (int il = w; il < TP; il += 8) {
+    const int i = i0 + il;
+    float hv = 0.0f;
+    if (i < M) {
+      const size_t n = (size_t)s * M + i;
+      const float2 v = b[n];
+      const float f[FF] = {v.x * inv, v.y * inv, l0, l1, al, (float)(i + 1) / (float)(M + 1)};
+      if (o < FF) feat[n * FF + o] = f[o];
+      hv = Wl[FC * FF + o];
+#pragma unroll
+      for (int q = 0; q < FF; ++q) hv = fmaf(Wl[o * FF + q], f[q], hv);
+      h0[n * FC + o] = hv;
+    }
+    raw[il * FC + o] = hv;
+  }
+  tile_dft(raw, part + ((size_t)s * nch + ch) * FK * FC);
 }
 
 // Spectral mixing, one block per (mode k, group of MIX_S samples), R[k] staged in shared memory.
@@ -220,32 +226,28 @@ __global__ void __launch_bounds__(512) k_mix(const float2* __restrict__ part, in
   out[((size_t)s * FK + k) * FC + a] = float2{re, im};
 }
 
-constexpr int TP = 64;  // grid points per block in the point-wise kernels (8 per warp)
-
-// z = (1/M) Re sum_k c_k G_k e^{+i theta} + W h + b;  h_out = act(z).
-// Thread o keeps G[.][o] (scaled by c_k / M) and row o of W in registers; per
-// point it reads the activation row and the 16 twiddles as broadcast float4.
+// z = (1/M) Re sum_k c_k G_k e^{+i theta} + W h + b;  h_out = act(z); with part != null also the
+// next layer's DFT partials of h_out for this tile (tile_dft).
+// Thread o keeps G[.][o] (scaled by c_k / M) and row o of W in registers; per point it reads the
+// activation row and the 16 twiddles as broadcast float4.
 __global__ void __launch_bounds__(256) k_inv_pw(const float2* __restrict__ G, const float* __restrict__ hin,
                                                 const bf16* __restrict__ P, int offW, int offb, int M,
                                                 const float2* __restrict__ tw, float* __restrict__ z,
-                                                float* __restrict__ hout, int act) {
-  __shared__ __align__(16) float hs[TP][FC];
-  __shared__ __align__(16) float2 ts[TP][FK];
+                                                float* __restrict__ hout, int act, float2* __restrict__ part,
+                                                int nch) {
+  __shared__ __align__(16) float raw[TILE_SMEM_FLOATS];
   __shared__ float Ws[FC][FC + 1];
-  const int s = blockIdx.y, i0 = blockIdx.x * TP, t = threadIdx.x;
+  float* hs = raw;                                          // [TP][FC]
+  float2* ts = reinterpret_cast<float2*>(raw + TP * FC);    // [TP][FK]
+  const int s = blockIdx.y, ch = blockIdx.x, i0 = ch * TP, t = threadIdx.x;
   for (int q = t; q < FC * FC; q += blockDim.x) Ws[q >> 5][q & 31] = wv(P, offW + q);
   for (int q = t; q < TP * FC / 4; q += blockDim.x) {
     const int r = q >> 3, c4 = q & 7, i = i0 + r;
     float4 v{0, 0, 0, 0};
     if (i < M) v = reinterpret_cast<const float4*>(hin + ((size_t)s * M + i) * FC)[c4];
-    reinterpret_cast<float4*>(hs[r])[c4] = v;
+    reinterpret_cast<float4*>(hs + r * FC)[c4] = v;
   }
-  for (int q = t; q < TP * FK / 2; q += blockDim.x) {
-    const int r = q >> 3, i = i0 + r;
-    float4 v{0, 0, 0, 0};
-    if (i < M) v = __ldg(reinterpret_cast<const float4*>(tw) + (size_t)i * (FK / 2) + (q & 7));
-    reinterpret_cast<float4*>(ts[r])[q & 7] = v;
-  }
+  load_tile_twiddles(ts, tw, i0, M);
   const int o = t & 31, w = t >> 5;
   const float invM = 1.0f / (float)M;
   float2 g[FK];
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(256) k_inv_pw(const float2* __restrict__ G, co
     const int i = i0 + il;
     if (i >= M) break;
     float sp = 0, u = bias;
-    const float4* t4 = reinterpret_cast<const float4*>(ts[il]);
+    const float4* t4 = reinterpret_cast<const float4*>(ts + il * FK);
 #pragma unroll
     for (int k4 = 0; k4 < FK / 2; ++k4) {  // Re(G e^{+i theta}) with e^{+i theta} = conj(tw)
       const float4 q = t4[k4];
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256) k_inv_pw(const float2* __restrict__ G, co
       sp = fmaf(g[2 * k4 + 1].x, q.z, sp);
       sp = fmaf(g[2 * k4 + 1].y, q.w, sp);
     }
-    const float4* h4 = reinterpret_cast<const float4*>(hs[il]);
+    const float4* h4 = reinterpret_cast<const float4*>(hs + il * FC);
 #pragma unroll
     for (int c4 = 0; c4 < FC / 4; ++c4) {
       const float4 v = h4[c4];
@@ -284,10 +286,14 @@ __global__ void __launch_bounds__(256) k_inv_pw(const float2* __restrict__ G, co
       u = fmaf(wr[4 * c4 + 3], v.w, u);
     }
     const float zz = sp + u;
+    const float hv = act ? gelu(zz) : zz;
     const size_t e = ((size_t)s * M + i) * FC + o;
     z[e] = zz;
-    hout[e] = act ? gelu(zz) : zz;
+    hout[e] = hv;
+    __syncwarp();             // every lane has read row il
+    hs[il * FC + o] = hv;     // the warp owns row il: the tile becomes h_out
   }
+  if (part) tile_dft(raw, part + ((size_t)s * nch + ch) * FK * FC);
 }
 
 // y[n] = W_proj h[n] + b_proj, one thread per point (row read as float4)
@@ -572,15 +578,15 @@ aao_status fno_forward(aao_fno* f, int B, const float2* b, const double2* lam, c
   using namespace aao;
   const int M = f->M;
   const size_t N = (size_t)B * M;
+  const dim3 tiles(f->nch, B);
   k_norms<<<B, 256, 0, s>>>(b, M, f->norms);
-  k_features<<<nblk(N), 256, 0, s>>>(b, lam, alpha, f->norms, M, B, f->feat);
-  k_lift<<<nblk(N), 256, 0, s>>>(f->feat, f->P16, N, f->h[0]);
+  k_lift_dft<<<tiles, 256, 0, s>>>(b, lam, alpha, f->norms, f->P16, M, f->tw, f->feat, f->h[0], f->part, f->nch);
   for (int l = 0; l < FL; ++l) {
-    k_dft<<<dim3(f->nch, B), 256, 0, s>>>(f->h[l], M, f->tw, f->part, f->nch);
     k_mix<<<dim3(FK, (B + MIX_S - 1) / MIX_S), 512, 0, s>>>(f->part, f->nch, f->H[l], f->P16, off_R(l), B, M, f->G,
                                                             0, 0);
-    k_inv_pw<<<dim3((M + TP - 1) / TP, B), 256, 0, s>>>(f->G, f->h[l], f->P16, off_W(l), off_b(l), M, f->tw, f->z[l],
-                                                         f->h[l + 1], l < FL - 1);
+    const bool last = l == FL - 1;
+    k_inv_pw<<<tiles, 256, 0, s>>>(f->G, f->h[l], f->P16, off_W(l), off_b(l), M, f->tw, f->z[l], f->h[l + 1],
+                                   !last, last ? nullptr : f->part, f->nch);
   }
   k_proj<<<nblk(N), 256, 0, s>>>(f->h[FL], f->P16, N, f->y);
   FCK(cudaGetLastError());

@@ -282,7 +282,7 @@ aao_status fail(aao_plan* p, aao_status st, const std::string& msg) {
   } while (0)
 
 enum { ST_MATVEC = 0, ST_TDFT_FWD = 1, ST_COCG = 2, ST_TDFT_INV = 3, ST_VEC = 4, ST_FNO = 5 };
-constexpr int kFnoLaunches = 17;  // kernels of one aao_fno_predict
+constexpr int kFnoLaunches = 12;  // kernels of one aao_fno_predict
 
 cudaEvent_t take_event(aao_plan* p) {
   if (!p->ev_pool.empty()) {
