@@ -60,6 +60,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest x over all ranks (the job's time is its slowest rank's); x itself when world == 1.
+    Works on any process-group backend (NCCL with a CUDA device, gloo on the CPU)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -346,10 +358,7 @@ def run_ours(args):
         barrier()
         t_wall = time.perf_counter() - t_wall
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     launches_timed = sum(n for p in uniq for _, n in p.get_profile(reset=True).values())
     # stage breakdown: the same steps again with every launch bracketed by CUDA events (profiling
     # runs the host-driven Arnoldi steps; the timed region above replays graph-captured cycles)
@@ -376,10 +385,7 @@ def run_ours(args):
         plans[s % len(Fs)].gmres_solve_host(Fh[s % len(Fs)], Uh)
     barrier()
     t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, world, dev)
     e2e = {"value": world * M * My * Nt * args.steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": M * My * Nt * 8, "d2h_bytes_per_step": M * My * Nt * 8}
 
@@ -552,10 +558,7 @@ def run_learned(args):
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     launches_timed = sum(n for p in plans for _, n in p.get_profile(reset=True).values())
     cocg_threads = plans[0].cocg_threads
     for p in plans:  # stage breakdown from one more pass with every launch bracketed by events
@@ -726,10 +729,7 @@ def run_batched(args):
             infos = step()
         barrier()
         dt = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([dt], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dt, world, dev)
     launches = sum(n for p in plans for _, n in p.get_profile(reset=True).values())
     # for comparison: the same instances solved one after another on one stream (one pass)
     for U in Us:

@@ -723,7 +723,8 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
 }
 
 // aao_gmres_solve with each restart cycle replayed as one CUDA graph (1D); nF = ||F|| > 0.
-aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* info, double nF) {
+aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* info, double nF,
+                             bool zero_guess) {
   if (!p->cycle_exec || p->graph_fno != p->fno) TRY(build_cycle_graph(p));
   const size_t n = p->n;
   const size_t tail = sizeof(GmresDevState) - offsetof(GmresDevState, thr);
@@ -735,10 +736,15 @@ aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* 
   aao_status result = AAO_ENOCONV;
   int outer_prev = 0;
   for (int cycle = 0; cycle <= p->opts.max_cycles; ++cycle) {
-    TRY(matvec_any(p, U, false, F, p->V, p->sq));  // r = F - calA U into v_0, row sums of squares
-    inf.matvecs++;
     double beta2 = 0;
-    TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));  // leaves beta^2 in p->hdev[0]
+    if (cycle == 0 && zero_guess) {  // r = F; beta^2 = ||F||^2 is already in p->hdev[0]
+      CK(cudaMemcpyAsync(p->V, F, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+      beta2 = nF * nF;
+    } else {
+      TRY(matvec_any(p, U, false, F, p->V, p->sq));  // r = F - calA U into v_0, row sums of squares
+      inf.matvecs++;
+      TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));  // leaves beta^2 in p->hdev[0]
+    }
     const double beta = std::sqrt(beta2);
     if (!std::isfinite(beta)) { result = AAO_ENONFINITE; p->err = "non-finite residual"; break; }
     inf.true_rel_res = beta / nF;
@@ -1097,9 +1103,15 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
   const int m = p->m;
   const int nb = aao::blas_partial_blocks();
   aao_info inf{};
-  double nF2 = 0;
+  // ||F||^2 into p->hdev[0] and ||U||^2 into p->hdev[1]: with U = 0 the first residual is F itself
   LAUNCH(ST_VEC, 1, aao::launch_dots(F, F, 0, 1, n, p->partial, p->stream));
-  TRY(reduce_to_host(p, p->partial, nb, 1, &nF2));
+  LAUNCH(ST_VEC, 1, aao::launch_dots(U, U, 0, 1, n, p->partial + nb, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, 1, p->hdev, p->stream));
+  LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial + nb, nb, 1, p->hdev + 1, p->stream));
+  CK(cudaMemcpyAsync(p->pinned, p->hdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const double nF2 = p->pinned[0];
+  const bool zero_guess = p->pinned[1] == 0.0;
   const double nF = std::sqrt(nF2);
   if (!std::isfinite(nF)) return fail(p, AAO_ENONFINITE, "non-finite right-hand side");
   if (nF == 0.0) {
@@ -1109,17 +1121,22 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     return AAO_OK;
   }
   if (p->opts.use_graphs && p->dim == 1 && !p->prof_on && p->rec_cap <= p->rec_count)
-    return gmres_solve_graph(p, F, U, info, nF);
+    return gmres_solve_graph(p, F, U, info, nF, zero_guess);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   const double tol = p->opts.tol;
   aao_status result = AAO_ENOCONV;
   for (int cycle = 0; cycle <= p->opts.max_cycles; ++cycle) {
     // r = F - calA U  (into V_0) with row partial sums of squares
-    TRY(matvec_any(p, U, false, F, p->V, p->sq));
-    inf.matvecs++;
     double beta2 = 0;
-    TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));
+    if (cycle == 0 && zero_guess) {  // r = F
+      CK(cudaMemcpyAsync(p->V, F, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+      beta2 = nF2;
+    } else {
+      TRY(matvec_any(p, U, false, F, p->V, p->sq));
+      inf.matvecs++;
+      TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));
+    }
     const double beta = std::sqrt(beta2);
     if (!std::isfinite(beta)) { result = AAO_ENONFINITE; p->err = "non-finite residual"; break; }
     inf.true_rel_res = beta / nF;
