@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--inner", default="strang", choices=["strang", "tau"])
+    ap.add_argument("--matvec", default="ntt", choices=["fft64", "ntt"],
+                    help="1D matvec arithmetic: FP64 FFT convolution or exact NTT convolution of 58-bit rows")
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--Nt", type=int, default=NT_DEF)
     ap.add_argument("--dim", type=int, default=1, choices=[1, 2],
@@ -234,6 +236,21 @@ FP64_PEAK_TFLOPS = 2 * 1.60 * 152 * 2.07e9 / 1e12
 # launch; profiles/cocg_reg_matvec_small_full.md); traffic grows with the rows, so a full launch of
 # Nt rows moves Nt times this.
 MATVEC_DRAM_BYTES_PER_ROW_M8191 = 17.018e6 / 128
+# The same for the exact-integer (NTT) matvec: ntt_quant_kernel + ntt_conv_kernel (5 primes) +
+# ntt_epilogue_kernel read 8.40 + 10.43 + 37.76 MB and write 0 per 128-row launch triple
+# (profiles/ntt_matvec_small_full.md).
+NTT_DRAM_BYTES_PER_ROW_M8191 = (8.396e6 + 10.441e6 + 37.762e6) / 128
+# Lazy Shoup butterfly issue rate measured on GB300 (dependent-chain probe): 6.27 per clock per SM.
+NTT_PEAK_GBFLY = 6.27 * 152 * 2.07
+
+
+def ntt_butterflies(M, Nt):
+    """Radix-2-equivalent modular butterflies of one NTT matvec: 5 primes x (forward + inverse)
+    NTT of length L per time row (L/2 log2 L each)."""
+    L = 4
+    while L < 2 * M:
+        L *= 2
+    return 5 * 2 * (L // 2) * np.log2(L) * Nt
 FP32_PEAK_TFLOPS = 2 * 114.0 * 152 * 2.07e9 / 1e12
 
 
@@ -321,7 +338,8 @@ def run_ours(args):
     else:
         My = 1
         for i, a in enumerate(ALPHAS):
-            p = aao.Plan(M, Nt, a, kappa=1.0, T=1.0, prec=prec, inner=inner)
+            p = aao.Plan(M, Nt, a, kappa=1.0, T=1.0, prec=prec, inner=inner,
+                         matvec=aao.AAO_MATVEC_NTT if args.matvec == "ntt" else aao.AAO_MATVEC_FFT64)
             u0, f = workloads.make_inputs(M, Nt, seed=1000 * rank + i)
             F = torch.empty((Nt, M), dtype=torch.float64, device=dev)
             p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
@@ -397,7 +415,17 @@ def run_ours(args):
     n_apply = sum(i["outer_iters"] for i in prof_infos)
     inner_sum = sum(i["inner_iters_sum"] for i in prof_infos)
     nsys = Nt // 2 + 1
-    if dom == "matvec":
+    if dom == "matvec" and args.dim == 1 and args.matvec == "ntt":
+        n_mv = sum(i["matvecs"] for i in prof_infos)
+        t_launch = prof["matvec"][0] / max(n_mv, 1)  # per matvec (2 kernels)
+        achieved = ntt_butterflies(M, Nt) / (t_launch * 1e-3) / 1e9
+        traffic = NTT_DRAM_BYTES_PER_ROW_M8191 * Nt if M == 8191 else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": NTT_PEAK_GBFLY, "unit": "Gbutterfly/s",
+                "frac": achieved / NTT_PEAK_GBFLY, "traffic": traffic,
+                "kernel": "ntt_quant_kernel + ntt_conv_kernel + ntt_epilogue_kernel",
+                "peak_source": "lazy Shoup butterfly issue rate 6.27 /clk/SM x 152 SMs x 2.07 GHz (measured probe)",
+                "traffic_source": "ncu dram bytes of a 128-row launch triple scaled to Nt rows" if traffic else None}
+    elif dom == "matvec":
         n_mv = sum(i["matvecs"] for i in prof_infos)
         t_launch = prof["matvec"][0] / max(n_mv, 1)  # per matvec (2 kernels in 2D)
         fl = matvec_flops(M, Nt) if args.dim == 1 else matvec2d_flops(M, My, Nt)
@@ -432,6 +460,7 @@ def run_ours(args):
                                ("2D Riesz FDE all-at-once BDF2 to TRR<=1e-10, %dx%d, Nt=%d, alphas %s, kappa=(1,1), "
                                 "T=1, sine16_normal inputs (seeds 0-2)" % (M, My, Nt, list(ALPHAS_2D))),
                    "M": M, "My": My, "Nt": Nt, "precision": args.prec, "inner_precond": args.inner, "restart": 20,
+                   "matvec": args.matvec if args.dim == 1 else "fft64",
                    "l2": "no explicit flush: every solve streams a >2 GB Krylov working set through the "
                          "129 MB L2",
                    "outer_iters": [i["outer_iters"] for i in infos],

@@ -59,10 +59,9 @@ typedef enum {
 /* How the Toeplitz product c T v of the matvec (Sec. 3.2) is computed (1D). */
 typedef enum {
   AAO_MATVEC_FFT64 = 0, /* FP64 FFT convolution (circulant embedding) */
-  AAO_MATVEC_NTT = 1    /* exact integer convolution of the rows quantised to 51-bit fixed point
-                           (2^-52 relative to the row's largest entry) by NTTs modulo four primes
-                           and CRT; for smooth solutions the true residual it computes is less
-                           accurate than the FP64 FFT's (about 3e-10 at M 8191, Nt 1024) */
+  AAO_MATVEC_NTT = 1    /* exact integer convolution of the rows quantised to 58-bit fixed point
+                           (2^-59 relative to the row's largest entry) by NTTs modulo five primes
+                           and CRT */
 } aao_matvec_kind;
 
 /*
@@ -99,7 +98,7 @@ typedef struct {
                            conditional nodes, Givens rotations on the device, one host synchronisation
                            per cycle instead of one per step); ignored in 2D, while profiling, or
                            while recording pairs.  0: host-driven steps. */
-  aao_matvec_kind matvec; /* [AAO_MATVEC_FFT64] 1D matvec arithmetic; 2D always uses FP64 FFTs */
+  aao_matvec_kind matvec; /* [AAO_MATVEC_NTT] 1D matvec arithmetic; 2D always uses FP64 FFTs */
   int cocg_threads;     /* [0] mixed 1D, M <= 8192: CTA size of the register-resident COCG kernel
                            (64, 128, 256 or 512, at least M / 16); 0 lets plan creation time the
                            admissible sizes on the plan's own systems and keep the fastest (cached

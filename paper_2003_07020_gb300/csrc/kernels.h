@@ -84,18 +84,20 @@ int cocg_reg_min_threads(int M);
 cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s);
 
 // ---- exact-integer matvec (NTT), ntt.cu ---------------------------------------------
-// Four primes p < 2^30 with 2^21 | p - 1 (product ~2^119.5) and a primitive root of each.
-constexpr uint32_t kNttPrime[4] = {1004535809u, 998244353u, 985661441u, 943718401u};
-constexpr uint32_t kNttGen[4] = {3u, 3u, 3u, 7u};
+// Five primes p < 2^30 with 2^22 | p - 1 (product ~2^149) and a primitive root of each.
+constexpr int kNttPrimes = 5;
+constexpr uint32_t kNttPrime[kNttPrimes] = {1004535809u, 998244353u, 985661441u, 943718401u, 880803841u};
+constexpr uint32_t kNttGen[kNttPrimes] = {3u, 3u, 3u, 7u, 26u};
 struct NttTables {
-  const uint2* twf;     // [4][L/2] (w^e, floor(w^e 2^32 / p))
-  const uint2* twi;     // [4][L/2] inverse roots
-  const uint2* ghat;    // [4][L] stencil spectrum, bit-reversed, times L^-1
-  uint32_t crt[6];      // p0^-1 mod p1, p0^-1 mod p2, p1^-1 mod p2, p0^-1 mod p3, p1^-1 mod p3, p2^-1 mod p3
-  double c_gscale;      // c 2^(e_g - 51)
+  const uint2* twf;     // [5][L] (w^e, floor(w^e 2^32 / p)), w a primitive L-th root mod p
+  const uint2* twi;     // [5][L] inverse roots
+  const uint2* ghat;    // [5][L] stencil spectrum, bit-reversed, times L^-1
+  uint32_t crt[10];     // Garner constants: p0^-1 mod p1..p4, p1^-1 mod p2..p4, p2^-1 mod p3, p4, p3^-1 mod p4
+  double c_gscale;      // c 2^(e_g - 58)
 };
 // w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the quantised row
-// (same contract as launch_matvec_f64).  res: 4 n uint32 scratch; rowscale: Nt doubles.
+// (same contract as launch_matvec_f64).  res: 7 n uint32 scratch (5 n residues, then n int64
+// quantised entries, 8-byte aligned when res is); rowscale: Nt doubles.
 cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                               int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
 cudaError_t launch_matvec_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,

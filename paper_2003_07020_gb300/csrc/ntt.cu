@@ -4,20 +4,27 @@
 // integer pipes are an order of magnitude faster).
 //
 // Row k of v is scaled by a power of two so that its largest magnitude lies in
-// [2^50, 2^51) and rounded to integers V (relative quantisation error 2^-52,
-// FP64 level); the FCD stencil g is quantised the same way once at plan
-// creation (G).  The linear convolution Y = G * V has |Y| < M 2^102 <= 2^115
-// and is computed modulo four NTT primes p_q < 2^30 (product ~2^119.5) by
+// [2^57, 2^58) and rounded to integers V (quantisation error 2^-59 of the row's
+// largest entry); the FCD stencil g is quantised the same way once at plan
+// creation (G).  The linear convolution Y = G * V has |Y| < M 2^116 <= 2^129
+// and is computed modulo five NTT primes p_q < 2^30 (product ~2^149) by
 // cyclic convolution of length L >= 2M - 1 (circulant embedding), then
 // reconstructed by Garner's mixed-radix CRT and converted to FP64:
-// c T v_k = c 2^(e_v + e_g - 102) Y.
+// c T v_k = c 2^(e_v + e_g - 116) Y.
 //
-// Kernel 1 (ntt_conv_kernel): one CTA per (time row, prime): quantise the row
-// mod p, forward NTT (radix-4 DIF passes in shared memory, natural order in,
-// bit-reversed out), multiply by the stencil spectrum (stored bit-reversed,
-// L^-1 folded in), inverse NTT (radix-4 DIT, bit-reversed in, natural out),
-// write the residues of the first M outputs.
-// Kernel 2 (ntt_epilogue_kernel): one CTA per row: Garner CRT of the four
+// Kernel 0 (ntt_quant_kernel): one CTA per time row: the row's scale and its
+// int64 quantisation (the only FP64 work before the epilogue).
+// Kernel 1 (ntt_conv_kernel): one CTA per (time row, prime): residues of the
+// quantised row mod p, forward NTT, multiply by the stencil spectrum (stored
+// bit-reversed, L^-1 folded in), inverse NTT, write the residues of the first
+// M outputs.
+// The transforms run in passes of r <= 4 radix-2 stages: each thread loads a
+// group of 2^r elements at stride S = L / 2^(s0 + r) from shared memory into
+// registers, applies the 2^r-point transform with constant roots, multiplies
+// by the external twiddles w^(j bitrev_r(k) 2^s0) (DIF; conjugate order for
+// the DIT inverse) and stores back (natural order in, bit-reversed out, and
+// back).  Shared memory is padded by one word per 32 (conflict-free strides).
+// Kernel 2 (ntt_epilogue_kernel): one CTA per row: Garner CRT of the five
 // residues, scaling, the BDF band of C (Eq. 1.7), optional residual rhs - w and
 // per-row sums of squares (as the FP64 matvec).
 //
@@ -31,12 +38,10 @@ namespace aao {
 
 namespace {
 
-constexpr uint32_t kP0 = kNttPrime[0], kP1 = kNttPrime[1], kP2 = kNttPrime[2], kP3 = kNttPrime[3];
-template <int Q> struct Prime;
-template <> struct Prime<0> { static constexpr uint32_t p = kP0; };
-template <> struct Prime<1> { static constexpr uint32_t p = kP1; };
-template <> struct Prime<2> { static constexpr uint32_t p = kP2; };
-template <> struct Prime<3> { static constexpr uint32_t p = kP3; };
+constexpr int NP = kNttPrimes;
+constexpr int QBITS = 58;  // quantisation: |V| < 2^58
+
+template <int Q> struct Prime { static constexpr uint32_t p = kNttPrime[Q]; };
 
 // a * w mod p in [0, 2p) for a < 2^32, w = (w, floor(w 2^32 / p))
 template <uint32_t P>
@@ -46,97 +51,129 @@ __device__ __forceinline__ uint32_t mulsh(uint32_t a, uint2 w) {
 }
 template <uint32_t P> __device__ __forceinline__ uint32_t red2(uint32_t a) { return a >= 2 * P ? a - 2 * P : a; }
 template <uint32_t P> __device__ __forceinline__ uint32_t red1(uint32_t a) { return a >= P ? a - P : a; }
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
-// Gentleman-Sande butterfly: (x, y) -> (x + y, (x - y) w), all in [0, 2p)
-template <uint32_t P>
+// Gentleman-Sande butterfly (x, y) -> (x + y, (x - y) w); w == 1 when ONE; all values in [0, 2p)
+template <uint32_t P, bool ONE>
 __device__ __forceinline__ void dif2(uint32_t& x, uint32_t& y, uint2 w) {
   const uint32_t s = x + y, d = x - y + 2 * P;
   x = red2<P>(s);
-  y = mulsh<P>(d, w);
+  y = ONE ? red2<P>(d) : mulsh<P>(d, w);
 }
-// Cooley-Tukey butterfly: (x, y) -> (x + y w, x - y w), all in [0, 2p)
-template <uint32_t P>
+// Cooley-Tukey butterfly (x, y) -> (x + y w, x - y w)
+template <uint32_t P, bool ONE>
 __device__ __forceinline__ void dit2(uint32_t& x, uint32_t& y, uint2 w) {
-  const uint32_t t = mulsh<P>(y, w);
+  const uint32_t t = ONE ? y : mulsh<P>(y, w);
   const uint32_t s = x + t, d = x - t + 2 * P;
   x = red2<P>(s);
   y = red2<P>(d);
 }
 
-// Forward cyclic NTT X[k] = sum_j x_j w^{jk} (w a primitive L-th root, tw[e] = w^e for e < L/2),
-// natural order in, bit-reversed order out.  Each radix-4 pass performs the DIF stages of half
-// sizes h and h/2; an odd last stage (h = 1) is done as a radix-2 pass.
-template <uint32_t P>
-__device__ void ntt_dif(uint32_t* buf, int logL, const uint2* __restrict__ tw) {
-  const int L = 1 << logL;
-  int s = 0;
-  for (; s + 2 <= logL; s += 2) {
-    const int h = L >> (s + 1), hq = h >> 1;
-    __syncthreads();
-    for (int g = threadIdx.x; g < L / 4; g += blockDim.x) {
-      const int b = g >> (logL - s - 2), j = g & (hq - 1);
-      const int i0 = (b << (logL - s)) + j, i1 = i0 + hq, i2 = i0 + h, i3 = i2 + hq;
-      uint32_t a0 = buf[i0], a1 = buf[i1], a2 = buf[i2], a3 = buf[i3];
-      const int e1 = j << s;
-      const uint2 w1 = __ldg(&tw[e1]), w2 = __ldg(&tw[e1 + (L >> 2)]), w3 = __ldg(&tw[e1 << 1]);
-      dif2<P>(a0, a2, w1);
-      dif2<P>(a1, a3, w2);
-      dif2<P>(a0, a1, w3);
-      dif2<P>(a2, a3, w3);
-      buf[i0] = a0;
-      buf[i1] = a1;
-      buf[i2] = a2;
-      buf[i3] = a3;
+template <int r> __device__ __forceinline__ constexpr int brev_r(int k) {
+  int o = 0;
+  for (int b = 0; b < r; ++b) o |= ((k >> b) & 1) << (r - 1 - b);
+  return o;
+}
+
+// One forward pass of r stages starting at stage s0 (see the file comment).  wint[e] = w^(e L / R).
+template <uint32_t P, int r>
+__device__ __forceinline__ void dif_pass(uint32_t* buf, int logL, int s0, const uint2* __restrict__ tw,
+                                         const uint2 (&wint)[8]) {
+  constexpr int R = 1 << r;
+  const int L = 1 << logL, logS = logL - s0 - r, S = 1 << logS;
+  for (int g = threadIdx.x; g < (L >> r); g += blockDim.x) {
+    const int b = g >> logS, j = g & (S - 1);
+    const int base = (b << (logL - s0)) + j;
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = buf[pad32(base + k * S)];
+#pragma unroll
+    for (int t = 0; t < r; ++t) {
+      const int half = R >> (t + 1);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (k & half) continue;
+        const int e = (k % half) << t;  // power of w^(L/R)
+        if (e == 0) dif2<P, true>(v[k], v[k + half], wint[0]);
+        else dif2<P, false>(v[k], v[k + half], wint[e]);
+      }
+    }
+    const int jj = j << s0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&tw[jj * brev_r<r>(k)]));
+      buf[pad32(base + k * S)] = v[k];
     }
   }
-  if (s < logL) {
+}
+
+// Inverse of dif_pass with the inverse roots (twi, wint = w^(-e L / R)).
+template <uint32_t P, int r>
+__device__ __forceinline__ void dit_pass(uint32_t* buf, int logL, int s0, const uint2* __restrict__ twi,
+                                         const uint2 (&wint)[8]) {
+  constexpr int R = 1 << r;
+  const int L = 1 << logL, logS = logL - s0 - r, S = 1 << logS;
+  for (int g = threadIdx.x; g < (L >> r); g += blockDim.x) {
+    const int b = g >> logS, j = g & (S - 1);
+    const int base = (b << (logL - s0)) + j;
+    const int jj = j << s0;
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      v[k] = buf[pad32(base + k * S)];
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&twi[jj * brev_r<r>(k)]));
+    }
+#pragma unroll
+    for (int t = r - 1; t >= 0; --t) {
+      const int half = R >> (t + 1);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (k & half) continue;
+        const int e = (k % half) << t;
+        if (e == 0) dit2<P, true>(v[k], v[k + half], wint[0]);
+        else dit2<P, false>(v[k], v[k + half], wint[e]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) buf[pad32(base + k * S)] = v[k];
+  }
+}
+
+// wint[e] = tab[e L / R] for e < R / 2
+template <int r>
+__device__ __forceinline__ void load_roots(uint2 (&wint)[8], const uint2* __restrict__ tab, int logL) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) wint[e] = (e < (1 << r) / 2) ? __ldg(&tab[e << (logL - r)]) : uint2{1, 0};
+}
+
+template <uint32_t P>
+__device__ void ntt_forward(uint32_t* buf, int logL, const uint2* __restrict__ tw) {
+  for (int s0 = 0; s0 < logL; s0 += 4) {
+    const int r = logL - s0 < 4 ? logL - s0 : 4;
+    uint2 wint[8];
     __syncthreads();
-    const uint2 w0 = __ldg(&tw[0]);
-    for (int g = threadIdx.x; g < L / 2; g += blockDim.x) {
-      uint32_t a = buf[2 * g], c = buf[2 * g + 1];
-      dif2<P>(a, c, w0);
-      buf[2 * g] = a;
-      buf[2 * g + 1] = c;
+    switch (r) {
+      case 1: load_roots<1>(wint, tw, logL); dif_pass<P, 1>(buf, logL, s0, tw, wint); break;
+      case 2: load_roots<2>(wint, tw, logL); dif_pass<P, 2>(buf, logL, s0, tw, wint); break;
+      case 3: load_roots<3>(wint, tw, logL); dif_pass<P, 3>(buf, logL, s0, tw, wint); break;
+      default: load_roots<4>(wint, tw, logL); dif_pass<P, 4>(buf, logL, s0, tw, wint); break;
     }
   }
   __syncthreads();
 }
 
-// Inverse (unnormalised) cyclic NTT x_j = sum_k X[k] w^{-jk} (twi[e] = w^{-e}), bit-reversed order
-// in, natural order out: radix-4 DIT passes of half sizes h and 2h, an odd first stage (h = 1)
-// as a radix-2 pass.
 template <uint32_t P>
-__device__ void ntt_dit(uint32_t* buf, int logL, const uint2* __restrict__ twi) {
-  const int L = 1 << logL;
-  int s = 0;
-  if (logL & 1) {
+__device__ void ntt_inverse(uint32_t* buf, int logL, const uint2* __restrict__ twi) {
+  const int last = ((logL - 1) / 4) * 4;  // start stage of the last forward pass
+  for (int s0 = last; s0 >= 0; s0 -= 4) {
+    const int r = logL - s0 < 4 ? logL - s0 : 4;
+    uint2 wint[8];
     __syncthreads();
-    const uint2 w0 = __ldg(&twi[0]);
-    for (int g = threadIdx.x; g < L / 2; g += blockDim.x) {
-      uint32_t a = buf[2 * g], c = buf[2 * g + 1];
-      dit2<P>(a, c, w0);
-      buf[2 * g] = a;
-      buf[2 * g + 1] = c;
-    }
-    s = 1;
-  }
-  for (; s + 2 <= logL; s += 2) {
-    const int h = 1 << s;
-    __syncthreads();
-    for (int g = threadIdx.x; g < L / 4; g += blockDim.x) {
-      const int b = g >> s, j = g & (h - 1);
-      const int i0 = (b << (s + 2)) + j, i1 = i0 + h, i2 = i1 + h, i3 = i2 + h;
-      uint32_t a0 = buf[i0], a1 = buf[i1], a2 = buf[i2], a3 = buf[i3];
-      const int e2 = j << (logL - s - 2);
-      const uint2 w1 = __ldg(&twi[e2 << 1]), w2 = __ldg(&twi[e2]), w3 = __ldg(&twi[e2 + (L >> 2)]);
-      dit2<P>(a0, a1, w1);
-      dit2<P>(a2, a3, w1);
-      dit2<P>(a0, a2, w2);
-      dit2<P>(a1, a3, w3);
-      buf[i0] = a0;
-      buf[i1] = a1;
-      buf[i2] = a2;
-      buf[i3] = a3;
+    switch (r) {
+      case 1: load_roots<1>(wint, twi, logL); dit_pass<P, 1>(buf, logL, s0, twi, wint); break;
+      case 2: load_roots<2>(wint, twi, logL); dit_pass<P, 2>(buf, logL, s0, twi, wint); break;
+      case 3: load_roots<3>(wint, twi, logL); dit_pass<P, 3>(buf, logL, s0, twi, wint); break;
+      default: load_roots<4>(wint, twi, logL); dit_pass<P, 4>(buf, logL, s0, twi, wint); break;
     }
   }
   __syncthreads();
@@ -144,39 +181,15 @@ __device__ void ntt_dit(uint32_t* buf, int logL, const uint2* __restrict__ twi) 
 
 template <typename TIn> __device__ __forceinline__ double ldd(const TIn* p) { return (double)__ldg(p); }
 
-template <typename TIn, int Q>
-__device__ __forceinline__ void conv_row(const TIn* __restrict__ vk, int M, int logL, double qs,
-                                         const NttTables& t, uint32_t* buf, uint32_t* __restrict__ out) {
-  constexpr uint32_t P = Prime<Q>::p;
-  const int L = 1 << logL;
-  const size_t half = (size_t)(L >> 1);
-  for (int i = threadIdx.x; i < L; i += blockDim.x) {
-    uint32_t r = 0;
-    if (i < M) {
-      const long long V = __double2ll_rn(ldd(vk + i) * qs);  // |V| <= 2^51, exact power-of-two scaling
-      long long m = V % (long long)P;
-      if (m < 0) m += P;
-      r = (uint32_t)m;
-    }
-    buf[i] = r;
-  }
-  ntt_dif<P>(buf, logL, t.twf + Q * half);
-  const uint2* gh = t.ghat + (size_t)Q * L;
-  for (int k = threadIdx.x; k < L; k += blockDim.x) buf[k] = mulsh<P>(buf[k], __ldg(&gh[k]));
-  ntt_dit<P>(buf, logL, t.twi + Q * half);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = red1<P>(red2<P>(buf[i]));
-}
-
-// grid (Nt, 4): blockIdx.y selects the prime.  res: [4][Nt][M] residues; rowscale[k] = 2^(e_v - 51)
-// (0 for a zero row, NaN for a row with a non-finite entry), written by the prime-0 CTAs.
+// Quantisation pre-pass, one CTA per row: V[k][i] = round(v[k][i] 2^(58 - e_v)) with the row's
+// largest magnitude below 2^e_v (int64, |V| < 2^58); rowscale[k] = 2^(e_v - 58) (0 for a zero row,
+// NaN for a row with a non-finite entry, whose V is left 0).
 template <typename TIn>
-__global__ void __launch_bounds__(512) ntt_conv_kernel(const TIn* __restrict__ v, int M, int Nt, int logL,
-                                                       NttTables t, uint32_t* __restrict__ res,
-                                                       double* __restrict__ rowscale) {
-  extern __shared__ uint32_t nbuf[];
+__global__ void __launch_bounds__(512) ntt_quant_kernel(const TIn* __restrict__ v, int M, long long* __restrict__ V,
+                                                        double* __restrict__ rowscale) {
   __shared__ double red[32];
   __shared__ int bad_any;
-  const int k = blockIdx.x, q = blockIdx.y;
+  const int k = blockIdx.x;
   const TIn* vk = v + (size_t)k * M;
   if (threadIdx.x == 0) bad_any = 0;
   double mx = 0.0;
@@ -195,35 +208,77 @@ __global__ void __launch_bounds__(512) ntt_conv_kernel(const TIn* __restrict__ v
   mx = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
   int ev = 0;
-  if (mx > 0) frexp(mx, &ev);                // mx < 2^ev
-  const double qs = mx > 0 ? ldexp(1.0, 51 - ev) : 0.0;
-  if (q == 0 && threadIdx.x == 0) rowscale[k] = bad_any ? __longlong_as_double(0x7ff8000000000000ll)
-                                                        : (mx > 0 ? ldexp(1.0, ev - 51) : 0.0);
+  if (mx > 0) frexp(mx, &ev);  // mx < 2^ev
+  const double qs = mx > 0 && !bad_any ? ldexp(1.0, QBITS - ev) : 0.0;
+  if (threadIdx.x == 0) rowscale[k] = bad_any ? __longlong_as_double(0x7ff8000000000000ll)
+                                              : (mx > 0 ? ldexp(1.0, ev - QBITS) : 0.0);
+  long long* Vk = V + (size_t)k * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) Vk[i] = __double2ll_rn(ldd(vk + i) * qs);  // exact scaling
+}
+
+template <int Q>
+__device__ __forceinline__ void conv_row(const long long* __restrict__ Vk, int M, int logL, const NttTables& t,
+                                         uint32_t* buf, uint32_t* __restrict__ out) {
+  constexpr uint32_t P = Prime<Q>::p;
+  const int L = 1 << logL;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    uint32_t r = 0;
+    if (i < M) {
+      long long m = __ldg(Vk + i) % (long long)P;
+      if (m < 0) m += P;
+      r = (uint32_t)m;
+    }
+    buf[pad32(i)] = r;
+  }
+  ntt_forward<P>(buf, logL, t.twf + (size_t)Q * L);
+  const uint2* gh = t.ghat + (size_t)Q * L;
+  for (int k = threadIdx.x; k < L; k += blockDim.x) buf[pad32(k)] = mulsh<P>(buf[pad32(k)], __ldg(&gh[k]));
+  ntt_inverse<P>(buf, logL, t.twi + (size_t)Q * L);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = red1<P>(buf[pad32(i)]);
+}
+
+// grid (Nt, NP): blockIdx.y selects the prime.  V: the quantised rows; res: [NP][Nt][M] residues.
+__global__ void __launch_bounds__(512) ntt_conv_kernel(const long long* __restrict__ V, int M, int Nt, int logL,
+                                                       NttTables t, uint32_t* __restrict__ res) {
+  extern __shared__ uint32_t nbuf[];
+  const int k = blockIdx.x, q = blockIdx.y;
+  const long long* Vk = V + (size_t)k * M;
   uint32_t* out = res + ((size_t)q * Nt + k) * M;
   switch (q) {
-    case 0: conv_row<TIn, 0>(vk, M, logL, qs, t, nbuf, out); break;
-    case 1: conv_row<TIn, 1>(vk, M, logL, qs, t, nbuf, out); break;
-    case 2: conv_row<TIn, 2>(vk, M, logL, qs, t, nbuf, out); break;
-    default: conv_row<TIn, 3>(vk, M, logL, qs, t, nbuf, out); break;
+    case 0: conv_row<0>(Vk, M, logL, t, nbuf, out); break;
+    case 1: conv_row<1>(Vk, M, logL, t, nbuf, out); break;
+    case 2: conv_row<2>(Vk, M, logL, t, nbuf, out); break;
+    case 3: conv_row<3>(Vk, M, logL, t, nbuf, out); break;
+    default: conv_row<4>(Vk, M, logL, t, nbuf, out); break;
   }
 }
 
-// Garner's mixed-radix digits d_q of the residues, then Y = d0 + p0 (d1 + p1 (d2 + p2 d3)) in
-// FP64, negative when d3 > p3/2 (|Y| < 2^115 << p0 p1 p2 p3 / 2).
-__device__ __forceinline__ double crt4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, const uint32_t* inv) {
-  const uint64_t d0 = r0;
-  const uint64_t d1 = ((uint64_t)(r1 + kP1 - (uint32_t)(d0 % kP1)) * inv[0]) % kP1;  // inv[0] = p0^-1 mod p1
-  uint64_t t2 = ((uint64_t)(r2 + kP2 - (uint32_t)(d0 % kP2)) * inv[1]) % kP2;        // inv[1] = p0^-1 mod p2
-  const uint64_t d2 = ((t2 + kP2 - d1 % kP2) * inv[2]) % kP2;                         // inv[2] = p1^-1 mod p2
-  uint64_t t3 = ((uint64_t)(r3 + kP3 - (uint32_t)(d0 % kP3)) * inv[3]) % kP3;        // inv[3] = p0^-1 mod p3
-  t3 = ((t3 + kP3 - d1 % kP3) * inv[4]) % kP3;                                        // inv[4] = p1^-1 mod p3
-  const uint64_t d3 = ((t3 + kP3 - d2 % kP3) * inv[5]) % kP3;                         // inv[5] = p2^-1 mod p3
-  if (d3 <= kP3 / 2)
-    return (((double)d3 * kP2 + (double)d2) * kP1 + (double)d1) * kP0 + (double)d0;
+// x mod p for x < 2p^2 (64-bit), p < 2^30
+template <int Q> __device__ __forceinline__ uint64_t md(uint64_t x) { return x % (uint64_t)Prime<Q>::p; }
+
+// Garner's mixed-radix digits d_q of the residues r_q, then
+// Y = d0 + p0 (d1 + p1 (d2 + p2 (d3 + p3 d4))) in FP64, negative when d4 > p4 / 2
+// (|Y| < 2^129, far below half the product of the primes).
+__device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint32_t* c) {
+  constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p, p4 = Prime<4>::p;
+  // c: p0^-1 mod p1..p4 (c[0..3]), p1^-1 mod p2..p4 (c[4..6]), p2^-1 mod p3, p4 (c[7..8]), p3^-1 mod p4 (c[9])
+  const uint64_t d0 = rq[0];
+  const uint64_t d1 = md<1>((rq[1] + p1 - md<1>(d0)) * c[0]);
+  uint64_t t = md<2>((rq[2] + p2 - md<2>(d0)) * c[1]);
+  const uint64_t d2 = md<2>((t + p2 - md<2>(d1)) * c[4]);
+  t = md<3>((rq[3] + p3 - md<3>(d0)) * c[2]);
+  t = md<3>((t + p3 - md<3>(d1)) * c[5]);
+  const uint64_t d3 = md<3>((t + p3 - d2 % p3) * c[7]);
+  t = md<4>((rq[4] + p4 - md<4>(d0)) * c[3]);
+  t = md<4>((t + p4 - md<4>(d1)) * c[6]);
+  t = md<4>((t + p4 - md<4>(d2)) * c[8]);
+  const uint64_t d4 = md<4>((t + p4 - md<4>(d3)) * c[9]);
+  auto u2d = [](uint64_t d) { return __uint2double_rn((uint32_t)d); };  // digits < 2^30
+  if (d4 <= p4 / 2)
+    return ((((u2d(d4) * p3 + u2d(d3)) * p2 + u2d(d2)) * p1 + u2d(d1)) * p0 + u2d(d0));
   // negative: Y = -(P - Y), P - 1 - Y has the complemented digits p_q - 1 - d_q
-  const double e3 = (double)(kP3 - 1 - d3), e2 = (double)(kP2 - 1 - d2), e1 = (double)(kP1 - 1 - d1),
-               e0 = (double)(kP0 - 1 - d0);
-  return -((((e3 * kP2 + e2) * kP1 + e1) * kP0 + e0) + 1.0);
+  return -(((((u2d(p4 - 1 - d4) * p3 + u2d(p3 - 1 - d3)) * p2 + u2d(p2 - 1 - d2)) * p1 + u2d(p1 - 1 - d1)) * p0 +
+            u2d(p0 - 1 - d0)) + 1.0);
 }
 
 template <typename TIn>
@@ -233,7 +288,7 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
                                                            const double* __restrict__ rowscale, NttTables t) {
   __shared__ double redb[32];
   const int k = blockIdx.x;
-  const double f = t.c_gscale * rowscale[k];  // c 2^(e_g - 51) 2^(e_v - 51)
+  const double f = t.c_gscale * rowscale[k];  // c 2^(e_g - 58) 2^(e_v - 58)
   const TIn* vk = v + (size_t)k * M;
   const TIn* vk1 = vk - M;
   const TIn* vk2 = vk - 2 * M;
@@ -242,8 +297,10 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
   const size_t n = (size_t)Nt * M, base = (size_t)k * M;
   double sq = 0.0;
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    const double Y = crt4(res[base + i], res[n + base + i], res[2 * n + base + i], res[3 * n + base + i], t.crt);
-    const double y = f * Y;
+    uint32_t rq[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) rq[q] = res[q * n + base + i];
+    const double y = f * crt5(rq, t.crt);
     double band;
     if (k == 0) band = ldd(vk + i);
     else if (k == 1) band = 1.5 * ldd(vk + i) - 2.0 * ldd(vk1 + i);
@@ -263,10 +320,15 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
 template <typename TIn>
 cudaError_t launch_ntt(const TIn* v, const double* rhs, double* w, double* sq_partial, int M, int Nt, int logL,
                        const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s) {
-  const size_t smem = (size_t)(1u << logL) * sizeof(uint32_t);
-  cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel<TIn>);
+  const int L = 1 << logL;
+  const size_t smem = (size_t)(L + L / 32 + 1) * sizeof(uint32_t);
+  cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel);
   if (e != cudaSuccess) return e;
-  ntt_conv_kernel<TIn><<<dim3(Nt, 4), 512, smem, s>>>(v, M, Nt, logL, t, res, rowscale);
+  long long* V = reinterpret_cast<long long*>(res + (size_t)NP * Nt * M);  // after the residues
+  ntt_quant_kernel<TIn><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ntt_conv_kernel<<<dim3(Nt, NP), 512, smem, s>>>(V, M, Nt, logL, t, res);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ntt_epilogue_kernel<TIn><<<Nt, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t);

@@ -232,7 +232,7 @@ struct aao_plan {
   // exact-integer matvec (opts.matvec == AAO_MATVEC_NTT, 1D)
   bool ntt = false;
   aao::NttTables ntt_tab{};
-  uint32_t* ntt_res = nullptr;  // 4 n residues
+  uint32_t* ntt_res = nullptr;  // 5 n residues + n int64 quantised entries
   double* ntt_rowscale = nullptr;
   int* iters = nullptr;
   int* flags = nullptr;
@@ -382,10 +382,10 @@ aao_status matvec_any(aao_plan* p, const void* v, bool v_is_f32, const double* r
   }
   if (p->ntt) {
     if (v_is_f32)
-      LAUNCH(ST_MATVEC, 2, aao::launch_matvec_ntt_fin((const float*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->ntt_tab,
+      LAUNCH(ST_MATVEC, 3, aao::launch_matvec_ntt_fin((const float*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->ntt_tab,
                                                       p->ntt_res, p->ntt_rowscale, p->stream));
     else
-      LAUNCH(ST_MATVEC, 2, aao::launch_matvec_ntt((const double*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->ntt_tab,
+      LAUNCH(ST_MATVEC, 3, aao::launch_matvec_ntt((const double*)v, rhs, w, sq, p->M, p->Nt, p->logL, p->ntt_tab,
                                                   p->ntt_res, p->ntt_rowscale, p->stream));
     return AAO_OK;
   }
@@ -797,7 +797,7 @@ void aao_default_opts(aao_opts* o, aao_precision prec) {
   o->prec = prec;
   o->inner = AAO_INNER_STRANG;
   o->use_graphs = 1;
-  o->matvec = AAO_MATVEC_FFT64;
+  o->matvec = AAO_MATVEC_NTT;
   o->cocg_threads = 0;
 }
 
@@ -905,9 +905,9 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->ntt_tab.twi = (const uint2*)q32;
     TRYP(upload(p, &q32, p->ht.ntt_ghat));
     p->ntt_tab.ghat = (const uint2*)q32;
-    for (int i = 0; i < 6; ++i) p->ntt_tab.crt[i] = p->ht.ntt_crt[i];
+    for (int i = 0; i < 10; ++i) p->ntt_tab.crt[i] = p->ht.ntt_crt[i];
     p->ntt_tab.c_gscale = p->ht.ntt_c_gscale;
-    TRYP(dalloc(p, &p->ntt_res, 4 * n));
+    TRYP(dalloc(p, &p->ntt_res, (size_t)(aao::kNttPrimes + 2) * n));  // residues + int64 quantised rows
     TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));
     p->ntt = true;
   }

@@ -241,21 +241,22 @@ void host_ntt(std::vector<uint64_t>& a, uint64_t p, uint64_t w) {
 void build_ntt_tables(HostTables& t) {
   const int64_t L = t.L, M = t.M;
   const int logL = t.logL;
-  // quantised stencil: G_j = round(g_j 2^(51 - e_g)), g_0 = max |g_j| < 2^e_g
+  constexpr int NP = kNttPrimes, QB = 58;
+  // quantised stencil: G_j = round(g_j 2^(58 - e_g)), g_0 = max |g_j| < 2^e_g
   int eg = 0;
   std::frexp(t.g[0], &eg);
   std::vector<int64_t> G((size_t)M);
-  for (int64_t j = 0; j < M; ++j) G[j] = std::llround(std::ldexp(t.g[j], 51 - eg));
-  t.ntt_c_gscale = t.c * std::ldexp(1.0, eg - 51);
-  t.ntt_twf.assign((size_t)4 * (L / 2) * 2, 0);
-  t.ntt_twi.assign((size_t)4 * (L / 2) * 2, 0);
-  t.ntt_ghat.assign((size_t)4 * L * 2, 0);
-  for (int q = 0; q < 4; ++q) {
+  for (int64_t j = 0; j < M; ++j) G[j] = std::llround(std::ldexp(t.g[j], QB - eg));
+  t.ntt_c_gscale = t.c * std::ldexp(1.0, eg - QB);
+  t.ntt_twf.assign((size_t)NP * L * 2, 0);
+  t.ntt_twi.assign((size_t)NP * L * 2, 0);
+  t.ntt_ghat.assign((size_t)NP * L * 2, 0);
+  for (int q = 0; q < NP; ++q) {
     const uint64_t p = kNttPrime[q];
     const uint64_t w = powmod(kNttGen[q], (p - 1) / (uint64_t)L, p), wi = powmod(w, p - 2, p);
     uint64_t a = 1, b = 1;
-    for (int64_t e = 0; e < L / 2; ++e) {
-      const size_t o = ((size_t)q * (L / 2) + e) * 2;
+    for (int64_t e = 0; e < L; ++e) {
+      const size_t o = ((size_t)q * L + e) * 2;
       t.ntt_twf[o] = (uint32_t)a;
       t.ntt_twf[o + 1] = shoup(a, p);
       t.ntt_twi[o] = (uint32_t)b;
@@ -279,13 +280,13 @@ void build_ntt_tables(HostTables& t) {
       t.ntt_ghat[((size_t)q * L + k) * 2 + 1] = shoup(v, p);
     }
   }
-  const uint64_t p0 = kNttPrime[0], p1 = kNttPrime[1], p2 = kNttPrime[2], p3 = kNttPrime[3];
-  t.ntt_crt[0] = (uint32_t)powmod(p0 % p1, p1 - 2, p1);
-  t.ntt_crt[1] = (uint32_t)powmod(p0 % p2, p2 - 2, p2);
-  t.ntt_crt[2] = (uint32_t)powmod(p1 % p2, p2 - 2, p2);
-  t.ntt_crt[3] = (uint32_t)powmod(p0 % p3, p3 - 2, p3);
-  t.ntt_crt[4] = (uint32_t)powmod(p1 % p3, p3 - 2, p3);
-  t.ntt_crt[5] = (uint32_t)powmod(p2 % p3, p3 - 2, p3);
+  // Garner constants p_a^-1 mod p_b (a < b) in the order (0,1) (0,2) (0,3) (0,4) (1,2) (1,3) (1,4) (2,3) (2,4) (3,4)
+  int o = 0;
+  for (int a = 0; a < NP - 1; ++a)
+    for (int bq = a + 1; bq < NP; ++bq) {
+      const uint64_t pb = kNttPrime[bq];
+      t.ntt_crt[o++] = (uint32_t)powmod(kNttPrime[a] % pb, pb - 2, pb);
+    }
 }
 
 }  // namespace aao

@@ -166,9 +166,9 @@ def test_build_rhs():
 
 
 # ---------------------------------------------------------------- solve
-def solve_case(M, Nt, alpha, prec, inner, recipe="sine8_normal", seed=0):
+def solve_case(M, Nt, alpha, prec, inner, recipe="sine8_normal", seed=0, matvec=aao.AAO_MATVEC_FFT64):
     u0, f = workloads.make_inputs(M, Nt, seed=seed, recipe=recipe)
-    with aao.Plan(M, Nt, alpha, prec=prec, inner=inner) as plan:
+    with aao.Plan(M, Nt, alpha, prec=prec, inner=inner, matvec=matvec) as plan:
         F = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
         U = torch.zeros_like(F)
         plan.build_rhs(cu(u0), cu(f), F)
@@ -190,9 +190,10 @@ def test_gmres_solve_matches_time_stepping(M, Nt, alpha, recipe, prec, bound, in
     assert rel(U, Useq) <= bound, (rel(U, Useq), info)
 
 
-def test_gmres_full_size_config():
+@pytest.mark.parametrize("kind", [aao.AAO_MATVEC_FFT64, aao.AAO_MATVEC_NTT])
+def test_gmres_full_size_config(kind):
     M, Nt, alpha = 8191, 1024, 1.8
-    u0, f, U, info = solve_case(M, Nt, alpha, aao.AAO_PREC_MIXED, aao.AAO_INNER_STRANG)
+    u0, f, U, info = solve_case(M, Nt, alpha, aao.AAO_PREC_MIXED, aao.AAO_INNER_STRANG, matvec=kind)
     K = jac(M, alpha)
     tau = 1.0 / Nt
     F = oaao.build_rhs(u0, f, tau)
