@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--inner", default="strang", choices=["strang", "tau"])
+    ap.add_argument("--inner-tol", type=float, default=None,
+                    help="COCG relative tolerance per shifted system (library default: 1e-6 mixed, 1e-12 fp64)")
     ap.add_argument("--matvec", default="ntt", choices=["fft64", "ntt"],
                     help="1D matvec arithmetic: FP64 FFT convolution or exact NTT convolution of 58-bit rows")
     ap.add_argument("--M", type=int, default=M_DEF)
@@ -338,8 +340,9 @@ def run_ours(args):
     else:
         My = 1
         for i, a in enumerate(ALPHAS):
+            kw = {} if args.inner_tol is None else {"inner_tol": args.inner_tol}
             p = aao.Plan(M, Nt, a, kappa=1.0, T=1.0, prec=prec, inner=inner,
-                         matvec=aao.AAO_MATVEC_NTT if args.matvec == "ntt" else aao.AAO_MATVEC_FFT64)
+                         matvec=aao.AAO_MATVEC_NTT if args.matvec == "ntt" else aao.AAO_MATVEC_FFT64, **kw)
             u0, f = workloads.make_inputs(M, Nt, seed=1000 * rank + i)
             F = torch.empty((Nt, M), dtype=torch.float64, device=dev)
             p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
@@ -461,6 +464,8 @@ def run_ours(args):
                                 "T=1, sine16_normal inputs (seeds 0-2)" % (M, My, Nt, list(ALPHAS_2D))),
                    "M": M, "My": My, "Nt": Nt, "precision": args.prec, "inner_precond": args.inner, "restart": 20,
                    "matvec": args.matvec if args.dim == 1 else "fft64",
+                   "inner_tol": args.inner_tol if args.inner_tol is not None else (1e-6 if args.prec == "mixed"
+                                                                                 else 1e-12),
                    "l2": "no explicit flush: every solve streams a >2 GB Krylov working set through the "
                          "129 MB L2",
                    "outer_iters": [i["outer_iters"] for i in infos],

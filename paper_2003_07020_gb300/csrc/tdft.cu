@@ -14,6 +14,7 @@ namespace aao {
 
 constexpr int TW = 16;   // columns per CTA
 constexpr int TWH = TW / 2;
+constexpr int LU = 8;    // independent global loads in flight per thread (the loads are latency-bound)
 
 template <typename R> __device__ __forceinline__ R ldv(const double* p) { return (R)__ldg(p); }
 
@@ -33,12 +34,22 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const double* __restrict_
   C* tq = sm + TWH * bstride;
   load_quarter(tq, tw, Nt / 4);
   // load y_k = scale_k v_k (real) into position bitrev(k); column cc -> transform cc % TWH, part cc / TWH
-  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
-    const int k = idx / TW, cc = idx - k * TW;
-    const int col = c0 + cc;
-    const R val = (col < M) ? ldv<R>(v + (size_t)k * M + col) * __ldg(&scale[k]) : (R)0;
-    const int q = cc & (TWH - 1), part = cc / TWH;
-    smr[2 * (q * bstride + pad16(bitrev(k, logNt))) + part] = val;
+  for (int base = threadIdx.x; base < Nt * TW; base += LU * blockDim.x) {
+    R vals[LU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int k = idx / TW, col = c0 + (idx - k * TW);
+      vals[u] = (idx < Nt * TW && col < M) ? ldv<R>(v + (size_t)k * M + col) : (R)0;
+    }
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= Nt * TW) break;
+      const int k = idx / TW, cc = idx - k * TW;
+      const int q = cc & (TWH - 1), part = cc / TWH;
+      smr[2 * (q * bstride + pad16(bitrev(k, logNt))) + part] = vals[u] * __ldg(&scale[k]);
+    }
   }
   fft_backward(sm, logNt, TWH, bstride, tq, logNt);  // sum_k y_k exp(+2 pi i nk/Nt), natural order
   const int half = Nt / 2;
@@ -71,14 +82,27 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
   const int half = Nt / 2;
   C* tq = sm + TWH * bstride;
   load_quarter(tq, tw, Nt / 4);
-  for (int idx = threadIdx.x; idx < (half + 1) * TWH; idx += blockDim.x) {
-    const int n = idx / TWH, q = idx - n * TWH;
-    const int ca = c0 + q, cb = c0 + q + TWH;
-    C Xa = (ca < M) ? in[(size_t)n * M + ca] : C{0, 0};
-    C Xb = (cb < M) ? in[(size_t)n * M + cb] : C{0, 0};
-    if (n == 0 || n == half) { Xa.y = 0; Xb.y = 0; }
-    sm[q * bstride + pad16(n)] = C{Xa.x - Xb.y, Xa.y + Xb.x};                  // Xa + i Xb
-    if (n != 0 && n != half) sm[q * bstride + pad16(Nt - n)] = C{Xa.x + Xb.y, Xb.x - Xa.y};  // conj Xa + i conj Xb
+  const int nin = (half + 1) * TWH;
+  for (int base = threadIdx.x; base < nin; base += LU * blockDim.x) {
+    C xa[LU], xb[LU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int n = idx / TWH, q = idx - n * TWH;
+      const int ca = c0 + q, cb = c0 + q + TWH;
+      xa[u] = (idx < nin && ca < M) ? in[(size_t)n * M + ca] : C{0, 0};
+      xb[u] = (idx < nin && cb < M) ? in[(size_t)n * M + cb] : C{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= nin) break;
+      const int n = idx / TWH, q = idx - n * TWH;
+      C Xa = xa[u], Xb = xb[u];
+      if (n == 0 || n == half) { Xa.y = 0; Xb.y = 0; }
+      sm[q * bstride + pad16(n)] = C{Xa.x - Xb.y, Xa.y + Xb.x};                  // Xa + i Xb
+      if (n != 0 && n != half) sm[q * bstride + pad16(Nt - n)] = C{Xa.x + Xb.y, Xb.x - Xa.y};  // conj Xa + i conj Xb
+    }
   }
   fft_forward(sm, logNt, TWH, bstride, tq, logNt);  // sum_n Z_n exp(-2 pi i nk/Nt), bit-reversed
   for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
