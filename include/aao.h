@@ -137,7 +137,12 @@ aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host);
  * Creates a plan for one problem: host FP64 setup of g_k, the circulant
  * embedding spectrum of T, the eigenvalues lambda_n of C_eps (Eq. 1.6a) for
  * n = 0..Nt/2, the inner preconditioner's spectrum, FFT twiddle tables, and
- * all device workspace (about (2m+6) * 8 * M * Nt bytes for restart m).
+ * all device workspace: about (2m+6) * 8 * M * Nt bytes for restart m, plus
+ * 28 * M * Nt bytes of NTT scratch (AAO_MATVEC_NTT) and, for the mixed Strang
+ * path, the per-system spectra of the Strang inverse ((Nt/2+1) * L * 8 bytes,
+ * L the embedding length, a power of two >= 2M).  Mixed 1D plans with
+ * M <= 8192 launch kernels during creation (those spectra, and the CTA-size
+ * autotuner when opts.cocg_threads is 0) and synchronise the stream.
  * cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
  * On failure *out is NULL.
  */

@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(kLineThreads) mv2d_cols(const TIn* __restrict_
 }
 
 // ---------------------------------------------------------------- Step (b), 2D COCG
+constexpr int kLU = 8;  // independent global loads in flight per thread in the line kernels
+
 struct SysState {  // per system, FP64 scalars
   double2 rho, a, beta;
   double nb2, thr;
@@ -175,14 +177,25 @@ __global__ void __launch_bounds__(kLineThreads) c2d_rows_dst(const Cx<R>* __rest
   load_quarter(q, twx, Lx / 4);
   const size_t slab = (size_t)n * Mx * My;
   const int j0 = blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < B * Lx; idx += blockDim.x) {
-    const int b = idx / Lx, l = idx - b * Lx, j = j0 + b;
-    C y{0, 0};
-    if (j < My) {
-      if (l >= 1 && l <= Mx) y = in[slab + (size_t)j * Mx + (l - 1)];
-      else if (l > Mx + 1) { const C t = in[slab + (size_t)j * Mx + (Lx - l - 1)]; y = C{-t.x, -t.y}; }
+  for (int base = threadIdx.x; base < B * Lx; base += kLU * blockDim.x) {
+    C y[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {  // independent loads first (latency-bound otherwise)
+      const int idx = base + u * blockDim.x;
+      const int b = idx / Lx, l = idx - b * Lx, j = j0 + b;
+      y[u] = C{0, 0};
+      if (idx < B * Lx && j < My) {
+        if (l >= 1 && l <= Mx) y[u] = in[slab + (size_t)j * Mx + (l - 1)];
+        else if (l > Mx + 1) { const C t = in[slab + (size_t)j * Mx + (Lx - l - 1)]; y[u] = C{-t.x, -t.y}; }
+      }
     }
-    buf[b * bs + pad16(l)] = y;
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= B * Lx) break;
+      const int b = idx / Lx, l = idx - b * Lx;
+      buf[b * bs + pad16(l)] = y[u];
+    }
   }
   fft_forward(buf, logLx, B, bs, q, logLx);
   R sre = 0, sim = 0;
@@ -222,14 +235,25 @@ __global__ void __launch_bounds__(kLineThreads) c2d_cols_dst_div(const Cx<R>* __
   load_quarter(q, twy, Ly / 4);
   const size_t slab = (size_t)n * Mx * My;
   const int i0 = blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < Ly * B; idx += blockDim.x) {
-    const int l = idx / B, b = idx - l * B, i = i0 + b;
-    C y{0, 0};
-    if (i < Mx) {
-      if (l >= 1 && l <= My) y = in[slab + (size_t)(l - 1) * Mx + i];
-      else if (l > My + 1) { const C t = in[slab + (size_t)(Ly - l - 1) * Mx + i]; y = C{-t.x, -t.y}; }
+  for (int base = threadIdx.x; base < Ly * B; base += kLU * blockDim.x) {
+    C y[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int l = idx / B, b = idx - l * B, i = i0 + b;
+      y[u] = C{0, 0};
+      if (idx < Ly * B && i < Mx) {
+        if (l >= 1 && l <= My) y[u] = in[slab + (size_t)(l - 1) * Mx + i];
+        else if (l > My + 1) { const C t = in[slab + (size_t)(Ly - l - 1) * Mx + i]; y[u] = C{-t.x, -t.y}; }
+      }
     }
-    buf[b * bs + pad16(l)] = y;
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= Ly * B) break;
+      const int l = idx / B, b = idx - l * B;
+      buf[b * bs + pad16(l)] = y[u];
+    }
   }
   const C lam = to_c<R>(lambda[n]);
   const R invL = (R)1 / (R)Ly;
@@ -264,15 +288,29 @@ __global__ void __launch_bounds__(kLineThreads) c2d_rows_conv(const Cx<R>* __res
   const C beta = to_c<R>(st[n].beta);
   const size_t slab = (size_t)n * Mx * My;
   const int j0 = blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < B * Lx; idx += blockDim.x) {
-    const int b = idx / Lx, i = idx - b * Lx, j = j0 + b;
-    C pv{0, 0};
-    if (j < My && i < Mx) {
-      const size_t e = slab + (size_t)j * Mx + i;
-      pv = cadd(Z[e], cmul(beta, P[e]));
-      P[e] = pv;
+  for (int base = threadIdx.x; base < B * Lx; base += kLU * blockDim.x) {
+    C zv[kLU], pv[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int b = idx / Lx, i = idx - b * Lx, j = j0 + b;
+      zv[u] = C{0, 0};
+      pv[u] = C{0, 0};
+      if (idx < B * Lx && j < My && i < Mx) {
+        const size_t e = slab + (size_t)j * Mx + i;
+        zv[u] = Z[e];
+        pv[u] = P[e];
+      }
     }
-    buf[b * bs + pad16(i)] = pv;
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= B * Lx) break;
+      const int b = idx / Lx, i = idx - b * Lx, j = j0 + b;
+      const C p = cadd(zv[u], cmul(beta, pv[u]));
+      if (j < My && i < Mx) P[slab + (size_t)j * Mx + i] = p;
+      buf[b * bs + pad16(i)] = (j < My && i < Mx) ? p : C{0, 0};
+    }
   }
   fft_convolve_batched(buf, logLx, B, bs, q, logLx, [&](int, int pf) { return C{__ldg(&Exf[pf]), (R)0}; });
   for (int idx = threadIdx.x; idx < B * Mx; idx += blockDim.x) {
@@ -301,9 +339,21 @@ __global__ void __launch_bounds__(kLineThreads) c2d_cols_conv(const Cx<R>* __res
   load_quarter(q, twy, Ly / 4);
   const size_t slab = (size_t)n * Mx * My;
   const int i0 = blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < Ly * B; idx += blockDim.x) {
-    const int j = idx / B, b = idx - j * B, i = i0 + b;
-    buf[b * bs + pad16(j)] = (j < My && i < Mx) ? P[slab + (size_t)j * Mx + i] : C{0, 0};
+  for (int base = threadIdx.x; base < Ly * B; base += kLU * blockDim.x) {
+    C pv[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int j = idx / B, b = idx - j * B, i = i0 + b;
+      pv[u] = (idx < Ly * B && j < My && i < Mx) ? P[slab + (size_t)j * Mx + i] : C{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= Ly * B) break;
+      const int j = idx / B, b = idx - j * B;
+      buf[b * bs + pad16(j)] = pv[u];
+    }
   }
   fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int, int pf) { return C{__ldg(&Eyf[pf]), (R)0}; });
   const C lam = to_c<R>(lambda[n]);

@@ -117,3 +117,12 @@ def test_plan_create_validates_launch_options_without_gpu(lib):
         o = aao.default_opts(**kw)
         assert lib.aao_plan_create(ctypes.byref(prob), ctypes.byref(o), None, ctypes.byref(h)) == aao.AAO_EINVAL, kw
     assert lib.aao_plan_get_tuning(None, None) == aao.AAO_EINVAL
+
+
+def test_plan_create_rejects_bad_matvec_kind_without_gpu(lib):
+    prob = aao.AaoProblem(1, 63, 16, 1.0, 1.5, 1.0, 0.0, 0, 1.5, 1.0)
+    h = ctypes.c_void_p()
+    o = aao.default_opts(matvec=7)
+    assert lib.aao_plan_create(ctypes.byref(prob), ctypes.byref(o), None, ctypes.byref(h)) == aao.AAO_EINVAL
+    o = aao.default_opts()
+    assert o.matvec == aao.AAO_MATVEC_NTT and o.use_graphs == 1 and o.cocg_threads == 0
