@@ -242,6 +242,9 @@ MATVEC_DRAM_BYTES_PER_ROW_M8191 = 17.018e6 / 128
 # ntt_epilogue_kernel read 8.40 + 10.43 + 37.76 MB and write 0 per 128-row launch triple
 # (profiles/ntt_matvec_small_full.md).
 NTT_DRAM_BYTES_PER_ROW_M8191 = (8.396e6 + 10.441e6 + 37.762e6) / 128
+# DRAM bytes of cocg_reg_kernel<Strang spectra> per shifted system at M = 8191 (13.21 MB read + 0.03 MB
+# written for 65 systems; profiles/cocg_reg_matvec_small_full.md): the per-system spectrum and tables.
+COCG_DRAM_BYTES_PER_SYSTEM_M8191 = (13.207e6 + 0.028e6) / 65
 # Lazy Shoup butterfly issue rate measured on GB300 (dependent-chain probe): 6.27 per clock per SM.
 NTT_PEAK_GBFLY = 6.27 * 152 * 2.07
 
@@ -272,15 +275,16 @@ def matvec_flops(M, Nt):
     return Nt * (2 * fft_flops(L // 2) + 20.0 * (L // 2) + 5.0 * M)
 
 
-def cocg_flops(M, inner, inner_iters_sum, n_apply, nsys):
+def cocg_flops(M, inner, inner_iters_sum, n_apply, nsys, strang_ffts=4):
     """Algorithmic flops of Step (b): per COCG iteration one Toeplitz product
-    (2 complex FFTs of L) plus one preconditioner solve (Strang: 4, tau: 2
-    complex FFTs of L) and ~40 flops per point of vector updates; each system
-    also applies the preconditioner once before its first iteration."""
+    (2 complex FFTs of L) plus one preconditioner solve (tau: 2 complex FFTs of L;
+    Strang: 2 with the precomputed circulant spectra of the mixed path, 4 by
+    Bluestein) and ~40 flops per point of vector updates; each system also applies
+    the preconditioner once before its first iteration."""
     L = 4
     while L < 2 * M:
         L *= 2
-    pre = (4 if inner == "strang" else 2) * fft_flops(L)
+    pre = (strang_ffts if inner == "strang" else 2) * fft_flops(L)
     per_it = 2 * fft_flops(L) + pre + 40.0 * M
     return inner_iters_sum * per_it + n_apply * nsys * pre
 
@@ -440,13 +444,18 @@ def run_ours(args):
                 "traffic_source": "ncu dram bytes of a 128-row launch scaled to Nt rows" if traffic else None}
     elif dom == "cocg":
         t_launch = prof["cocg"][0] / max(n_apply, 1)  # per preconditioner apply
-        fl = (cocg_flops(M, args.inner, inner_sum, n_apply, nsys) if args.dim == 1 else
-              cocg2d_flops(M, My, inner_sum, n_apply, nsys)) / max(n_apply, 1)
+        reg = args.dim == 1 and args.prec == "mixed" and M <= 8192  # register kernel, Strang spectra
+        fl = (cocg_flops(M, args.inner, inner_sum, n_apply, nsys, strang_ffts=2 if reg else 4) if args.dim == 1
+              else cocg2d_flops(M, My, inner_sum, n_apply, nsys)) / max(n_apply, 1)
         pkv = FP32_PEAK_TFLOPS if args.prec == "mixed" else FP64_PEAK_TFLOPS
         achieved = fl / (t_launch * 1e-3) / 1e12
+        traffic = (COCG_DRAM_BYTES_PER_SYSTEM_M8191 * nsys
+                   if (reg and args.inner == "strang" and M == 8191) else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": pkv, "unit": "TFLOP/s", "frac": achieved / pkv,
-                "traffic": None, "kernel": "cocg_kernel",
-                "peak_source": "FMA issue rate x 152 SMs x 2.07 GHz (derived)"}
+                "traffic": traffic,
+                "kernel": ("cocg_reg_kernel" if reg else ("c2d line kernels" if args.dim == 2 else "cocg_kernel")),
+                "peak_source": "FMA issue rate x 152 SMs x 2.07 GHz (derived)",
+                "traffic_source": "ncu dram bytes of a 65-system launch scaled to the systems" if traffic else None}
     else:
         t_launch = prof[dom][0] / max(prof[dom][1], 1)
         hb = pk.get("hbm_gbs", 6800.0)

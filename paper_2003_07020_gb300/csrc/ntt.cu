@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(512) ntt_conv_kernel(const long long* __restri
 template <int Q> __device__ __forceinline__ uint64_t md(uint64_t x) { return x % (uint64_t)Prime<Q>::p; }
 
 // Garner's mixed-radix digits d_q of the residues r_q, then
-// Y = d0 + p0 (d1 + p1 (d2 + p2 (d3 + p3 d4))) in FP64, negative when d4 > p4 / 2
-// (|Y| < 2^129, far below half the product of the primes).
+// Y = d0 + p0 (d1 + p1 (d2 + p2 (d3 + p3 d4))) in integer arithmetic, converted to FP64 once
+// (correctly rounded); negative when d4 > p4 / 2 (|Y| < 2^129, far below half the product).
 __device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint32_t* c) {
   constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p, p4 = Prime<4>::p;
   // c: p0^-1 mod p1..p4 (c[0..3]), p1^-1 mod p2..p4 (c[4..6]), p2^-1 mod p3, p4 (c[7..8]), p3^-1 mod p4 (c[9])
@@ -273,12 +273,54 @@ __device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint32_t*
   t = md<4>((t + p4 - md<4>(d1)) * c[6]);
   t = md<4>((t + p4 - md<4>(d2)) * c[8]);
   const uint64_t d4 = md<4>((t + p4 - md<4>(d3)) * c[9]);
-  auto u2d = [](uint64_t d) { return __uint2double_rn((uint32_t)d); };  // digits < 2^30
-  if (d4 <= p4 / 2)
-    return ((((u2d(d4) * p3 + u2d(d3)) * p2 + u2d(d2)) * p1 + u2d(d1)) * p0 + u2d(d0));
-  // negative: Y = -(P - Y), P - 1 - Y has the complemented digits p_q - 1 - d_q
-  return -(((((u2d(p4 - 1 - d4) * p3 + u2d(p3 - 1 - d3)) * p2 + u2d(p2 - 1 - d2)) * p1 + u2d(p1 - 1 - d1)) * p0 +
-            u2d(p0 - 1 - d0)) + 1.0);
+  // Y (|Y| < 2^129) as a 3-limb integer from the mixed-radix digits, negative when d4 > p4 / 2
+  // (then |Y| = (P - 1 - Y) + 1 with the complemented digits p_q - 1 - d_q), converted once.
+  const bool neg = d4 > p4 / 2;
+  const uint64_t e[NP] = {neg ? p0 - 1 - d0 : d0, neg ? p1 - 1 - d1 : d1, neg ? p2 - 1 - d2 : d2,
+                          neg ? p3 - 1 - d3 : d3, neg ? p4 - 1 - d4 : d4};
+  const uint64_t pm[4] = {p0, p1, p2, p3};
+  uint64_t l0 = e[4], l1 = 0, l2 = 0;
+#pragma unroll
+  for (int q = 3; q >= 0; --q) {  // (l2, l1, l0) = (l2, l1, l0) * p_q + e_q
+    const uint64_t m = pm[q];
+    const uint64_t lo0 = l0 * m, hi0 = __umul64hi(l0, m);
+    const uint64_t lo1 = l1 * m, hi1 = __umul64hi(l1, m);
+    const uint64_t n0 = lo0 + e[q];
+    const uint64_t c0 = n0 < lo0;
+    const uint64_t s1 = lo1 + hi0;
+    uint64_t c1 = s1 < lo1;
+    const uint64_t n1 = s1 + c0;
+    c1 += n1 < s1;
+    l2 = l2 * m + hi1 + c1;
+    l1 = n1;
+    l0 = n0;
+  }
+  if (neg) {  // + 1
+    l0 += 1;
+    const uint64_t c = l0 == 0;
+    l1 += c;
+    l2 += (c && l1 == 0);
+  }
+  // top 64 significant bits with a sticky bit (correct rounding), times 2^shift
+  uint64_t top;
+  int sh;
+  if (l2) {
+    const int z = __clzll(l2);
+    top = z ? (l2 << z) | (l1 >> (64 - z)) : l2;
+    const uint64_t rest = z ? (l1 << z) | l0 : (l1 | l0);
+    top |= (rest != 0);
+    sh = 128 - z;
+  } else if (l1) {
+    const int z = __clzll(l1);
+    top = z ? (l1 << z) | (l0 >> (64 - z)) : l1;
+    top |= (z ? (l0 << z) : l0) != 0;
+    sh = 64 - z;
+  } else {
+    top = l0;
+    sh = 0;
+  }
+  const double mag = __ull2double_rn(top) * __longlong_as_double((long long)(1023 + sh) << 52);
+  return neg ? -mag : mag;
 }
 
 template <typename TIn>
