@@ -1,0 +1,300 @@
+// Register-resident FP32 COCG for Step (b) (Sec. 3.1), shared by the translation units that
+// instantiate it (cocg.cu: the Bluestein Strang form; cocg_reg_tau.cu and cocg_reg_sconv.cu:
+// the tau matrix and the precomputed Strang spectra, each for every CTA size and with or without
+// a learned initial guess).  Splitting the instantiations keeps each file's compile short and
+// lets them build in parallel.
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace aao {
+
+template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
+  const auto d = b.x * b.x + b.y * b.y;
+  return C{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+
+// ---- FP32 path with register-resident vectors -------------------------------------------
+// NT threads (64 .. 512, chosen per problem by the autotuner of plan creation); thread t owns
+// elements i = t + NT j, j < 16 (M <= 16 NT), so r and p live in registers for the whole solve
+// and only x is updated in global memory.  Every variant keeps <= 128 registers per thread so
+// that 512 / NT CTAs fit on an SM.
+constexpr int kRegMaxThreads = 512;
+constexpr int kRegElems = 16;
+
+// KIND 0: Strang by Bluestein (4 FFTs of L); 1: natural tau matrix by DST-I (2 FFTs); 2: Strang by
+// the precomputed per-system circulant spectrum sc (2 FFTs).  The result is read by zval().
+template <int KIND, int NT>
+__device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegElems], int M, int logL, float2 lam,
+                                            const CocgTables32& tb, const float2* q, const float2* pt,
+                                            const float2* __restrict__ sc) {
+  const int L = 1 << logL;
+  const int t = threadIdx.x;
+  if constexpr (KIND == 2) {
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < L) buf[pad16(i)] = (i < M) ? r[j] : float2{0, 0};
+    }
+    for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+    fft_convolve(buf, logL, q, logL, [&](int p) { return __ldg(&sc[p]); }, pt);
+  } else if constexpr (KIND == 0) {
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < L) buf[pad16(i)] = (i < M) ? cmul(r[j], __ldg(&tb.chirp[i])) : float2{0, 0};
+    }
+    for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+    fft_convolve(buf, logL, q, logL, [&](int p) { return __ldg(&tb.chat_br[p]); }, pt);
+    const float invM = 1.0f / (float)M;
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int k = t + NT * j;
+      if (k < M) {
+        float2 d = lam;
+        d.x += __ldg(&tb.seig[k]);
+        buf[pad16(k)] = cscale(cdiv(buf[pad16(k)], d), invM);
+      } else if (k < L) {
+        buf[pad16(k)] = float2{0, 0};
+      }
+    }
+    for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+    fft_convolve(buf, logL, q, logL, [&](int p) { return cconj(__ldg(&tb.chat_br[p])); }, pt);
+  } else {
+    (void)sc;
+    if (t == 0) {
+      buf[pad16(0)] = float2{0, 0};
+      buf[pad16(M + 1)] = float2{0, 0};
+    }
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) {
+        buf[pad16(i + 1)] = r[j];
+        buf[pad16(L - 1 - i)] = float2{-r[j].x, -r[j].y};
+      }
+    }
+    const int Mp1 = M + 1;
+    const float invL = 1.0f / (float)L;
+    fft_convolve(buf, logL, q, logL, [&](int p) {
+      float2 d = lam;
+      d.x += __ldg(&tb.taueig_br[p]);
+      return cdiv(float2{invL, 0}, d);
+    }, pt);
+    (void)Mp1;
+  }
+}
+
+// Element i of the preconditioned residual left in buf by precond_reg<KIND>.
+template <int KIND>
+__device__ __forceinline__ float2 zval(const float2* buf, const CocgTables32& tb, int i) {
+  if constexpr (KIND == 0) return cmulc(buf[pad16(i)], __ldg(&tb.chirp[i]));
+  else if constexpr (KIND == 1) return buf[pad16(i + 1)];
+  else return buf[pad16(i)];
+}
+
+template <int KIND, bool WARM, int NT>
+__global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
+    cocg_reg_kernel(float2* __restrict__ xb, const float2* __restrict__ x0b, int M, int logL, int nsys,
+                    CocgTables32 tb, float tol, int maxit, int* __restrict__ iters, int* __restrict__ flags) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ float red[4 * 32];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* q = buf + padded_size(1 << logL);
+  float2* pt = q + (1 << logL) / 4;  // per-pass twiddle tables
+  const int L = 1 << logL;
+  const int t = threadIdx.x;
+  load_quarter(q, tb.twL, L / 4);
+  __syncthreads();
+  build_pass_tables(pt, q, logL, logL);
+  for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
+    const double2 lamd = tb.lambda[n];
+    const float2 lam{(float)lamd.x, (float)lamd.y};
+    float2* x = xb + (size_t)n * M;
+    const float2* sc = KIND == 2 ? tb.sconv + ((size_t)n << logL) : nullptr;
+    float2 r[kRegElems], p[kRegElems];
+    float nb2[1] = {0};
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      r[j] = (i < M) ? x[i] : float2{0, 0};
+      nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+    }
+    block_sum<float, 1>(nb2, red);
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) x[i] = float2{0, 0};
+    }
+    if (nb2[0] == 0.0f) {
+      if (t == 0) { iters[n] = 0; flags[n] = 0; }
+      continue;
+    }
+    const float thr = tol * tol * nb2[0];
+    int accepted = 0;
+    if constexpr (WARM) {
+      // warm start: r0 = b - (lambda I + c T) x0, kept only if ||r0|| < ||b||
+      const float2* x0 = x0b + (size_t)n * M;
+      float2 w[kRegElems];
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        w[j] = (i < M) ? x0[i] : float2{0, 0};
+        if (i < L) buf[pad16(i)] = w[j];
+      }
+      for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+      fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
+      float r02[1] = {0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        if (i < M) {
+          const float2 rj = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
+          r02[0] += rj.x * rj.x + rj.y * rj.y;
+        }
+      }
+      block_sum<float, 1>(r02, red);
+      if (r02[0] < nb2[0]) {  // uniform across the block
+        accepted = 1;
+#pragma unroll
+        for (int j = 0; j < kRegElems; ++j) {
+          const int i = t + NT * j;
+          if (i < M) {
+            r[j] = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
+            x[i] = w[j];
+          }
+        }
+        if (r02[0] <= thr) {
+          if (t == 0) { iters[n] = 0; flags[n] = 4; }
+          __syncthreads();
+          continue;
+        }
+      }
+      __syncthreads();
+    }
+    // z = P^{-1} r, p = z, rho = r^T z
+    precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
+    float rho2[2] = {0, 0};
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      float2 z{0, 0};
+      if (i < M) z = zval<KIND>(buf, tb, i);
+      p[j] = z;
+      rho2[0] += r[j].x * z.x - r[j].y * z.y;
+      rho2[1] += r[j].x * z.y + r[j].y * z.x;
+    }
+    block_sum<float, 2>(rho2, red);
+    float2 rho{rho2[0], rho2[1]};
+    int it = 0, flag = 1;
+    while (it < maxit) {
+      // q = (lambda I + c T) p
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        if (i < L) buf[pad16(i)] = (i < M) ? p[j] : float2{0, 0};
+      }
+      for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+      fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
+      float pq2[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        if (i < M) {
+          const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
+          pq2[0] += p[j].x * qq.x - p[j].y * qq.y;
+          pq2[1] += p[j].x * qq.y + p[j].y * qq.x;
+        }
+      }
+      block_sum<float, 2>(pq2, red);
+      const float2 pq{pq2[0], pq2[1]};
+      if (!(pq.x * pq.x + pq.y * pq.y > 0.0f)) { flag = 2; break; }
+      const float2 a = cdiv(rho, pq);
+      float rr[1] = {0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        if (i < M) {
+          const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
+          x[i] = cadd(x[i], cmul(a, p[j]));
+          r[j] = csub(r[j], cmul(a, qq));
+          rr[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+        }
+      }
+      block_sum<float, 1>(rr, red);
+      ++it;
+      if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
+      if (rr[0] <= thr) { flag = 0; break; }
+      precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
+      float rn2[2] = {0, 0};
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        if (i < M) {
+          const float2 z = zval<KIND>(buf, tb, i);
+          rn2[0] += r[j].x * z.x - r[j].y * z.y;
+          rn2[1] += r[j].x * z.y + r[j].y * z.x;
+        }
+      }
+      block_sum<float, 2>(rn2, red);
+      const float2 rho_new{rn2[0], rn2[1]};
+      if (!(rho.x * rho.x + rho.y * rho.y > 0.0f)) { flag = 2; break; }
+      const float2 beta = cdiv(rho_new, rho);
+      rho = rho_new;
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        float2 z{0, 0};
+        if (i < M) z = zval<KIND>(buf, tb, i);
+        p[j] = cadd(z, cmul(beta, p[j]));
+      }
+      __syncthreads();
+    }
+    if (t == 0) { iters[n] = it; flags[n] = flag | (accepted << 2); }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+static size_t cocg_smem(int logL) { return (size_t)padded_size(1 << logL) * sizeof(typename cplx_t<R>::type); }
+template <typename R>
+static size_t cocg_table_bytes(int logL) { return (size_t)(1 << (logL - 2)) * sizeof(typename cplx_t<R>::type); }
+static inline size_t cocg_reg_smem(int logL) {
+  return cocg_smem<float>(logL) + cocg_table_bytes<float>(logL) + (size_t)pass_table_size(logL) * sizeof(float2);
+}
+
+template <int KIND, bool WARM, int NT>
+static cudaError_t launch_reg_one(float2* xb, const float2* x0, int M, int logL, int nsys, const CocgTables32& tb,
+                                  float tol, int maxit, int* iters, int* flags, int grid, cudaStream_t s) {
+  auto kern = cocg_reg_kernel<KIND, WARM, NT>;
+  cudaError_t e = allow_max_dynamic_smem(kern);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, NT, cocg_reg_smem(logL), s>>>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags);
+  return cudaGetLastError();
+}
+
+// Every CTA size (64 .. 512) and both initial-guess forms of one preconditioner kind.
+template <int KIND>
+static cudaError_t launch_reg_kind(float2* xb, const float2* x0, int M, int logL, int nsys, const CocgTables32& tb,
+                                   float tol, int maxit, int* iters, int* flags, int grid, int nt, cudaStream_t s) {
+#define AAO_REG_NT(N)                                                                                      \
+  case N:                                                                                                  \
+    return x0 ? launch_reg_one<KIND, true, N>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s) \
+              : launch_reg_one<KIND, false, N>(xb, x0, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+  switch (nt) {
+    AAO_REG_NT(64)
+    AAO_REG_NT(128)
+    AAO_REG_NT(256)
+    AAO_REG_NT(512)
+    default: return cudaErrorInvalidValue;
+  }
+#undef AAO_REG_NT
+}
+
+// Per-kind entry points (defined in cocg_reg_tau.cu and cocg_reg_sconv.cu).
+cudaError_t launch_cocg_reg_tau(float2* xb, const float2* x0, int M, int logL, int nsys, const CocgTables32& tb,
+                                float tol, int maxit, int* iters, int* flags, int grid, int nt, cudaStream_t s);
+cudaError_t launch_cocg_reg_sconv(float2* xb, const float2* x0, int M, int logL, int nsys, const CocgTables32& tb,
+                                  float tol, int maxit, int* iters, int* flags, int grid, int nt, cudaStream_t s);
+
+}  // namespace aao
