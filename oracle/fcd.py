@@ -18,14 +18,19 @@ def fcd_weights(alpha, n):
     g_k = (-1)^k Gamma(1+alpha) / (Gamma(1+alpha/2-k) Gamma(1+alpha/2+k)),
     evaluated through log|Gamma| and the sign of Gamma (both library
     routines), so that it does not overflow for large k.  For 1 < alpha < 2
-    none of the Gamma arguments is a pole.
+    none of the Gamma arguments is a pole; for alpha = 2 the argument
+    1 + alpha/2 - k is a pole for every k >= 2, where 1/Gamma vanishes, so
+    those weights are exactly 0 (the classical second difference [2, -1]).
     """
     k = np.arange(n, dtype=np.float64)
     a = float(alpha)
-    lg = gammaln(1.0 + a) - gammaln(1.0 + a / 2.0 - k) - gammaln(1.0 + a / 2.0 + k)
-    sgn = ((-1.0) ** k) * gammasgn(1.0 + a) * gammasgn(1.0 + a / 2.0 - k) \
-        * gammasgn(1.0 + a / 2.0 + k)
-    return sgn * np.exp(lg)
+    arg = 1.0 + a / 2.0 - k
+    pole = (arg <= 0) & (arg == np.floor(arg))
+    with np.errstate(invalid="ignore"):
+        lg = gammaln(1.0 + a) - gammaln(arg) - gammaln(1.0 + a / 2.0 + k)
+        sgn = ((-1.0) ** k) * gammasgn(1.0 + a) * gammasgn(arg) * gammasgn(1.0 + a / 2.0 + k)
+        g = sgn * np.exp(lg)
+    return np.where(pole, 0.0, g)
 
 
 def toeplitz_T(alpha, M):

@@ -78,3 +78,9 @@ def test_jacobian_2d_is_kronecker_sum():
     # acting on U[j, i] (x fastest): K vec(U) = vec(U Kx^T + Ky U)
     U = np.random.default_rng(0).standard_normal((4, 5))
     np.testing.assert_allclose(K @ U.ravel(), (U @ Kx.T + Ky @ U).ravel(), rtol=1e-13, atol=1e-13)
+
+
+def test_alpha_two_is_the_classical_second_difference():
+    """Lemma 2.2 at alpha = 2: the weights are [2, -1, 0, ...] exactly (1/Gamma vanishes at its poles)."""
+    g = fcd.fcd_weights(2.0, 64)
+    assert g[0] == 2.0 and g[1] == -1.0 and np.all(g[2:] == 0.0)
