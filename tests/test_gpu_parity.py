@@ -268,3 +268,25 @@ def test_ntt_matvec_edge_rows():
         torch.cuda.synchronize()
         W = host(w)
         assert np.isnan(W[5]).all() and np.isfinite(W[:5]).all()
+
+
+@pytest.mark.parametrize("alpha,kappa,T", [(2.0, 1.0, 1.0), (1.01, 1.0, 1.0), (1.5, 0.01, 2.0), (1.9, 3.0, 0.5)])
+@pytest.mark.parametrize("prec", [aao.AAO_PREC_MIXED, aao.AAO_PREC_FP64])
+def test_gmres_parameter_extremes(alpha, kappa, T, prec):
+    """alpha = 2 (the classical Laplacian stencil [2, -1]: the quantised stencil tail is exactly zero), alpha near
+    1, the small kappa of the paper's tables, and T != 1 (tau = T / Nt), against sequential BDF2."""
+    M, Nt = 127, 32
+    u0, f = workloads.make_inputs(M, Nt, seed=11)
+    tau = T / Nt
+    with aao.Plan(M, Nt, alpha, kappa=kappa, T=T, prec=prec) as plan:
+        F = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.build_rhs(cu(u0), cu(f), F)
+        U = torch.zeros_like(F)
+        info = plan.gmres_solve(F, U)
+    K = fcd.jacobian_1d(alpha, kappa, M, 1.0 / (M + 1))
+    Fh = oaao.build_rhs(u0, f, tau)
+    trr = oaao.true_relative_residual(K, tau, Fh, host(U))
+    assert info["true_rel_res"] <= 1e-10 and trr <= 1e-10, (info, trr)
+    Useq = oaao.sequential_bdf2(K, tau, u0, f)
+    bound = 1e-10 if prec == aao.AAO_PREC_FP64 else 1e-9
+    assert rel(host(U), Useq) <= bound, rel(host(U), Useq)
