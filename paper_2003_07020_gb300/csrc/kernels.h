@@ -88,9 +88,31 @@ cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s);
 constexpr int kNttPrimes = 5;
 constexpr uint32_t kNttPrime[kNttPrimes] = {1004535809u, 998244353u, 985661441u, 943718401u, 880803841u};
 constexpr uint32_t kNttGen[kNttPrimes] = {3u, 3u, 3u, 7u, 26u};
+// Twiddle tables of the transforms, per prime and direction, in the order the passes read
+// them: 8 constant roots w^(e L / Rmax) (Rmax = min(16, L)), then for every pass but the last
+// (stages s0 .. s0 + r - 1, r = min(4, logL - s0), S = L >> (s0 + r)) its (2^r - 1) S external
+// twiddles w^(j bitrev_r(k) 2^s0) at (k - 1) S + j, so that consecutive threads (consecutive j)
+// read consecutive entries.  Each entry is (w, floor(w 2^32 / p)).
+#ifdef __CUDACC__
+#define AAO_HD __host__ __device__
+#else
+#define AAO_HD
+#endif
+AAO_HD inline int ntt_pass_r(int logL, int s0) { return logL - s0 < 4 ? logL - s0 : 4; }
+AAO_HD inline int ntt_last_pass(int logL) { return ((logL - 1) / 4) * 4; }
+AAO_HD inline int ntt_tw_offset(int logL, int s0) {
+  int off = 8;
+  for (int t = 0; t < s0; t += 4) {
+    const int r = ntt_pass_r(logL, t);
+    off += ((1 << r) - 1) * (1 << (logL - t - r));
+  }
+  return off;
+}
+AAO_HD inline int ntt_tw_size(int logL) { return ntt_tw_offset(logL, ntt_last_pass(logL)); }
+#undef AAO_HD
 struct NttTables {
-  const uint2* twf;     // [5][L] (w^e, floor(w^e 2^32 / p)), w a primitive L-th root mod p
-  const uint2* twi;     // [5][L] inverse roots
+  const uint2* twf;     // [5][ntt_tw_size(logL)] forward roots w (a primitive L-th root mod p), layout above
+  const uint2* twi;     // [5][ntt_tw_size(logL)] the same for w^-1
   const uint2* ghat;    // [5][L] stencil spectrum, bit-reversed, times L^-1
   uint32_t crt[10];     // Garner constants: p0^-1 mod p1..p4, p1^-1 mod p2..p4, p2^-1 mod p3, p4, p3^-1 mod p4
   double c_gscale;      // c 2^(e_g - 58)

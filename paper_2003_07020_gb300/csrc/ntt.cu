@@ -18,12 +18,18 @@
 // quantised row mod p, forward NTT, multiply by the stencil spectrum (stored
 // bit-reversed, L^-1 folded in), inverse NTT, write the residues of the first
 // M outputs.
-// The transforms run in passes of r <= 4 radix-2 stages: each thread loads a
-// group of 2^r elements at stride S = L / 2^(s0 + r) from shared memory into
-// registers, applies the 2^r-point transform with constant roots, multiplies
-// by the external twiddles w^(j bitrev_r(k) 2^s0) (DIF; conjugate order for
-// the DIT inverse) and stores back (natural order in, bit-reversed out, and
-// back).  Shared memory is padded by one word per 32 (conflict-free strides).
+// The transforms run in passes of r <= 4 radix-2 stages: each thread takes a
+// group of 2^r elements at stride S = L / 2^(s0 + r) into registers, applies
+// the 2^r-point transform with constant roots, multiplies by the external
+// twiddles w^(j bitrev_r(k) 2^s0) (DIF; conjugate order for the DIT inverse)
+// and stores back (natural order in, bit-reversed out, and back).  The
+// twiddles are stored pass by pass in the order the threads read them
+// (coalesced).  The first forward pass reads its group straight from the
+// quantised row (the upper half of the embedding is zero), the last forward
+// pass, the spectrum product and the first inverse pass are one register pass
+// (stride 1, no external twiddles), and the last inverse pass writes the
+// residues straight to global memory, so shared memory sees 2 (log2 L / 4) - 1
+// read-write sweeps per row.  Shared memory is padded by one word per 32.
 // Kernel 2 (ntt_epilogue_kernel): one CTA per row: Garner CRT of the five
 // residues, scaling, the BDF band of C (Eq. 1.7), optional residual rhs - w and
 // per-row sums of squares (as the FP64 matvec).
@@ -69,17 +75,45 @@ __device__ __forceinline__ void dit2(uint32_t& x, uint32_t& y, uint2 w) {
   y = red2<P>(d);
 }
 
-template <int r> __device__ __forceinline__ constexpr int brev_r(int k) {
-  int o = 0;
-  for (int b = 0; b < r; ++b) o |= ((k >> b) & 1) << (r - 1 - b);
-  return o;
+// The 2^r-point transforms with constant roots wint[e] = w^(e L / R): DIF (natural order in,
+// bit-reversed out) and its inverse DIT.
+template <uint32_t P, int r>
+__device__ __forceinline__ void dif_core(uint32_t (&v)[1 << r], const uint2 (&wint)[8]) {
+  constexpr int R = 1 << r;
+#pragma unroll
+  for (int t = 0; t < r; ++t) {
+    const int half = R >> (t + 1);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (k & half) continue;
+      const int e = (k % half) << t;  // power of w^(L/R)
+      if (e == 0) dif2<P, true>(v[k], v[k + half], wint[0]);
+      else dif2<P, false>(v[k], v[k + half], wint[e]);
+    }
+  }
+}
+template <uint32_t P, int r>
+__device__ __forceinline__ void dit_core(uint32_t (&v)[1 << r], const uint2 (&wint)[8]) {
+  constexpr int R = 1 << r;
+#pragma unroll
+  for (int t = r - 1; t >= 0; --t) {
+    const int half = R >> (t + 1);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (k & half) continue;
+      const int e = (k % half) << t;
+      if (e == 0) dit2<P, true>(v[k], v[k + half], wint[0]);
+      else dit2<P, false>(v[k], v[k + half], wint[e]);
+    }
+  }
 }
 
-// One forward pass of r stages starting at stage s0 (see the file comment).  wint[e] = w^(e L / R).
-template <uint32_t P, int r>
+// A middle forward pass of 4 stages starting at stage s0 (see the file comment); tw is this
+// pass's table: w^(j bitrev_4(k) 2^s0) at (k - 1) S + j.
+template <uint32_t P>
 __device__ __forceinline__ void dif_pass(uint32_t* buf, int logL, int s0, const uint2* __restrict__ tw,
                                          const uint2 (&wint)[8]) {
-  constexpr int R = 1 << r;
+  constexpr int r = 4, R = 16;
   const int L = 1 << logL, logS = logL - s0 - r, S = 1 << logS;
   for (int g = threadIdx.x; g < (L >> r); g += blockDim.x) {
     const int b = g >> logS, j = g & (S - 1);
@@ -87,96 +121,136 @@ __device__ __forceinline__ void dif_pass(uint32_t* buf, int logL, int s0, const 
     uint32_t v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = buf[pad32(base + k * S)];
-#pragma unroll
-    for (int t = 0; t < r; ++t) {
-      const int half = R >> (t + 1);
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        if (k & half) continue;
-        const int e = (k % half) << t;  // power of w^(L/R)
-        if (e == 0) dif2<P, true>(v[k], v[k + half], wint[0]);
-        else dif2<P, false>(v[k], v[k + half], wint[e]);
-      }
-    }
-    const int jj = j << s0;
+    dif_core<P, r>(v, wint);
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      if (k) v[k] = mulsh<P>(v[k], __ldg(&tw[jj * brev_r<r>(k)]));
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&tw[(k - 1) * S + j]));
       buf[pad32(base + k * S)] = v[k];
     }
   }
 }
 
-// Inverse of dif_pass with the inverse roots (twi, wint = w^(-e L / R)).
-template <uint32_t P, int r>
+// The inverse of dif_pass with the inverse table (w^-1 in place of w).
+template <uint32_t P>
 __device__ __forceinline__ void dit_pass(uint32_t* buf, int logL, int s0, const uint2* __restrict__ twi,
                                          const uint2 (&wint)[8]) {
-  constexpr int R = 1 << r;
+  constexpr int r = 4, R = 16;
   const int L = 1 << logL, logS = logL - s0 - r, S = 1 << logS;
   for (int g = threadIdx.x; g < (L >> r); g += blockDim.x) {
     const int b = g >> logS, j = g & (S - 1);
     const int base = (b << (logL - s0)) + j;
-    const int jj = j << s0;
     uint32_t v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       v[k] = buf[pad32(base + k * S)];
-      if (k) v[k] = mulsh<P>(v[k], __ldg(&twi[jj * brev_r<r>(k)]));
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&twi[(k - 1) * S + j]));
     }
-#pragma unroll
-    for (int t = r - 1; t >= 0; --t) {
-      const int half = R >> (t + 1);
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        if (k & half) continue;
-        const int e = (k % half) << t;
-        if (e == 0) dit2<P, true>(v[k], v[k + half], wint[0]);
-        else dit2<P, false>(v[k], v[k + half], wint[e]);
-      }
-    }
+    dit_core<P, r>(v, wint);
 #pragma unroll
     for (int k = 0; k < R; ++k) buf[pad32(base + k * S)] = v[k];
   }
 }
 
-// wint[e] = tab[e L / R] for e < R / 2
+// x mod p in [0, p) for a signed 64-bit x
+template <uint32_t P> __device__ __forceinline__ uint32_t residue(long long x) {
+  long long m = x % (long long)P;
+  if (m < 0) m += P;
+  return (uint32_t)m;
+}
+
+// The first forward pass (stages 0..3, stride S = L / 16) reading the quantised row from global
+// memory: element i = j + k S is V[i] mod p for i < M, else 0 (the circulant embedding's padding;
+// the plan takes L >= 2M, so the upper half of every group is zero).
+template <uint32_t P>
+__device__ __forceinline__ void dif_first(const long long* __restrict__ Vk, int M, uint32_t* buf, int logL,
+                                          const uint2* __restrict__ tw, const uint2 (&wint)[8]) {
+  constexpr int r = 4, R = 16;
+  const int S = 1 << (logL - r);
+  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {  // L >= 2M: elements k >= R / 2 lie in the zero half
+      const int i = j + k * S;
+      v[k] = (k < R / 2 && i < M) ? residue<P>(__ldg(Vk + i)) : 0u;
+    }
+    dif_core<P, r>(v, wint);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&tw[(k - 1) * S + j]));
+      buf[pad32(j + k * S)] = v[k];
+    }
+  }
+}
+
+// The last inverse pass (stages 3..0, stride S = L / 16) writing the residues of the first M
+// outputs to global memory.
+template <uint32_t P>
+__device__ __forceinline__ void dit_last(const uint32_t* buf, int logL, int M, const uint2* __restrict__ twi,
+                                         const uint2 (&wint)[8], uint32_t* __restrict__ out) {
+  constexpr int r = 4, R = 16;
+  const int S = 1 << (logL - r);
+  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      v[k] = buf[pad32(j + k * S)];
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&twi[(k - 1) * S + j]));
+    }
+    dit_core<P, r>(v, wint);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {  // L >= 2M: outputs k >= R / 2 are not needed
+      const int i = j + k * S;
+      if (i < M) out[i] = red1<P>(v[k]);
+    }
+  }
+}
+
+// The last forward pass (stride 1, so its external twiddles are all 1), the product with the
+// bit-reversed stencil spectrum gh and the first inverse pass, on the same 2^r contiguous elements.
+template <uint32_t P, int r>
+__device__ __forceinline__ void mid_fused(uint32_t* buf, int logL, const uint2* __restrict__ gh,
+                                          const uint2 (&wf)[8], const uint2 (&wi)[8]) {
+  constexpr int R = 1 << r;
+  const int per = 1 << (logL - r);
+  for (int g = threadIdx.x; g < per; g += blockDim.x) {
+    const int base = g << r;
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = buf[pad32(base + k)];
+    dif_core<P, r>(v, wf);
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = mulsh<P>(v[k], __ldg(&gh[base + k]));
+    dit_core<P, r>(v, wi);
+#pragma unroll
+    for (int k = 0; k < R; ++k) buf[pad32(base + k)] = v[k];
+  }
+}
+
+// wint[e] = w^(e L / 2^r) for e < 2^r / 2 from the table's constant roots w^(e L / Rmax)
 template <int r>
 __device__ __forceinline__ void load_roots(uint2 (&wint)[8], const uint2* __restrict__ tab, int logL) {
+  const int rmax = logL < 4 ? logL : 4;
 #pragma unroll
-  for (int e = 0; e < 8; ++e) wint[e] = (e < (1 << r) / 2) ? __ldg(&tab[e << (logL - r)]) : uint2{1, 0};
+  for (int e = 0; e < 8; ++e) wint[e] = (e < (1 << r) / 2) ? __ldg(&tab[e << (rmax - r)]) : uint2{1, 0};
 }
 
-template <uint32_t P>
-__device__ void ntt_forward(uint32_t* buf, int logL, const uint2* __restrict__ tw) {
-  for (int s0 = 0; s0 < logL; s0 += 4) {
-    const int r = logL - s0 < 4 ? logL - s0 : 4;
-    uint2 wint[8];
-    __syncthreads();
-    switch (r) {
-      case 1: load_roots<1>(wint, tw, logL); dif_pass<P, 1>(buf, logL, s0, tw, wint); break;
-      case 2: load_roots<2>(wint, tw, logL); dif_pass<P, 2>(buf, logL, s0, tw, wint); break;
-      case 3: load_roots<3>(wint, tw, logL); dif_pass<P, 3>(buf, logL, s0, tw, wint); break;
-      default: load_roots<4>(wint, tw, logL); dif_pass<P, 4>(buf, logL, s0, tw, wint); break;
-    }
-  }
-  __syncthreads();
+template <uint32_t P, int r>
+__device__ __forceinline__ void mid_fused_roots(uint32_t* buf, int logL, const uint2* __restrict__ gh,
+                                                const uint2* __restrict__ twf, const uint2* __restrict__ twi) {
+  uint2 wf[8], wi[8];
+  load_roots<r>(wf, twf, logL);
+  load_roots<r>(wi, twi, logL);
+  mid_fused<P, r>(buf, logL, gh, wf, wi);
 }
-
 template <uint32_t P>
-__device__ void ntt_inverse(uint32_t* buf, int logL, const uint2* __restrict__ twi) {
-  const int last = ((logL - 1) / 4) * 4;  // start stage of the last forward pass
-  for (int s0 = last; s0 >= 0; s0 -= 4) {
-    const int r = logL - s0 < 4 ? logL - s0 : 4;
-    uint2 wint[8];
-    __syncthreads();
-    switch (r) {
-      case 1: load_roots<1>(wint, twi, logL); dit_pass<P, 1>(buf, logL, s0, twi, wint); break;
-      case 2: load_roots<2>(wint, twi, logL); dit_pass<P, 2>(buf, logL, s0, twi, wint); break;
-      case 3: load_roots<3>(wint, twi, logL); dit_pass<P, 3>(buf, logL, s0, twi, wint); break;
-      default: load_roots<4>(wint, twi, logL); dit_pass<P, 4>(buf, logL, s0, twi, wint); break;
-    }
+__device__ __forceinline__ void mid_fused_any(int r, uint32_t* buf, int logL, const uint2* __restrict__ gh,
+                                              const uint2* __restrict__ twf, const uint2* __restrict__ twi) {
+  switch (r) {
+    case 1: mid_fused_roots<P, 1>(buf, logL, gh, twf, twi); break;
+    case 2: mid_fused_roots<P, 2>(buf, logL, gh, twf, twi); break;
+    case 3: mid_fused_roots<P, 3>(buf, logL, gh, twf, twi); break;
+    default: mid_fused_roots<P, 4>(buf, logL, gh, twf, twi); break;
   }
-  __syncthreads();
 }
 
 template <typename TIn> __device__ __forceinline__ double ldd(const TIn* p) { return (double)__ldg(p); }
@@ -221,24 +295,46 @@ __device__ __forceinline__ void conv_row(const long long* __restrict__ Vk, int M
                                          uint32_t* buf, uint32_t* __restrict__ out) {
   constexpr uint32_t P = Prime<Q>::p;
   const int L = 1 << logL;
-  for (int i = threadIdx.x; i < L; i += blockDim.x) {
-    uint32_t r = 0;
-    if (i < M) {
-      long long m = __ldg(Vk + i) % (long long)P;
-      if (m < 0) m += P;
-      r = (uint32_t)m;
-    }
-    buf[pad32(i)] = r;
-  }
-  ntt_forward<P>(buf, logL, t.twf + (size_t)Q * L);
+  const size_t tsz = (size_t)ntt_tw_size(logL);
+  const uint2* twf = t.twf + Q * tsz;
+  const uint2* twi = t.twi + Q * tsz;
   const uint2* gh = t.ghat + (size_t)Q * L;
-  for (int k = threadIdx.x; k < L; k += blockDim.x) buf[pad32(k)] = mulsh<P>(buf[pad32(k)], __ldg(&gh[k]));
-  ntt_inverse<P>(buf, logL, t.twi + (size_t)Q * L);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = red1<P>(buf[pad32(i)]);
+  const int sl = ntt_last_pass(logL);
+  if (sl == 0) {  // L <= 16: one pass
+    for (int i = threadIdx.x; i < L; i += blockDim.x) buf[pad32(i)] = i < M ? residue<P>(__ldg(Vk + i)) : 0u;
+    __syncthreads();
+    mid_fused_any<P>(logL, buf, logL, gh, twf, twi);
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = red1<P>(buf[pad32(i)]);
+    return;
+  }
+  {
+    uint2 w[8];
+    load_roots<4>(w, twf, logL);
+    dif_first<P>(Vk, M, buf, logL, twf + 8, w);
+  }
+  for (int s0 = 4; s0 < sl; s0 += 4) {
+    __syncthreads();
+    uint2 w[8];
+    load_roots<4>(w, twf, logL);
+    dif_pass<P>(buf, logL, s0, twf + ntt_tw_offset(logL, s0), w);
+  }
+  __syncthreads();
+  mid_fused_any<P>(logL - sl, buf, logL, gh, twf, twi);
+  for (int s0 = sl - 4; s0 >= 4; s0 -= 4) {
+    __syncthreads();
+    uint2 w[8];
+    load_roots<4>(w, twi, logL);
+    dit_pass<P>(buf, logL, s0, twi + ntt_tw_offset(logL, s0), w);
+  }
+  __syncthreads();
+  uint2 w[8];
+  load_roots<4>(w, twi, logL);
+  dit_last<P>(buf, logL, M, twi + 8, w, out);
 }
 
 // grid (Nt, NP): blockIdx.y selects the prime.  V: the quantised rows; res: [NP][Nt][M] residues.
-__global__ void __launch_bounds__(512) ntt_conv_kernel(const long long* __restrict__ V, int M, int Nt, int logL,
+__global__ void __launch_bounds__(512, 2) ntt_conv_kernel(const long long* __restrict__ V, int M, int Nt, int logL,
                                                        NttTables t, uint32_t* __restrict__ res) {
   extern __shared__ uint32_t nbuf[];
   const int k = blockIdx.x, q = blockIdx.y;

@@ -248,21 +248,34 @@ void build_ntt_tables(HostTables& t) {
   std::vector<int64_t> G((size_t)M);
   for (int64_t j = 0; j < M; ++j) G[j] = std::llround(std::ldexp(t.g[j], QB - eg));
   t.ntt_c_gscale = t.c * std::ldexp(1.0, eg - QB);
-  t.ntt_twf.assign((size_t)NP * L * 2, 0);
-  t.ntt_twi.assign((size_t)NP * L * 2, 0);
+  const size_t tsz = (size_t)ntt_tw_size(logL);
+  t.ntt_twf.assign((size_t)NP * tsz * 2, 0);
+  t.ntt_twi.assign((size_t)NP * tsz * 2, 0);
   t.ntt_ghat.assign((size_t)NP * L * 2, 0);
   for (int q = 0; q < NP; ++q) {
     const uint64_t p = kNttPrime[q];
     const uint64_t w = powmod(kNttGen[q], (p - 1) / (uint64_t)L, p), wi = powmod(w, p - 2, p);
-    uint64_t a = 1, b = 1;
-    for (int64_t e = 0; e < L; ++e) {
-      const size_t o = ((size_t)q * L + e) * 2;
+    // entry idx of prime q: w^e and w^-e with their Shoup companions
+    auto put = [&](size_t idx, uint64_t e) {
+      const size_t o = ((size_t)q * tsz + idx) * 2;
+      const uint64_t a = powmod(w, e, p), b = powmod(wi, e, p);
       t.ntt_twf[o] = (uint32_t)a;
       t.ntt_twf[o + 1] = shoup(a, p);
       t.ntt_twi[o] = (uint32_t)b;
       t.ntt_twi[o + 1] = shoup(b, p);
-      a = mulmod(a, w, p);
-      b = mulmod(b, wi, p);
+    };
+    const int rmax = logL < 4 ? logL : 4;
+    for (int e = 0; e < 8; ++e) put((size_t)e, (uint64_t)e * (uint64_t)(L >> rmax));
+    for (int s0 = 0; s0 < ntt_last_pass(logL); s0 += 4) {
+      const int r = ntt_pass_r(logL, s0), R = 1 << r;
+      const int64_t S = L >> (s0 + r);
+      const size_t off = (size_t)ntt_tw_offset(logL, s0);
+      for (int k = 1; k < R; ++k) {
+        int bk = 0;  // bit reversal of k over r bits
+        for (int bit = 0; bit < r; ++bit)
+          if (k & (1 << bit)) bk |= 1 << (r - 1 - bit);
+        for (int64_t j = 0; j < S; ++j) put(off + (size_t)(k - 1) * S + j, ((uint64_t)j * bk) << s0);
+      }
     }
     // circulant embedding of the stencil: c_0 = G_0, c_j = c_{L-j} = G_j (1 <= j < M)
     std::vector<uint64_t> c((size_t)L, 0);

@@ -43,8 +43,8 @@ struct HostTables {
   std::vector<double> tau_eig_nat;  // c * sigma_j, j = 1..M, stored at j - 1
   bool tau_ok = false;
   // exact integer Toeplitz product (NTT matvec): per prime q, interleaved (value, Shoup companion)
-  std::vector<uint32_t> ntt_twf;    // [5][L][2]: w_q^e, w_q a primitive L-th root mod p_q
-  std::vector<uint32_t> ntt_twi;    // [5][L][2]: w_q^-e
+  std::vector<uint32_t> ntt_twf;    // [5][ntt_tw_size][2]: pass-ordered powers of w_q (kernels.h)
+  std::vector<uint32_t> ntt_twi;    // [5][ntt_tw_size][2]: the same for w_q^-1
   std::vector<uint32_t> ntt_ghat;   // [5][L][2]: NTT of the quantised stencil embedding, bit-reversed, times L^-1
   uint32_t ntt_crt[10] = {0};       // Garner constants (see ntt.cu)
   double ntt_c_gscale = 0;          // c 2^(e_g - 58): G_j = round(g_j 2^(58 - e_g))

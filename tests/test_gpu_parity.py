@@ -50,7 +50,7 @@ def rel(a, b):
 
 # ---------------------------------------------------------------- matvec
 @pytest.mark.parametrize("M,Nt,alpha", [(63, 64, 1.5), (100, 16, 1.2), (1, 4, 1.5), (2, 8, 1.9),
-                                        (1023, 32, 1.8), (4095, 8, 1.3)])
+                                        (8, 4, 1.4), (16, 8, 1.7), (1023, 32, 1.8), (4095, 8, 1.3)])
 @pytest.mark.parametrize("kind", [aao.AAO_MATVEC_NTT, aao.AAO_MATVEC_FFT64])
 def test_matvec_matches_dense_oracle(M, Nt, alpha, kind):
     v = workloads.random_vector(Nt, M, seed=M + Nt)
