@@ -22,6 +22,79 @@ template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
 constexpr int kRegMaxThreads = 512;
 constexpr int kRegElems = 16;
 
+// The embedding length L = 32 NT, for which the first and last FFT passes (2^r0 points at stride
+// S0 = L / 2^r0, a multiple of NT) only touch elements t + NT m of one thread t.
+template <int NT> __host__ __device__ constexpr int own_logL() { return NT == 64 ? 11 : NT == 128 ? 12 : NT == 256 ? 13 : 14; }
+
+// For L = 32 NT: buf[i] <- (backward(factor .* forward(x)))[i] for the thread's own elements
+// i = t + NT j (j < 16) of the register vector x (element t + NT j in x[j], zero at and beyond M,
+// so the upper half of the embedding is zero).  The first forward pass reads its groups
+// (elements t + NT (a + k A), k < 2^r0 / 2; the rest are zero) from registers and the last backward
+// pass stores only the lower half of each group, which are the thread's own elements: no staging
+// sweep, no zero fill and no trailing barrier, since each thread then reads back only its own
+// elements.  Starts synchronised.
+template <int NT, typename F>
+__device__ __forceinline__ void fft_convolve_own(float2* buf, const float2 (&x)[kRegElems], const float2* q,
+                                                 F factor, const float2* pt) {
+  constexpr int LOGL = own_logL<NT>(), L = 1 << LOGL;
+  constexpr int r0 = (LOGL & 3) ? (LOGL & 3) : 4, R0 = 1 << r0, S0 = L / R0, A = S0 / NT;
+  static_assert(S0 % NT == 0 && A * R0 / 2 == kRegElems, "first-pass groups must be thread-local");
+  const int t = threadIdx.x;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int j0 = t + NT * a;
+    float2 v[R0];
+#pragma unroll
+    for (int k = 0; k < R0; ++k) v[k] = k < R0 / 2 ? x[a + k * A] : float2{0, 0};
+    dft<-1, r0>(v);
+    if (j0 != 0) {
+#pragma unroll
+      for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], twiddle<-1>(q, j0 * m, LOGL));
+    }
+#pragma unroll
+    for (int m = 0; m < R0; ++m) buf[pad16(j0 + brev_c<r0>(m) * S0)] = v[m];
+  }
+  __syncthreads();
+  fft_convolve_inner(buf, LOGL, q, LOGL, factor, pt);
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int j0 = t + NT * a;
+    float2 v[R0];
+#pragma unroll
+    for (int m = 0; m < R0; ++m) v[m] = buf[pad16(j0 + brev_c<r0>(m) * S0)];
+    if (j0 != 0) {
+#pragma unroll
+      for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], twiddle<+1>(q, j0 * m, LOGL));
+    }
+    dft<+1, r0>(v);
+#pragma unroll
+    for (int k = 0; k < R0 / 2; ++k) buf[pad16(j0 + k * S0)] = v[k];
+  }
+}
+
+// buf[i] <- (c T x)[i] (the Toeplitz product by its circulant embedding, real spectrum Ebr) for the
+// thread's own elements i = t + NT j < M; starts synchronised.
+template <int NT>
+__device__ __forceinline__ void toeplitz_reg(float2* buf, const float2 (&x)[kRegElems], int M, int logL,
+                                             const CocgTables32& tb, const float2* q, const float2* pt) {
+  auto ef = [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; };
+  if (logL == own_logL<NT>()) {
+    fft_convolve_own<NT>(buf, x, q, ef, pt);
+    return;
+  }
+  const int L = 1 << logL;
+  const int t = threadIdx.x;
+  __syncthreads();  // earlier readers of buf are done
+#pragma unroll
+  for (int j = 0; j < kRegElems; ++j) {
+    const int i = t + NT * j;
+    if (i < L) buf[pad16(i)] = (i < M) ? x[j] : float2{0, 0};
+  }
+  for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
+  fft_convolve(buf, logL, q, logL, ef, pt);
+}
+
 // KIND 0: Strang by Bluestein (4 FFTs of L); 1: natural tau matrix by DST-I (2 FFTs); 2: Strang by
 // the precomputed per-system circulant spectrum sc (2 FFTs).  The result is read by zval().
 template <int KIND, int NT>
@@ -31,13 +104,19 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
   const int L = 1 << logL;
   const int t = threadIdx.x;
   if constexpr (KIND == 2) {
+    auto sf = [&](int p) { return __ldg(&sc[p]); };
+    if (logL == own_logL<NT>()) {
+      fft_convolve_own<NT>(buf, r, q, sf, pt);
+      return;
+    }
+    __syncthreads();  // earlier readers of buf are done
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
       if (i < L) buf[pad16(i)] = (i < M) ? r[j] : float2{0, 0};
     }
     for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
-    fft_convolve(buf, logL, q, logL, [&](int p) { return __ldg(&sc[p]); }, pt);
+    fft_convolve(buf, logL, q, logL, sf, pt);
   } else if constexpr (KIND == 0) {
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
@@ -140,10 +219,8 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       for (int j = 0; j < kRegElems; ++j) {
         const int i = t + NT * j;
         w[j] = (i < M) ? x0[i] : float2{0, 0};
-        if (i < L) buf[pad16(i)] = w[j];
       }
-      for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
-      fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
+      toeplitz_reg<NT>(buf, w, M, logL, tb, q, pt);
       float r02[1] = {0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
@@ -189,13 +266,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     int it = 0, flag = 1;
     while (it < maxit) {
       // q = (lambda I + c T) p
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        if (i < L) buf[pad16(i)] = (i < M) ? p[j] : float2{0, 0};
-      }
-      for (int i = t + NT * kRegElems; i < L; i += NT) buf[pad16(i)] = float2{0, 0};
-      fft_convolve(buf, logL, q, logL, [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; }, pt);
+      toeplitz_reg<NT>(buf, p, M, logL, tb, q, pt);
       float pq2[2] = {0, 0};
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {

@@ -449,6 +449,33 @@ __device__ void fft_convolve(T* buf, int logN, const T* q, int logNq, F factor, 
   }
 }
 
+// The passes of fft_convolve between its first forward and its last backward pass (both of
+// r0 = first_pass_stages(logN) stages at stride N >> r0), for logN > r0: the remaining forward
+// 16-point passes, the fused middle pass and the backward 16-point passes.  The caller has
+// synchronised after the first pass; ends synchronised.
+template <typename T, typename F>
+__device__ void fft_convolve_inner(T* buf, int logN, const T* q, int logNq, F factor, const T* pt) {
+  const int r0 = first_pass_stages(logN);
+  int s0 = r0, off = 0;
+  while (s0 + 4 < logN) {
+    dif_pass<T, 4>(buf, logN, s0, 1, 0, q, logNq, pt ? pt + off : nullptr);
+    off += 15 * (1 << (logN - s0 - 4));
+    __syncthreads();
+    s0 += 4;
+  }
+  switch (logN - s0) {
+    case 1: fused_mid_pass<T, 1>(buf, logN, factor); break;
+    case 2: fused_mid_pass<T, 2>(buf, logN, factor); break;
+    case 3: fused_mid_pass<T, 3>(buf, logN, factor); break;
+    default: fused_mid_pass<T, 4>(buf, logN, factor); break;
+  }
+  __syncthreads();
+  for (int t0 = s0 - 4; t0 >= r0; t0 -= 4) {
+    dit_pass<T, 4>(buf, logN, t0, 1, 0, q, logNq, pt ? pt + pass_table_offset(logN, t0) : nullptr);
+    __syncthreads();
+  }
+}
+
 // Last forward pass of fft_forward_fused: the 2^r-point DFT of each group, stored in fused order.
 template <typename T, int r>
 __device__ __forceinline__ void fused_last_pass(T* buf, int logN) {
