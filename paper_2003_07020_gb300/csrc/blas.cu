@@ -1,5 +1,6 @@
-// FP64 vector kernels for the flexible GMRES driver: classical Gram-Schmidt
-// with re-orthogonalisation (two passes) fused into three sweeps, the
+// Vector kernels for the flexible GMRES driver: classical Gram-Schmidt with
+// re-orthogonalisation (two passes) fused into three sweeps, in FP64 or on a
+// float-float basis (mixed precision), the
 // solution update U += Z y, the right-hand side of Eq. 12, and deterministic
 // two-stage reductions (per-block partial sums, then a fixed-order sum).
 #include <mutex>
@@ -121,6 +122,136 @@ __global__ void __launch_bounds__(kBlasThreads) update_norm_kernel(double* __res
   block_partials(acc, 1, partial);
 }
 
+// ---- float-float basis (mixed precision) ---------------------------------------------------
+// In the mixed path the Arnoldi basis v_0..v_m is stored as float-float pairs (hi, lo), hi + lo
+// with |lo| <= ulp(hi) / 2 (about 48 significant bits), in the same 8 bytes per element as an FP64
+// vector.  Error-free transformations (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2): two_sum and
+// quick_two_sum for sums, fma for the exact product error.  This moves CGS2 from the FP64 pipe
+// (1.6 FMA per clock per SM on this GPU) to the FP32 pipe; the basis and the Hessenberg
+// coefficients keep ~1e-14 relative accuracy, far below the 1e-10 target of FGMRES.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return float2{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ float2 ff_quick_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return float2{s, b - (s - a)};
+}
+__device__ __forceinline__ float2 ff_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return float2{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(float2 x) { return (double)x.x + (double)x.y; }
+__device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
+  const float p = x.x * y.x;
+  const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
+  return ff_quick_sum(p, e);
+}
+// x + y with error ~2^-46 (|x| + |y|)
+__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
+  float2 s = ff_two_sum(x.x, y.x);
+  s.y += x.y + y.y;
+  return ff_quick_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 ff_neg(float2 x) { return float2{-x.x, -x.y}; }
+
+// CGS2 pass 1 on the float-float basis: partial sums of hi(V_i) w in FP32.  Its error (~1e-6 of
+// sum |terms|) only leaves components along V_i that the second pass removes.
+template <int NVMAX>
+__global__ void __launch_bounds__(kBlasThreads) dots_ff_kernel(const double* __restrict__ w,
+                                                               const float2* __restrict__ V, size_t vstride, int nv,
+                                                               size_t n, double* __restrict__ partial) {
+  float acc[NVMAX];
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) acc[i] = 0.0f;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float we = __double2float_rn(w[e]);
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) acc[i] = fmaf(we, __ldg(&V[i * vstride + e]).x, acc[i]);
+  }
+  double accd[NVMAX];
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) accd[i] = (double)acc[i];
+  block_partials(accd, nv, partial);
+}
+
+// CGS2 pass 2: wout = w - sum_i h_i V_i in float-float (the FP64 w split once), then partial sums
+// of V_i . wout accumulated in float-float (the second-pass coefficients are small corrections of
+// large cancelling terms and need the extra precision).
+template <int NVMAX>
+__global__ void __launch_bounds__(kBlasThreads) update_dots_ff_kernel(const double* __restrict__ w,
+                                                                      float2* __restrict__ wout,
+                                                                      const float2* __restrict__ V, size_t vstride,
+                                                                      int nv, size_t n,
+                                                                      const double* __restrict__ h,
+                                                                      double* __restrict__ partial) {
+  __shared__ float2 hs[NVMAX];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = ff_from_double(h[i]);
+  __syncthreads();
+  float2 acc[NVMAX];
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) acc[i] = float2{0.0f, 0.0f};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float2 vv[NVMAX];
+    float2 wf = ff_from_double(w[e]);
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) {
+        vv[i] = __ldg(&V[i * vstride + e]);
+        wf = ff_add(wf, ff_neg(ff_mul(hs[i], vv[i])));
+      }
+    wout[e] = wf;
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) acc[i] = ff_add(acc[i], ff_mul(wf, vv[i]));
+  }
+  double accd[NVMAX];
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) accd[i] = ff_to_double(acc[i]);
+  __syncthreads();
+  block_partials(accd, nv, partial);
+}
+
+// CGS2 update of pass 2 in place on the float-float w, and the partial sums of ||w||^2.
+template <int NVMAX>
+__global__ void __launch_bounds__(kBlasThreads) update_norm_ff_kernel(float2* __restrict__ w,
+                                                                      const float2* __restrict__ V, size_t vstride,
+                                                                      int nv, size_t n,
+                                                                      const double* __restrict__ h,
+                                                                      double* __restrict__ partial) {
+  __shared__ float2 hs[NVMAX];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = ff_from_double(h[i]);
+  __syncthreads();
+  float2 acc{0.0f, 0.0f};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float2 wf = w[e];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) wf = ff_add(wf, ff_neg(ff_mul(hs[i], __ldg(&V[i * vstride + e]))));
+    w[e] = wf;
+    acc = ff_add(acc, ff_mul(wf, wf));
+  }
+  double accd[1] = {ff_to_double(acc)};
+  __syncthreads();
+  block_partials(accd, 1, partial);
+}
+
+// y = a x into the float-float basis from an FP64 vector; a = *a_dev if a_dev, else a.
+__global__ void scale_to_ff_kernel(float2* __restrict__ y, const double* __restrict__ x,
+                                   const double* __restrict__ a_dev, double a, size_t n) {
+  const double s = a_dev ? *a_dev : a;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = ff_from_double(s * x[e]);
+}
+
+// x *= a in place on a float-float vector; a = *a_dev if a_dev, else a.
+__global__ void scale_ff_kernel(float2* __restrict__ x, const double* __restrict__ a_dev, double a, size_t n) {
+  const float2 s = ff_from_double(a_dev ? *a_dev : a);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    x[e] = ff_mul(x[e], s);
+}
+
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int nv,
                                        double* __restrict__ out) {
   __shared__ double s[256];
@@ -205,6 +336,29 @@ cudaError_t launch_update_dots(double* w, const double* V, size_t vstride, int n
 cudaError_t launch_update_norm(double* w, const double* V, size_t vstride, int nv, size_t n, const double* h,
                                double* partial, cudaStream_t s) {
   AAO_NV_DISPATCH(update_norm_kernel, nv, w, V, vstride, nv, n, h, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_dots_ff(const double* w, const float2* V, size_t vstride, int nv, size_t n, double* partial,
+                           cudaStream_t s) {
+  AAO_NV_DISPATCH(dots_ff_kernel, nv, w, V, vstride, nv, n, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_update_dots_ff(const double* w, float2* wout, const float2* V, size_t vstride, int nv, size_t n,
+                                  const double* h, double* partial, cudaStream_t s) {
+  AAO_NV_DISPATCH(update_dots_ff_kernel, nv, w, wout, V, vstride, nv, n, h, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_update_norm_ff(float2* w, const float2* V, size_t vstride, int nv, size_t n, const double* h,
+                                  double* partial, cudaStream_t s) {
+  AAO_NV_DISPATCH(update_norm_ff_kernel, nv, w, V, vstride, nv, n, h, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_to_ff(float2* y, const double* x, const double* a_dev, double a, size_t n, cudaStream_t s) {
+  scale_to_ff_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(y, x, a_dev, a, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_ff(float2* x, const double* a_dev, double a, size_t n, cudaStream_t s) {
+  scale_ff_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(x, a_dev, a, n);
   return cudaGetLastError();
 }
 cudaError_t launch_reduce_partials(const double* partial, int nblocks, int nv, double* out, cudaStream_t s) {

@@ -23,6 +23,9 @@ size_t matvec_smem_bytes(int logL);
 
 // ---- time DFT, Steps (a) and (c), tdft.cu -------------------------------------------
 // Step (a): out[n][i] = sum_k scale[k] theta^{nk} v[k][i], n = 0..Nt/2, theta = exp(2 pi i/Nt)
+// launch_tdft_fwd_f32_ff: the same with v a float-float vector (hi, lo per element; hi is used).
+cudaError_t launch_tdft_fwd_f32_ff(const float2* v, float2* out, int M, int Nt, const float* scale,
+                                   const float2* twNt, cudaStream_t s);
 cudaError_t launch_tdft_fwd_f32(const double* v, float2* out, int M, int Nt, const float* scale,
                                 const float2* twNt, cudaStream_t s);
 cudaError_t launch_tdft_fwd_f64(const double* v, double2* out, int M, int Nt, const double* scale,
@@ -175,6 +178,18 @@ cudaError_t launch_update_norm(double* w, const double* V, size_t vstride, int n
 // out[i] = sum_b partial[b*nv + i], fixed order
 cudaError_t launch_reduce_partials(const double* partial, int nblocks, int nv, double* out,
                                    cudaStream_t s);
+// The same three CGS2 sweeps on a float-float basis V (hi, lo per element, mixed precision): pass-1
+// dots of the FP64 w in FP32; wout = w - sum h_i V_i (float-float) with the pass-2 dots; the pass-2
+// update in place with ||w||^2.  Partial sums as launch_dots.
+cudaError_t launch_dots_ff(const double* w, const float2* V, size_t vstride, int nv, size_t n, double* partial,
+                           cudaStream_t s);
+cudaError_t launch_update_dots_ff(const double* w, float2* wout, const float2* V, size_t vstride, int nv, size_t n,
+                                  const double* h, double* partial, cudaStream_t s);
+cudaError_t launch_update_norm_ff(float2* w, const float2* V, size_t vstride, int nv, size_t n, const double* h,
+                                  double* partial, cudaStream_t s);
+// y = a x (FP64 x into a float-float y) and x *= a (float-float x); a = *a_dev if a_dev != nullptr
+cudaError_t launch_scale_to_ff(float2* y, const double* x, const double* a_dev, double a, size_t n, cudaStream_t s);
+cudaError_t launch_scale_ff(float2* x, const double* a_dev, double a, size_t n, cudaStream_t s);
 cudaError_t launch_scale(double* out, const double* in, double a, size_t n, cudaStream_t s);
 // out = (*a_dev) * in, the factor read from device memory
 cudaError_t launch_scale_dev(double* out, const double* in, const double* a_dev, size_t n, cudaStream_t s);

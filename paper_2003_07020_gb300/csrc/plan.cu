@@ -220,7 +220,8 @@ struct aao_plan {
   double* tau64 = nullptr;
   float* tau32 = nullptr;
   // workspace
-  double* V = nullptr;   // (m+1) x n
+  double* V = nullptr;   // (m+1) x n; in the mixed path a float-float basis (float2 per element)
+  double* W = nullptr;   // n: the new Arnoldi vector A z_j (and r_0) in FP64 before its CGS2 (mixed path)
   void* Z = nullptr;     // m x n, float (mixed) or double
   void* spec = nullptr;  // nsys x M complex
   void* rws = nullptr;
@@ -438,12 +439,17 @@ aao_status cocg2d_any(aao_plan* p, void* spec) {
   return AAO_OK;
 }
 
-// out = P^{-1} v.  out_kind: 0 float (mixed Z basis), 1 double.
-aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind) {
+// out = P^{-1} v.  out_kind: 0 float (mixed Z basis), 1 double; v_ff: v is a float-float vector
+// (the mixed Arnoldi basis).
+aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind, bool v_ff = false) {
   const int Ms = (int)p->Msp;
   if (p->mixed) {
     float2* spec = (float2*)p->spec;
-    LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f32(v, spec, Ms, p->Nt, p->sfwd32, p->twNt32, p->stream));
+    if (v_ff)
+      LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f32_ff((const float2*)(const void*)v, spec, Ms, p->Nt, p->sfwd32,
+                                                         p->twNt32, p->stream));
+    else
+      LAUNCH(ST_TDFT_FWD, 1, aao::launch_tdft_fwd_f32(v, spec, Ms, p->Nt, p->sfwd32, p->twNt32, p->stream));
     if (p->dim == 2) {
       TRY(cocg2d_any<float>(p, spec));
     } else {
@@ -503,15 +509,27 @@ aao_status arnoldi_step(aao_plan* p, int j, GmresDevState* acc) {
   double* vj = p->V + (size_t)j * n;
   double* w = p->V + (size_t)(j + 1) * n;
   void* zj = p->mixed ? (void*)((float*)p->Z + (size_t)j * n) : (void*)((double*)p->Z + (size_t)j * n);
-  TRY(precond_any(p, vj, zj, p->mixed ? 0 : 1));
+  TRY(precond_any(p, vj, zj, p->mixed ? 0 : 1, p->mixed));
   if (acc)
     LAUNCH(ST_VEC, 1, (iter_stats_accum_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, acc),
                        cudaGetLastError()));
   else
     LAUNCH(ST_VEC, 1, (iter_stats_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->stats),
                        cudaGetLastError()));
-  TRY(matvec_any(p, zj, p->mixed, nullptr, w, nullptr));
   const int nv = j + 1;
+  if (p->mixed) {  // float-float basis: w = A z_j into W (FP64), CGS2 writes v_{j+1} as float-float
+    const float2* Vf = (const float2*)(const void*)p->V;
+    float2* wf = (float2*)(void*)w;
+    TRY(matvec_any(p, zj, true, nullptr, p->W, nullptr));
+    LAUNCH(ST_VEC, 1, aao::launch_dots_ff(p->W, Vf, n, nv, n, p->partial, p->stream));
+    LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
+    LAUNCH(ST_VEC, 1, aao::launch_update_dots_ff(p->W, wf, Vf, n, nv, n, p->hdev, p->partial, p->stream));
+    LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev + 65, p->stream));
+    LAUNCH(ST_VEC, 1, aao::launch_update_norm_ff(wf, Vf, n, nv, n, p->hdev + 65, p->partial, p->stream));
+    LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, 1, p->hdev + 130, p->stream));
+    return AAO_OK;
+  }
+  TRY(matvec_any(p, zj, p->mixed, nullptr, w, nullptr));
   LAUNCH(ST_VEC, 1, aao::launch_dots(w, p->V, n, nv, n, p->partial, p->stream));
   LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
   LAUNCH(ST_VEC, 1, aao::launch_update_dots(w, p->V, n, nv, n, p->hdev, p->partial, p->stream));
@@ -568,7 +586,9 @@ aao_status build_cycle_graph(aao_plan* p) {
     if (ok) {
       cycle_init_kernel<<<1, 1, 0, p->cap1>>>(p->gd, p->hdev, m, hs[0]);
       ok = check(cudaGetLastError(), "cycle init") &&
-           check(aao::launch_scale_dev(p->V, p->V, &p->gd->inv_beta, n, p->cap1), "scale v0");
+           check(p->mixed ? aao::launch_scale_to_ff((float2*)(void*)p->V, p->W, &p->gd->inv_beta, 0.0, n, p->cap1)
+                          : aao::launch_scale_dev(p->V, p->V, &p->gd->inv_beta, n, p->cap1),
+                 "scale v0");
     }
     for (int j = 0; ok && j < m; ++j) {
       ok = check(cudaStreamGetCaptureInfo(p->cap1, &cst, nullptr, nullptr, &deps, nullptr, &ndeps), "capture info");
@@ -596,7 +616,10 @@ aao_status build_cycle_graph(aao_plan* p) {
       if (st == AAO_OK) {
         givens_kernel<<<1, 1, 0, p->cap2>>>(p->gd, p->hdev, j, m, j + 1 < m ? hs[j + 1] : hs[j], j + 1 < m);
         double* w = p->V + (size_t)(j + 1) * n;
-        if (check(cudaGetLastError(), "givens")) check(aao::launch_scale_dev(w, w, &p->gd->inv_hn, n, p->cap2), "scale");
+        if (check(cudaGetLastError(), "givens"))
+          check(p->mixed ? aao::launch_scale_ff((float2*)(void*)w, &p->gd->inv_hn, 0.0, n, p->cap2)
+                         : aao::launch_scale_dev(w, w, &p->gd->inv_hn, n, p->cap2),
+                "scale");
         if (j == 0)
           for (int q = 0; q < AAO_NUM_STAGES; ++q) p->step_launches[q] = p->prof_launches[q] - before[q];
       } else if (err.empty()) {
@@ -737,11 +760,12 @@ aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* 
   int outer_prev = 0;
   for (int cycle = 0; cycle <= p->opts.max_cycles; ++cycle) {
     double beta2 = 0;
+    double* r0 = p->mixed ? p->W : p->V;  // the graph scales r0 into v_0
     if (cycle == 0 && zero_guess) {  // r = F; beta^2 = ||F||^2 is already in p->hdev[0]
-      CK(cudaMemcpyAsync(p->V, F, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+      CK(cudaMemcpyAsync(r0, F, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
       beta2 = nF * nF;
     } else {
-      TRY(matvec_any(p, U, false, F, p->V, p->sq));  // r = F - calA U into v_0, row sums of squares
+      TRY(matvec_any(p, U, false, F, r0, p->sq));  // r = F - calA U, row sums of squares
       inf.matvecs++;
       TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));  // leaves beta^2 in p->hdev[0]
     }
@@ -912,6 +936,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->ntt = true;
   }
   TRYP(dalloc(p, &p->V, (size_t)(p->m + 1) * n));
+  if (p->mixed) TRYP(dalloc(p, &p->W, n));
   {
     void* z = nullptr;
     TRYP(dalloc(p, reinterpret_cast<unsigned char**>(&z), (size_t)p->m * n * (p->mixed ? 4 : 8)));
@@ -1129,11 +1154,14 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
   for (int cycle = 0; cycle <= p->opts.max_cycles; ++cycle) {
     // r = F - calA U  (into V_0) with row partial sums of squares
     double beta2 = 0;
+    const double* r0 = p->V;
     if (cycle == 0 && zero_guess) {  // r = F
-      CK(cudaMemcpyAsync(p->V, F, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+      if (p->mixed) r0 = F;
+      else CK(cudaMemcpyAsync(p->V, F, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
       beta2 = nF2;
     } else {
-      TRY(matvec_any(p, U, false, F, p->V, p->sq));
+      r0 = p->mixed ? p->W : p->V;
+      TRY(matvec_any(p, U, false, F, const_cast<double*>(r0), p->sq));
       inf.matvecs++;
       TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &beta2));
     }
@@ -1143,7 +1171,10 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     inf.cycles = cycle;
     if (inf.true_rel_res <= tol) { result = AAO_OK; break; }
     if (cycle == p->opts.max_cycles) break;
-    LAUNCH(ST_VEC, 1, aao::launch_scale(p->V, p->V, 1.0 / beta, n, p->stream));
+    if (p->mixed)
+      LAUNCH(ST_VEC, 1, aao::launch_scale_to_ff((float2*)(void*)p->V, r0, nullptr, 1.0 / beta, n, p->stream));
+    else
+      LAUNCH(ST_VEC, 1, aao::launch_scale(p->V, p->V, 1.0 / beta, n, p->stream));
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -1167,7 +1198,10 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
       const double hn = std::sqrt(p->pinned[130]);
       Hij(j + 1, j) = hn;
       if (!std::isfinite(hn)) { result = AAO_ENONFINITE; p->err = "non-finite Arnoldi vector"; stop = true; break; }
-      if (hn > 0) LAUNCH(ST_VEC, 1, aao::launch_scale(w, w, 1.0 / hn, n, p->stream));
+      if (hn > 0) {
+        if (p->mixed) LAUNCH(ST_VEC, 1, aao::launch_scale_ff((float2*)(void*)w, nullptr, 1.0 / hn, n, p->stream));
+        else LAUNCH(ST_VEC, 1, aao::launch_scale(w, w, 1.0 / hn, n, p->stream));
+      }
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
         Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);

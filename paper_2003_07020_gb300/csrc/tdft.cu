@@ -17,10 +17,12 @@ constexpr int TWH = TW / 2;
 constexpr int LU = 8;    // independent global loads in flight per thread (the loads are latency-bound)
 
 template <typename R> __device__ __forceinline__ R ldv(const double* p) { return (R)__ldg(p); }
+// a float-float element hi + lo read in FP32: hi (|lo| is below half an FP32 ulp of hi)
+template <typename R> __device__ __forceinline__ R ldv(const float2* p) { return (R)__ldg(p).x; }
 
 // ---- Step (a) ----
-template <typename R>
-__global__ void __launch_bounds__(256) tdft_fwd_kernel(const double* __restrict__ v,
+template <typename R, typename TV>
+__global__ void __launch_bounds__(256) tdft_fwd_kernel(const TV* __restrict__ v,
                                                        typename cplx_t<R>::type* __restrict__ out, int M,
                                                        int logNt, const R* __restrict__ scale,
                                                        const typename cplx_t<R>::type* __restrict__ tw) {
@@ -123,13 +125,13 @@ static size_t tdft_smem(int Nt) {
 
 static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
-template <typename R>
-static cudaError_t fwd(const double* v, typename cplx_t<R>::type* out, int M, int Nt, const R* scale,
+template <typename R, typename TV>
+static cudaError_t fwd(const TV* v, typename cplx_t<R>::type* out, int M, int Nt, const R* scale,
                        const typename cplx_t<R>::type* tw, cudaStream_t s) {
   const size_t smem = tdft_smem<R>(Nt);
-  cudaError_t e = allow_max_dynamic_smem(tdft_fwd_kernel<R>);
+  cudaError_t e = allow_max_dynamic_smem(tdft_fwd_kernel<R, TV>);
   if (e != cudaSuccess) return e;
-  tdft_fwd_kernel<R><<<(M + TW - 1) / TW, 256, smem, s>>>(v, out, M, ilog2i(Nt), scale, tw);
+  tdft_fwd_kernel<R, TV><<<(M + TW - 1) / TW, 256, smem, s>>>(v, out, M, ilog2i(Nt), scale, tw);
   return cudaGetLastError();
 }
 
@@ -145,11 +147,15 @@ static cudaError_t inv(const typename cplx_t<R>::type* in, TOut* z, int M, int N
 
 cudaError_t launch_tdft_fwd_f32(const double* v, float2* out, int M, int Nt, const float* scale,
                                 const float2* twNt, cudaStream_t s) {
-  return fwd<float>(v, out, M, Nt, scale, twNt, s);
+  return fwd<float, double>(v, out, M, Nt, scale, twNt, s);
+}
+cudaError_t launch_tdft_fwd_f32_ff(const float2* v, float2* out, int M, int Nt, const float* scale,
+                                   const float2* twNt, cudaStream_t s) {
+  return fwd<float, float2>(v, out, M, Nt, scale, twNt, s);
 }
 cudaError_t launch_tdft_fwd_f64(const double* v, double2* out, int M, int Nt, const double* scale,
                                 const double2* twNt, cudaStream_t s) {
-  return fwd<double>(v, out, M, Nt, scale, twNt, s);
+  return fwd<double, double>(v, out, M, Nt, scale, twNt, s);
 }
 cudaError_t launch_tdft_inv_f32(const float2* in, float* z, int M, int Nt, const float* scale_inv,
                                 const float2* twNt, cudaStream_t s) {
