@@ -142,6 +142,33 @@ __device__ __forceinline__ float2 ff_from_double(double x) {
   return float2{h, __double2float_rn(x - (double)h)};
 }
 __device__ __forceinline__ double ff_to_double(float2 x) { return (double)x.x + (double)x.y; }
+
+// The same split with integer operations only (FP64<->FP32 conversions issue on the FP64 pipe, under 1 per
+// clock per SM on this GPU): for 2^-74 <= |x| < 2^127, hi = x truncated to its 24 leading significant bits
+// (exact in FP32) and lo = the remaining 29 bits correctly rounded to FP32 (|lo| < ulp(hi)), so
+// |hi + lo - x| <= 2^-48 |x|.  Other x (zero, tiny, huge, non-finite) take the conversions.
+__device__ __forceinline__ float2 ff_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const int e = (int)((hw >> 20) & 0x7ffu);  // biased exponent of x
+  if (e < 949 || e > 1150) return ff_from_double(x);
+  const unsigned int sign = hw & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned int)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  const unsigned int r = lw & 0x1fffffffu;  // lo = r 2^(e - 1075), r < 2^29
+  // (float) r correctly rounded: r = a 2^15 + c with a, c < 2^15 converted exactly through the 2^23 bias
+  const float fa = __uint_as_float(0x4b000000u | (r >> 15)) - 8388608.0f;
+  const float fc = __uint_as_float(0x4b000000u | (r & 0x7fffu)) - 8388608.0f;
+  const float lo = fmaf(fa, 32768.0f, fc) * __uint_as_float((unsigned int)(e - 948) << 23);
+  return float2{hi, __uint_as_float(__float_as_uint(lo) ^ sign)};
+}
+// (double) f from the bits for zero and normal f; denormal and non-finite f take the conversion.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ex == 0 || ex == 255) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3)),
+                          (int)((u & 0x7u) << 29));
+}
 __device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
   const float p = x.x * y.x;
   const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
@@ -165,7 +192,7 @@ __global__ void __launch_bounds__(kBlasThreads) dots_ff_kernel(const double* __r
 #pragma unroll
   for (int i = 0; i < NVMAX; ++i) acc[i] = 0.0f;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const float we = __double2float_rn(w[e]);
+    const float we = ff_split(w[e]).x;
 #pragma unroll
     for (int i = 0; i < NVMAX; ++i)
       if (i < nv) acc[i] = fmaf(we, __ldg(&V[i * vstride + e]).x, acc[i]);
@@ -194,7 +221,7 @@ __global__ void __launch_bounds__(kBlasThreads) update_dots_ff_kernel(const doub
   for (int i = 0; i < NVMAX; ++i) acc[i] = float2{0.0f, 0.0f};
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     float2 vv[NVMAX];
-    float2 wf = ff_from_double(w[e]);
+    float2 wf = ff_split(w[e]);
 #pragma unroll
     for (int i = 0; i < NVMAX; ++i)
       if (i < nv) {
@@ -225,16 +252,42 @@ __global__ void __launch_bounds__(kBlasThreads) update_norm_ff_kernel(float2* __
   __syncthreads();
   float2 acc{0.0f, 0.0f};
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float2 vv[NVMAX];  // all loads of the element issued before the dependent update chain
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) vv[i] = __ldg(&V[i * vstride + e]);
     float2 wf = w[e];
 #pragma unroll
     for (int i = 0; i < NVMAX; ++i)
-      if (i < nv) wf = ff_add(wf, ff_neg(ff_mul(hs[i], __ldg(&V[i * vstride + e]))));
+      if (i < nv) wf = ff_add(wf, ff_neg(ff_mul(hs[i], vv[i])));
     w[e] = wf;
     acc = ff_add(acc, ff_mul(wf, wf));
   }
   double accd[1] = {ff_to_double(acc)};
   __syncthreads();
   block_partials(accd, 1, partial);
+}
+
+// U += sum_j y_j Z_j for the FP32 Z of the mixed path: the sum in float-float on the FP32 pipe, then two
+// FP64 adds per element (instead of a conversion and an FMA per element and vector).
+template <int NZMAX>
+__global__ void __launch_bounds__(kBlasThreads) zy_ff_kernel(double* __restrict__ U, const float* __restrict__ Z,
+                                                             size_t zstride, int nz, size_t n,
+                                                             const double* __restrict__ y) {
+  __shared__ float2 ys[NZMAX];
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) ys[i] = ff_from_double(y[i]);
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float zz[NZMAX];
+#pragma unroll
+    for (int j = 0; j < NZMAX; ++j)
+      if (j < nz) zz[j] = __ldg(&Z[j * zstride + e]);
+    float2 acc{0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < NZMAX; ++j)
+      if (j < nz) acc = ff_add(acc, ff_mul(ys[j], float2{zz[j], 0.0f}));
+    U[e] += f2d_bits(acc.x) + f2d_bits(acc.y);
+  }
 }
 
 // y = a x into the float-float basis from an FP64 vector; a = *a_dev if a_dev, else a.
@@ -373,10 +426,9 @@ cudaError_t launch_scale_dev(double* out, const double* in, const double* a_dev,
   scale_dev_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(out, in, a_dev, n);
   return cudaGetLastError();
 }
-cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
-                                 cudaStream_t s) {
-  if (nz > kMaxVec) return cudaErrorInvalidValue;
-  zy_kernel<float, kMaxVec><<<kBlasBlocks, kBlasThreads, 0, s>>>(U, Z, zstride, nz, n, y);
+cudaError_t launch_zy_update_ff(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
+                                cudaStream_t s) {
+  AAO_NV_DISPATCH(zy_ff_kernel, nz, U, Z, zstride, nz, n, y);
   return cudaGetLastError();
 }
 cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int nz, size_t n, const double* y,

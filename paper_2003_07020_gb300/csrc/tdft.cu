@@ -12,7 +12,7 @@
 
 namespace aao {
 
-constexpr int TW = 16;   // columns per CTA
+constexpr int TW = 8;    // columns per CTA (8, 16 and 32 measured at M = 8191, Nt = 1024: 8 is fastest)
 constexpr int TWH = TW / 2;
 constexpr int LU = 8;    // independent global loads in flight per thread (the loads are latency-bound)
 
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const TV* __restrict__ v,
   C* sm = reinterpret_cast<C*>(smraw);
   R* smr = reinterpret_cast<R*>(smraw);
   const int Nt = 1 << logNt;
-  const int bstride = padded_size(Nt);
+  const int bstride = padded_size(Nt) + 1;  // odd stride: the TW/2 transforms start in different banks
   const int c0 = blockIdx.x * TW;
   C* tq = sm + TWH * bstride;
   load_quarter(tq, tw, Nt / 4);
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
   extern __shared__ unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int Nt = 1 << logNt;
-  const int bstride = padded_size(Nt);
+  const int bstride = padded_size(Nt) + 1;  // odd stride: the TW/2 transforms start in different banks
   const int c0 = blockIdx.x * TW;
   const int half = Nt / 2;
   C* tq = sm + TWH * bstride;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
 
 template <typename R>
 static size_t tdft_smem(int Nt) {
-  return ((size_t)TWH * padded_size(Nt) + (size_t)(Nt / 4)) * sizeof(typename cplx_t<R>::type);
+  return ((size_t)TWH * (padded_size(Nt) + 1) + (size_t)(Nt / 4)) * sizeof(typename cplx_t<R>::type);
 }
 
 static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
