@@ -192,10 +192,14 @@ __global__ void __launch_bounds__(kBlasThreads) dots_ff_kernel(const double* __r
 #pragma unroll
   for (int i = 0; i < NVMAX; ++i) acc[i] = 0.0f;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float vh[NVMAX];  // loads issued before the split's branch
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) vh[i] = __ldg(&V[i * vstride + e]).x;
     const float we = ff_split(w[e]).x;
 #pragma unroll
     for (int i = 0; i < NVMAX; ++i)
-      if (i < nv) acc[i] = fmaf(we, __ldg(&V[i * vstride + e]).x, acc[i]);
+      if (i < nv) acc[i] = fmaf(we, vh[i], acc[i]);
   }
   double accd[NVMAX];
 #pragma unroll
@@ -220,14 +224,14 @@ __global__ void __launch_bounds__(kBlasThreads) update_dots_ff_kernel(const doub
 #pragma unroll
   for (int i = 0; i < NVMAX; ++i) acc[i] = float2{0.0f, 0.0f};
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    float2 vv[NVMAX];
+    float2 vv[NVMAX];  // all loads of the element issued before the split and the dependent update chain
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) vv[i] = __ldg(&V[i * vstride + e]);
     float2 wf = ff_split(w[e]);
 #pragma unroll
     for (int i = 0; i < NVMAX; ++i)
-      if (i < nv) {
-        vv[i] = __ldg(&V[i * vstride + e]);
-        wf = ff_add(wf, ff_neg(ff_mul(hs[i], vv[i])));
-      }
+      if (i < nv) wf = ff_add(wf, ff_neg(ff_mul(hs[i], vv[i])));
     wout[e] = wf;
 #pragma unroll
     for (int i = 0; i < NVMAX; ++i)
@@ -268,25 +272,27 @@ __global__ void __launch_bounds__(kBlasThreads) update_norm_ff_kernel(float2* __
   block_partials(accd, 1, partial);
 }
 
-// U += sum_j y_j Z_j for the FP32 Z of the mixed path: the sum in float-float on the FP32 pipe, then two
-// FP64 adds per element (instead of a conversion and an FMA per element and vector).
+// U += sum_j y_j Z_j for the FP32 Z of the mixed path, in FP64 (the update must keep FP64 accuracy: an error
+// d in U shows in the residual as calA d, and ||c T|| is ~4e4 at M = 8191, so a float-float sum would put
+// ~1e-10 into the true residual); Z_j is widened exactly from its bits (f2d_bits), not by the FP64-pipe
+// conversion, so the FP64 pipe does one FMA per element and vector.
 template <int NZMAX>
-__global__ void __launch_bounds__(kBlasThreads) zy_ff_kernel(double* __restrict__ U, const float* __restrict__ Z,
-                                                             size_t zstride, int nz, size_t n,
-                                                             const double* __restrict__ y) {
-  __shared__ float2 ys[NZMAX];
-  for (int i = threadIdx.x; i < nz; i += blockDim.x) ys[i] = ff_from_double(y[i]);
+__global__ void __launch_bounds__(kBlasThreads) zy_f32_kernel(double* __restrict__ U, const float* __restrict__ Z,
+                                                              size_t zstride, int nz, size_t n,
+                                                              const double* __restrict__ y) {
+  __shared__ double ys[NZMAX];
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) ys[i] = y[i];
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     float zz[NZMAX];
 #pragma unroll
     for (int j = 0; j < NZMAX; ++j)
       if (j < nz) zz[j] = __ldg(&Z[j * zstride + e]);
-    float2 acc{0.0f, 0.0f};
+    double u = U[e];
 #pragma unroll
     for (int j = 0; j < NZMAX; ++j)
-      if (j < nz) acc = ff_add(acc, ff_mul(ys[j], float2{zz[j], 0.0f}));
-    U[e] += f2d_bits(acc.x) + f2d_bits(acc.y);
+      if (j < nz) u = fma(ys[j], f2d_bits(zz[j]), u);
+    U[e] = u;
   }
 }
 
@@ -426,9 +432,9 @@ cudaError_t launch_scale_dev(double* out, const double* in, const double* a_dev,
   scale_dev_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(out, in, a_dev, n);
   return cudaGetLastError();
 }
-cudaError_t launch_zy_update_ff(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
-                                cudaStream_t s) {
-  AAO_NV_DISPATCH(zy_ff_kernel, nz, U, Z, zstride, nz, n, y);
+cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
+                                 cudaStream_t s) {
+  AAO_NV_DISPATCH(zy_f32_kernel, nz, U, Z, zstride, nz, n, y);
   return cudaGetLastError();
 }
 cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int nz, size_t n, const double* y,

@@ -193,9 +193,9 @@ cudaError_t launch_scale_ff(float2* x, const double* a_dev, double a, size_t n, 
 cudaError_t launch_scale(double* out, const double* in, double a, size_t n, cudaStream_t s);
 // out = (*a_dev) * in, the factor read from device memory
 cudaError_t launch_scale_dev(double* out, const double* in, const double* a_dev, size_t n, cudaStream_t s);
-// U += sum_j y[j] Z_j: FP32 Z with the sum in float-float (mixed path), FP64 Z
-cudaError_t launch_zy_update_ff(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
-                                cudaStream_t s);
+// U += sum_j y[j] Z_j in FP64 for FP32 Z (mixed path) or FP64 Z
+cudaError_t launch_zy_update_f32(double* U, const float* Z, size_t zstride, int nz, size_t n, const double* y,
+                                 cudaStream_t s);
 cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int nz, size_t n,
                                  const double* y, cudaStream_t s);
 cudaError_t launch_build_rhs(const double* u0, const double* f, double* F, double tau, int M, int Nt,

@@ -790,7 +790,7 @@ aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* 
     }
     if (hs.jdone > 0) {
       if (p->mixed)
-        LAUNCH(ST_VEC, 1, aao::launch_zy_update_ff(U, (const float*)p->Z, n, hs.jdone, n, p->gd->y, p->stream));
+        LAUNCH(ST_VEC, 1, aao::launch_zy_update_f32(U, (const float*)p->Z, n, hs.jdone, n, p->gd->y, p->stream));
       else
         LAUNCH(ST_VEC, 1, aao::launch_zy_update_f64(U, (const double*)p->Z, n, hs.jdone, n, p->gd->y, p->stream));
     }
@@ -1228,7 +1228,7 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     std::memcpy(p->pinned, y.data(), jdone * sizeof(double));
     CK(cudaMemcpyAsync(p->hdev + 195, p->pinned, jdone * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     if (p->mixed)
-      LAUNCH(ST_VEC, 1, aao::launch_zy_update_ff(U, (const float*)p->Z, n, jdone, n, p->hdev + 195, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_zy_update_f32(U, (const float*)p->Z, n, jdone, n, p->hdev + 195, p->stream));
     else
       LAUNCH(ST_VEC, 1, aao::launch_zy_update_f64(U, (const double*)p->Z, n, jdone, n, p->hdev + 195, p->stream));
   }
