@@ -161,14 +161,6 @@ __device__ __forceinline__ float2 ff_split(double x) {
   const float lo = fmaf(fa, 32768.0f, fc) * __uint_as_float((unsigned int)(e - 948) << 23);
   return float2{hi, __uint_as_float(__float_as_uint(lo) ^ sign)};
 }
-// (double) f from the bits for zero and normal f; denormal and non-finite f take the conversion.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0 || ex == 255) return (double)f;
-  return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3)),
-                          (int)((u & 0x7u) << 29));
-}
 __device__ __forceinline__ float2 ff_mul(float2 x, float2 y) {
   const float p = x.x * y.x;
   const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));

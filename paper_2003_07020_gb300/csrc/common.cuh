@@ -520,6 +520,17 @@ __device__ void fft_forward_fused(T* buf, int logN, const T* q, int logNq, const
   __syncthreads();
 }
 
+// (double) f from the bits for zero and normal f (exact, like the conversion, but with integer operations: the
+// FP64<->FP32 conversions issue on the FP64 pipe of this GPU, under 1 per clock per SM); denormal and
+// non-finite f take the conversion.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ex == 0 || ex == 255) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3)),
+                          (int)((u & 0x7u) << 29));
+}
+
 // Copies the quarter twiddle table (n4 entries) from global to shared memory.
 template <typename T>
 __device__ __forceinline__ void load_quarter(T* dst, const T* __restrict__ src, int n4) {

@@ -253,7 +253,8 @@ __device__ __forceinline__ void mid_fused_any(int r, uint32_t* buf, int logL, co
   }
 }
 
-template <typename TIn> __device__ __forceinline__ double ldd(const TIn* p) { return (double)__ldg(p); }
+__device__ __forceinline__ double ldd(const double* p) { return __ldg(p); }
+__device__ __forceinline__ double ldd(const float* p) { return f2d_bits(__ldg(p)); }
 
 // Quantisation pre-pass, one CTA per row: V[k][i] = round(v[k][i] 2^(58 - e_v)) with the row's
 // largest magnitude below 2^e_v (int64, |V| < 2^58); rowscale[k] = 2^(e_v - 58) (0 for a zero row,
@@ -288,6 +289,49 @@ __global__ void __launch_bounds__(512) ntt_quant_kernel(const TIn* __restrict__ 
                                               : (mx > 0 ? ldexp(1.0, ev - QBITS) : 0.0);
   long long* Vk = V + (size_t)k * M;
   for (int i = threadIdx.x; i < M; i += blockDim.x) Vk[i] = __double2ll_rn(ldd(vk + i) * qs);  // exact scaling
+}
+
+// The quantisation pre-pass for FP32 rows, in integer arithmetic on the bit patterns: the row's largest
+// magnitude as bits (monotone for finite values) gives e_v, and each entry m 2^E (24-bit significand m) becomes
+// m 2^(E + 58 - e_v), shifted left exactly or right with rounding half to even -- the same integers as the FP64
+// form round(v 2^(58 - e_v)), without FP64<->FP32 conversions.
+__global__ void __launch_bounds__(512) ntt_quant_f32_kernel(const float* __restrict__ v, int M,
+                                                            long long* __restrict__ V, double* __restrict__ rowscale) {
+  __shared__ unsigned int redu[32];
+  const int k = blockIdx.x;
+  const unsigned int* vk = reinterpret_cast<const unsigned int*>(v + (size_t)k * M);
+  unsigned int amax = 0;  // >= 0x7f800000: a non-finite entry
+  for (int i = threadIdx.x; i < M; i += blockDim.x) amax = max(amax, __ldg(vk + i) & 0x7fffffffu);
+  amax = __reduce_max_sync(0xffffffffu, amax);
+  if ((threadIdx.x & 31) == 0) redu[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  amax = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = max(amax, redu[w]);
+  const bool bad = amax >= 0x7f800000u;
+  int ev = 0;  // largest magnitude < 2^ev
+  if (amax) ev = (amax >> 23) ? (int)(amax >> 23) - 126 : (32 - __clz((int)amax)) - 149;
+  if (threadIdx.x == 0) rowscale[k] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (amax ? ldexp(1.0, ev - QBITS) : 0.0);
+  long long* Vk = V + (size_t)k * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const unsigned int u = __ldg(vk + i), a = u & 0x7fffffffu;
+    long long q = 0;
+    if (!bad && a) {
+      const unsigned int ex = a >> 23;
+      const unsigned int m = ex ? ((a & 0x7fffffu) | 0x800000u) : a;
+      const int sh = (ex ? (int)ex - 150 : -149) + QBITS - ev;  // <= 34
+      if (sh >= 0) {
+        q = (long long)m << sh;
+      } else if (sh > -26) {  // m < 2^24: a shift by 26 or more rounds to 0
+        const int r = -sh;
+        unsigned int qq = m >> r;
+        const unsigned int rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+        if (rem > half || (rem == half && (qq & 1u))) ++qq;
+        q = qq;
+      }
+      if (u >> 31) q = -q;
+    }
+    Vk[i] = q;
+  }
 }
 
 template <int Q>
@@ -463,7 +507,8 @@ cudaError_t launch_ntt(const TIn* v, const double* rhs, double* w, double* sq_pa
   cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel);
   if (e != cudaSuccess) return e;
   long long* V = reinterpret_cast<long long*>(res + (size_t)NP * Nt * M);  // after the residues
-  ntt_quant_kernel<TIn><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
+  if constexpr (sizeof(TIn) == 4) ntt_quant_f32_kernel<<<Nt, 512, 0, s>>>(v, M, V, rowscale);
+  else ntt_quant_kernel<TIn><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ntt_conv_kernel<<<dim3(Nt, NP), 512, smem, s>>>(V, M, Nt, logL, t, res);
