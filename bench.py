@@ -103,7 +103,12 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-            time.sleep(0.3)
+            # let nvidia-smi finish its NVML start-up (which can briefly stall this process's CUDA
+            # calls) before the timed region: wait for its first sample, up to 5 s
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
+            time.sleep(0.2)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
