@@ -117,7 +117,8 @@ struct NttTables {
   const uint2* twf;     // [5][ntt_tw_size(logL)] forward roots w (a primitive L-th root mod p), layout above
   const uint2* twi;     // [5][ntt_tw_size(logL)] the same for w^-1
   const uint2* ghat;    // [5][L] stencil spectrum, bit-reversed, times L^-1
-  uint32_t crt[10];     // Garner constants: p0^-1 mod p1..p4, p1^-1 mod p2..p4, p2^-1 mod p3, p4, p3^-1 mod p4
+  uint2 crt[10];        // Garner constants (c, floor(c 2^32 / p_b)): p0^-1 mod p1..p4, p1^-1 mod p2..p4,
+                        // p2^-1 mod p3, p4, p3^-1 mod p4
   double c_gscale;      // c 2^(e_g - 58)
 };
 // w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the quantised row

@@ -393,26 +393,27 @@ __global__ void __launch_bounds__(512, 2) ntt_conv_kernel(const long long* __res
   }
 }
 
-// x mod p for x < 2p^2 (64-bit), p < 2^30
-template <int Q> __device__ __forceinline__ uint64_t md(uint64_t x) { return x % (uint64_t)Prime<Q>::p; }
+// One Garner step in 32-bit arithmetic: (r - x) c mod p_B for a residue r < p_B, a digit x < p_A (one
+// subtraction brings it below p_B: the five primes lie within a factor 1.15 of each other) and the constant
+// c = (c, floor(c 2^32 / p_B)) by Shoup multiplication.
+template <int B> __device__ __forceinline__ uint32_t gstep(uint32_t r, uint32_t x, uint2 c) {
+  constexpr uint32_t P = Prime<B>::p;
+  const uint32_t xr = x >= P ? x - P : x;
+  const uint32_t a = r >= xr ? r - xr : r + P - xr;
+  return red1<P>(mulsh<P>(a, c));
+}
 
 // Garner's mixed-radix digits d_q of the residues r_q, then
 // Y = d0 + p0 (d1 + p1 (d2 + p2 (d3 + p3 d4))) in integer arithmetic, converted to FP64 once
 // (correctly rounded); negative when d4 > p4 / 2 (|Y| < 2^129, far below half the product).
-__device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint32_t* c) {
+__device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint2* c) {
   constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p, p4 = Prime<4>::p;
   // c: p0^-1 mod p1..p4 (c[0..3]), p1^-1 mod p2..p4 (c[4..6]), p2^-1 mod p3, p4 (c[7..8]), p3^-1 mod p4 (c[9])
-  const uint64_t d0 = rq[0];
-  const uint64_t d1 = md<1>((rq[1] + p1 - md<1>(d0)) * c[0]);
-  uint64_t t = md<2>((rq[2] + p2 - md<2>(d0)) * c[1]);
-  const uint64_t d2 = md<2>((t + p2 - md<2>(d1)) * c[4]);
-  t = md<3>((rq[3] + p3 - md<3>(d0)) * c[2]);
-  t = md<3>((t + p3 - md<3>(d1)) * c[5]);
-  const uint64_t d3 = md<3>((t + p3 - d2 % p3) * c[7]);
-  t = md<4>((rq[4] + p4 - md<4>(d0)) * c[3]);
-  t = md<4>((t + p4 - md<4>(d1)) * c[6]);
-  t = md<4>((t + p4 - md<4>(d2)) * c[8]);
-  const uint64_t d4 = md<4>((t + p4 - md<4>(d3)) * c[9]);
+  const uint32_t d0 = rq[0];
+  const uint32_t d1 = gstep<1>(rq[1], d0, c[0]);
+  const uint32_t d2 = gstep<2>(gstep<2>(rq[2], d0, c[1]), d1, c[4]);
+  const uint32_t d3 = gstep<3>(gstep<3>(gstep<3>(rq[3], d0, c[2]), d1, c[5]), d2, c[7]);
+  const uint32_t d4 = gstep<4>(gstep<4>(gstep<4>(gstep<4>(rq[4], d0, c[3]), d1, c[6]), d2, c[8]), d3, c[9]);
   // Y (|Y| < 2^129) as a 3-limb integer from the mixed-radix digits, negative when d4 > p4 / 2
   // (then |Y| = (P - 1 - Y) + 1 with the complemented digits p_q - 1 - d_q), converted once.
   const bool neg = d4 > p4 / 2;

@@ -929,7 +929,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->ntt_tab.twi = (const uint2*)q32;
     TRYP(upload(p, &q32, p->ht.ntt_ghat));
     p->ntt_tab.ghat = (const uint2*)q32;
-    for (int i = 0; i < 10; ++i) p->ntt_tab.crt[i] = p->ht.ntt_crt[i];
+    for (int i = 0; i < 10; ++i) p->ntt_tab.crt[i] = make_uint2(p->ht.ntt_crt[2 * i], p->ht.ntt_crt[2 * i + 1]);
     p->ntt_tab.c_gscale = p->ht.ntt_c_gscale;
     TRYP(dalloc(p, &p->ntt_res, (size_t)(aao::kNttPrimes + 2) * n));  // residues + int64 quantised rows
     TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));

@@ -293,12 +293,16 @@ void build_ntt_tables(HostTables& t) {
       t.ntt_ghat[((size_t)q * L + k) * 2 + 1] = shoup(v, p);
     }
   }
-  // Garner constants p_a^-1 mod p_b (a < b) in the order (0,1) (0,2) (0,3) (0,4) (1,2) (1,3) (1,4) (2,3) (2,4) (3,4)
+  // Garner constants p_a^-1 mod p_b (a < b) in the order (0,1) (0,2) (0,3) (0,4) (1,2) (1,3) (1,4) (2,3) (2,4) (3,4),
+  // each with its Shoup companion floor(c 2^32 / p_b)
   int o = 0;
   for (int a = 0; a < NP - 1; ++a)
     for (int bq = a + 1; bq < NP; ++bq) {
       const uint64_t pb = kNttPrime[bq];
-      t.ntt_crt[o++] = (uint32_t)powmod(kNttPrime[a] % pb, pb - 2, pb);
+      const uint64_t c = powmod(kNttPrime[a] % pb, pb - 2, pb);
+      t.ntt_crt[2 * o] = (uint32_t)c;
+      t.ntt_crt[2 * o + 1] = shoup(c, pb);
+      ++o;
     }
 }
 

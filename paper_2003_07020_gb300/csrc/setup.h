@@ -46,7 +46,7 @@ struct HostTables {
   std::vector<uint32_t> ntt_twf;    // [5][ntt_tw_size][2]: pass-ordered powers of w_q (kernels.h)
   std::vector<uint32_t> ntt_twi;    // [5][ntt_tw_size][2]: the same for w_q^-1
   std::vector<uint32_t> ntt_ghat;   // [5][L][2]: NTT of the quantised stencil embedding, bit-reversed, times L^-1
-  uint32_t ntt_crt[10] = {0};       // Garner constants (see ntt.cu)
+  uint32_t ntt_crt[20] = {0};       // Garner constants and their Shoup companions (see ntt.cu)
   double ntt_c_gscale = 0;          // c 2^(e_g - 58): G_j = round(g_j 2^(58 - e_g))
 };
 
