@@ -243,10 +243,11 @@ FP64_PEAK_TFLOPS = 2 * 1.60 * 152 * 2.07e9 / 1e12
 # launch, M = 8191, Nt = 128); traffic grows with the rows, so a full launch of
 # Nt rows moves Nt times this.
 MATVEC_DRAM_BYTES_PER_ROW_M8191 = 17.018e6 / 128
-# The same for the exact-integer (NTT) matvec: ntt_quant_kernel + ntt_conv_kernel (5 primes) +
-# ntt_epilogue_kernel read 8.40 + 10.61 + 37.76 MB and write 0 per 128-row launch triple
-# (one ncu capture at M = 8191, Nt = 128).
-NTT_DRAM_BYTES_PER_ROW_M8191 = (8.396e6 + 10.613e6 + 37.764e6) / 128
+# The same for the exact-integer (NTT) matvec of the Arnoldi steps (FP32 input, 10 of the 11 matvecs of a
+# solve): ntt_quant_f32_kernel + ntt_conv_kernel (5 primes) + ntt_epilogue_kernel<float> read
+# 4.20 + 10.61 + 25.18 MB and write 0 per 128-row launch triple (one ncu capture at M = 8191, Nt = 128; the
+# FP64-input residual matvec reads 8.40 + 10.61 + 37.76 MB).
+NTT_DRAM_BYTES_PER_ROW_M8191 = (4.200e6 + 10.613e6 + 25.181e6) / 128
 # DRAM bytes of cocg_reg_kernel<Strang spectra> per shifted system at M = 8191 (13.21 MB read + 5 KB
 # written for 65 systems, one ncu capture at M = 8191, Nt = 128): the per-system spectrum and tables.
 COCG_DRAM_BYTES_PER_SYSTEM_M8191 = (13.215e6 + 0.005e6) / 65
