@@ -22,32 +22,6 @@ template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
 constexpr int kRegMaxThreads = 512;
 constexpr int kRegElems = 16;
 
-// block_sum with a single barrier: consecutive calls alternate between the two halves of scratch (2 x 64
-// values), so a half is written again only after every thread has passed the barrier of the call in between,
-// and the barrier orders every shared-memory access before the call against every access after it.  All
-// threads make the same sequence of calls; the sums are formed in the same order as block_sum's.
-template <int NV>
-__device__ __forceinline__ void block_sum_alt(float (&v)[NV], float* scratch, int& phase) {
-  static_assert(NV <= 2, "two halves of 2 x 32 values");
-#pragma unroll
-  for (int q = 0; q < NV; ++q)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-  float* s = scratch + (phase ? 64 : 0);
-  phase ^= 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) s[q * 32 + warp] = v[q];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    float acc = 0;
-    for (int w = 0; w < nw; ++w) acc += s[q * 32 + w];
-    v[q] = acc;
-  }
-}
-
 // The embedding length L = 32 NT, for which the first and last FFT passes (2^r0 points at stride
 // S0 = L / 2^r0, a multiple of NT) only touch elements t + NT m of one thread t.
 template <int NT> __host__ __device__ constexpr int own_logL() { return NT == 64 ? 11 : NT == 128 ? 12 : NT == 256 ? 13 : 14; }
@@ -203,8 +177,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     cocg_reg_kernel(float2* __restrict__ xb, const float2* __restrict__ x0b, int M, int logL, int nsys,
                     CocgTables32 tb, float tol, int maxit, int* __restrict__ iters, int* __restrict__ flags) {
   extern __shared__ unsigned char smraw[];
-  __shared__ float red[4 * 32];  // two halves for block_sum_alt
-  int bphase = 0;
+  __shared__ float red[4 * 32];
   float2* buf = reinterpret_cast<float2*>(smraw);
   float2* q = buf + padded_size(1 << logL);
   float2* pt = q + (1 << logL) / 4;  // per-pass twiddle tables
@@ -226,7 +199,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       r[j] = (i < M) ? x[i] : float2{0, 0};
       nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
     }
-    block_sum_alt(nb2, red, bphase);
+    block_sum<float, 1>(nb2, red);
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
@@ -257,7 +230,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
           r02[0] += rj.x * rj.x + rj.y * rj.y;
         }
       }
-      block_sum_alt(r02, red, bphase);
+      block_sum<float, 1>(r02, red);
       if (r02[0] < nb2[0]) {  // uniform across the block
         accepted = 1;
 #pragma unroll
@@ -288,7 +261,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       rho2[0] += r[j].x * z.x - r[j].y * z.y;
       rho2[1] += r[j].x * z.y + r[j].y * z.x;
     }
-    block_sum_alt(rho2, red, bphase);
+    block_sum<float, 2>(rho2, red);
     float2 rho{rho2[0], rho2[1]};
     int it = 0, flag = 1;
     while (it < maxit) {
@@ -304,7 +277,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
           pq2[1] += p[j].x * qq.y + p[j].y * qq.x;
         }
       }
-      block_sum_alt(pq2, red, bphase);
+      block_sum<float, 2>(pq2, red);
       const float2 pq{pq2[0], pq2[1]};
       if (!(pq.x * pq.x + pq.y * pq.y > 0.0f)) { flag = 2; break; }
       const float2 a = cdiv(rho, pq);
@@ -319,7 +292,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
           rr[0] += r[j].x * r[j].x + r[j].y * r[j].y;
         }
       }
-      block_sum_alt(rr, red, bphase);
+      block_sum<float, 1>(rr, red);
       ++it;
       if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
       if (rr[0] <= thr) { flag = 0; break; }
@@ -334,7 +307,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
           rn2[1] += r[j].x * z.y + r[j].y * z.x;
         }
       }
-      block_sum_alt(rn2, red, bphase);
+      block_sum<float, 2>(rn2, red);
       const float2 rho_new{rn2[0], rn2[1]};
       if (!(rho.x * rho.x + rho.y * rho.y > 0.0f)) { flag = 2; break; }
       const float2 beta = cdiv(rho_new, rho);
