@@ -184,8 +184,11 @@ aao_status aao_bc_precond_apply(aao_plan* plan, const double* v_dev, double* z_d
 /*
  * Solves calA U = F by restarted right-preconditioned flexible GMRES with
  * the preconditioner of aao_bc_precond_apply, CGS2 orthogonalisation and
- * Givens rotations in FP64.  Stops when the true relative residual, computed
- * in FP64 at the end of a cycle, is <= opts.tol.
+ * Givens rotations (AAO_PREC_FP64: basis and CGS2 in FP64; AAO_PREC_MIXED:
+ * the basis in float-float pairs of ~48 bits with CGS2 on the FP32 pipe;
+ * Hessenberg matrix, rotations and the update of U in FP64 in both).  Stops
+ * when the true relative residual, computed in FP64 at the end of a cycle,
+ * is <= opts.tol.
  * F_dev: double[Nt][M]; U_dev: double[Nt][M], initial guess on entry (zero it
  * for x0 = 0), solution on exit.  info may be NULL.  Returns AAO_ENOCONV if
  * max_cycles pass without meeting tol (U then holds the last iterate).
