@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--held-out", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison arms of the default run (plain FP64, the paper's eps, config 1)")
     return ap.parse_args()
 
 
@@ -322,6 +324,70 @@ def cocg2d_flops(Mx, My, inner_iters_sum, n_apply, nsys):
     return inner_iters_sum * per_it + n_apply * nsys * pre
 
 
+def timed_solves(plans, Fs, reps, barrier):
+    """One solve per (plan, F) pair, `reps` rounds, timed with CUDA events on the current stream after one
+    untimed round; returns (ms per solve, infos of the timed solves)."""
+    import torch
+    U = torch.zeros(Fs[0].shape, dtype=torch.float64, device=Fs[0].device)
+    for p, F in zip(plans, Fs):
+        U.zero_()
+        p.gmres_solve(F, U)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    barrier()
+    ev0.record(stream)
+    for _ in range(reps):
+        for p, F in zip(plans, Fs):
+            U.zero_()
+            infos.append(p.gmres_solve(F, U))
+    ev1.record(stream)
+    barrier()
+    return ev0.elapsed_time(ev1) / (reps * len(plans)), infos
+
+
+def comparison_arms(args, plans, Fs, rank, dev, barrier):
+    """The metric's comparison on the same config-2 inputs (and config 1): the plain FP64 solver, the mixed
+    solver at the paper's circulant parameter eps = min(0.5, 0.5 tau) (Sec. 4), and the default mixed
+    solver at config 1 (M = 63, Nt = 64).  Each arm: value (unknowns x steps / s), ms per solve, outer
+    iterations and the largest true relative residual."""
+    import torch
+    from paper_2003_07020_gb300 import aao, workloads
+    M, Nt = args.M, args.Nt
+    out = {}
+
+    def summary(ms, infos, m, nt):
+        return {"value": m * nt / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                "outer_iters": [i["outer_iters"] for i in infos],
+                "true_rel_res_max": max(i["true_rel_res"] for i in infos)}
+
+    arms = [("plain_fp64", dict(prec=aao.AAO_PREC_FP64)),
+            ("mixed_paper_eps", dict(prec=aao.AAO_PREC_MIXED, eps=min(0.5, 0.5 / Nt)))]
+    for name, kw in arms:
+        ps = [aao.Plan(M, Nt, a, kappa=1.0, T=1.0, inner=aao.AAO_INNER_STRANG,
+                       matvec=aao.AAO_MATVEC_NTT if args.matvec == "ntt" else aao.AAO_MATVEC_FFT64, **kw)
+              for a in ALPHAS]
+        ms, infos = timed_solves(ps, Fs, 1, barrier)
+        out[name] = summary(ms, infos, M, Nt)
+        out[name]["eps"] = kw.get("eps", "default (min(0.5, 0.5 tau) for FP64)")
+        for p in ps:
+            p.close()
+    # config 1: M = 63, Nt = 64, alpha 1.5, u0 = sin(pi x), f ~ U[-1, 1]
+    m1, n1 = 63, 64
+    p1 = aao.Plan(m1, n1, 1.5, kappa=1.0, T=1.0, prec=aao.AAO_PREC_MIXED)
+    F1s = []
+    for i in range(4):
+        u0, f = workloads.make_inputs(m1, n1, seed=1000 * rank + i, recipe="sine1_uniform")
+        F1 = torch.empty((n1, m1), dtype=torch.float64, device=dev)
+        p1.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F1)
+        F1s.append(F1)
+    ms, infos = timed_solves([p1] * len(F1s), F1s, 10, barrier)
+    out["config1_mixed"] = summary(ms, infos, m1, n1)
+    out["config1_mixed"]["workload"] = "M=63, Nt=64, alpha=1.5, kappa=1, T=1, sine1_uniform (seeds 0-3)"
+    p1.close()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2003_07020_gb300 import aao, workloads
@@ -420,6 +486,9 @@ def run_ours(args):
     e2e = {"value": world * M * My * Nt * args.steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": M * My * Nt * 8, "d2h_bytes_per_step": M * My * Nt * 8}
 
+    compare = None
+    if args.dim == 1 and args.prec == "mixed" and not args.no_compare:
+        compare = comparison_arms(args, plans, Fs, rank, dev, barrier)
     if rank != 0:
         return
     # roofline of the dominant kernel
@@ -493,6 +562,8 @@ def run_ours(args):
         "gpu_launches": int(launches_timed),
         "clocks": clocks, "roofline": roof, "e2e": e2e,
     }
+    if compare:
+        line["config"]["comparison"] = compare
     if world == 1 and not args.no_cpu_baseline and args.dim == 1:
         line["cpu_baseline"] = cpu_baseline(M, Nt)
     print(json.dumps(line), flush=True)
@@ -560,11 +631,8 @@ def run_learned(args):
     Bt = 128
     net = aao.Fno(M, max_batch=max(Bt, nsys), seed=rank)
     t0 = time.perf_counter()
-    losses = []
-    for s in range(args.train_steps):
-        o = (s * Bt) % (n - Bt)
-        lr = 2e-3 * 0.5 * (1 + np.cos(np.pi * s / args.train_steps))
-        losses.append(net.train_step(B_all[o:o + Bt], L_all[o:o + Bt], A_all[o:o + Bt], X_all[o:o + Bt], lr=lr))
+    # the library's training loop (aao_fno_train): contiguous batches of the shuffled pairs, cosine schedule
+    losses = list(net.train(B_all, L_all, A_all, X_all, args.train_steps, batch=Bt, lr0=2e-3, seed=0))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del B_all, X_all, L_all, A_all

@@ -52,7 +52,10 @@ typedef enum {
 } aao_precision;
 
 typedef enum {
-  AAO_INNER_STRANG = 0, /* Strang circulant of T, applied by Bluestein FFTs */
+  AAO_INNER_STRANG = 0, /* Strang circulant S of T.  Mixed 1D plans with M <= 8192 apply
+                           (lambda_n I + c S)^{-1} as a precomputed L-point circulant spectrum per
+                           shifted system (2 FFTs of L); the FP64 path and larger M apply it by
+                           Bluestein FFTs of the M-point circulant (4 FFTs of L) */
   AAO_INNER_TAU = 1     /* natural tau-matrix T - H(T), applied by DST-I (Sec. 3.2) */
 } aao_inner_precond;
 
@@ -74,7 +77,10 @@ typedef enum {
 typedef struct {
   int dim;              /* 1 or 2 */
   int64_t M;            /* interior points (x direction in 2D); h = 1/(M+1); M+1 a power of two for AAO_INNER_TAU */
-  int64_t Nt;           /* time steps, a power of two >= 4; tau = T/Nt */
+  int64_t Nt;           /* time steps, a power of two >= 4; tau = T/Nt.  The time DFTs keep all Nt rows
+                           of a column tile in shared memory, which bounds Nt: at most 4096 with
+                           AAO_PREC_MIXED and 2048 with AAO_PREC_FP64 on a GPU with 227 KB per block
+                           (larger Nt: AAO_EINVAL at plan creation) */
   double T;             /* final time (> 0) */
   double alpha;         /* fractional order (x direction in 2D), 1 < alpha <= 2 */
   double kappa;         /* diffusion coefficient (x direction in 2D), > 0 */
@@ -166,8 +172,11 @@ aao_status aao_build_rhs(aao_plan* plan, const double* u0_dev, const double* f_d
 
 /*
  * w = calA v (Sec. 3.2): row k of w is sum_{j<=2} C[k,k-j] v_{k-j} - tau K v_k,
- * with the Toeplitz product by circulant embedding and FFT, in FP64.
- * v_dev, w_dev: double[Nt][M], must not alias.
+ * with the Toeplitz product by circulant embedding.  opts.matvec selects the
+ * arithmetic: AAO_MATVEC_NTT (the default in 1D) quantises each row of v to
+ * 58-bit fixed point and convolves it exactly by NTTs modulo five primes;
+ * AAO_MATVEC_FFT64 (and every 2D plan) uses FP64 FFTs.  Either way the
+ * result carries FP64 accuracy.  v_dev, w_dev: double[Nt][M], must not alias.
  */
 aao_status aao_matvec(aao_plan* plan, const double* v_dev, double* w_dev);
 
@@ -240,8 +249,14 @@ aao_status aao_plan_get_profile(aao_plan* plan, double* ms, int64_t* launches, i
  * that loads it until the process exits; problems whose scratch
  * (nsys * M * 8 bytes plus tables, nsys = Nt/2 + 1) exceeds it are rejected
  * with AAO_EINVAL.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Calls
- * share the array, so calls that overlap on the GPU race.  opts.prec must be
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Each
+ * call writes its tables into the array with small kernels that carry them
+ * as launch parameters, so it copies nothing from pageable host memory and
+ * does not wait for work already queued on cuda_stream.  Calls share the
+ * array, so calls that overlap on the GPU race.  The shifted solves are not
+ * reported: a system that reaches opts.inner_maxit without meeting
+ * opts.inner_tol leaves its last iterate in z without an error code (use a
+ * plan and aao_gmres_solve's info for that).  opts.prec must be
  * AAO_PREC_MIXED; v_dev, z_dev: double[Nt][M] on the device; cuda_stream as
  * in aao_plan_create.  Errors: see aao_last_error(NULL).
  */
@@ -313,6 +328,26 @@ aao_status aao_fno_loss_grad(aao_fno* fno, int B, const void* b_dev, const void*
 aao_status aao_fno_train_step(aao_fno* fno, int B, const void* b_dev, const void* lambda_dev,
                               const float* alpha_dev, const void* x_dev, float lr, double* loss,
                               void* cuda_stream);
+
+/*
+ * Trains fno for `steps` Adam steps (as aao_fno_train_step) on n_pairs
+ * stored pairs (b, lambda, alpha, x as in aao_fno_loss_grad, n_pairs rows
+ * each; typically recorded by aao_plan_record_pairs), batch systems per
+ * step (1 <= batch <= max_batch, batch <= n_pairs), with the cosine
+ * learning-rate schedule lr_t = lr0 (1 + cos(pi t / steps)) / 2,
+ * t = 0 .. steps-1.  Batches: with seed 0, step t takes the contiguous
+ * pairs [o, o + batch), o = (t batch) mod (n_pairs - batch) (the pairs
+ * should then be stored in random order; o = 0 when n_pairs = batch);
+ * with seed != 0, every epoch of floor(n_pairs / batch) steps visits the
+ * pairs in a fresh permutation (Fisher-Yates driven by SplitMix64 from
+ * seed), gathered into model-owned buffers (allocated on the first such
+ * call).  losses_host (may be NULL): host double[steps] receiving each
+ * step's batch loss before its update.  Runs without host synchronisation
+ * per step; synchronises the stream at the end when losses_host is given.
+ */
+aao_status aao_fno_train(aao_fno* fno, int64_t n_pairs, const void* b_dev, const void* lambda_dev,
+                         const float* alpha_dev, const void* x_dev, int steps, int batch, float lr0, uint64_t seed,
+                         double* losses_host, void* cuda_stream);
 
 /*
  * Attaches fno (not owned; NULL detaches) to a 1D AAO_PREC_MIXED plan with

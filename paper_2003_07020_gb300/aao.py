@@ -28,7 +28,7 @@ EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan
             "aao_bc_precond_apply_noalloc", "aao_solve_batched", "aao_last_error",
             "aao_fno_num_params", "aao_fno_create", "aao_fno_destroy", "aao_fno_set_params",
             "aao_fno_get_params", "aao_fno_save", "aao_fno_load", "aao_fno_predict", "aao_fno_loss_grad",
-            "aao_fno_train_step", "aao_plan_set_warm_start", "aao_plan_record_pairs",
+            "aao_fno_train_step", "aao_fno_train", "aao_plan_set_warm_start", "aao_plan_record_pairs",
             "aao_plan_recorded_pairs", "aao_plan_get_tuning")
 STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector", "fno")
 
@@ -103,6 +103,8 @@ def load():
     lib.aao_fno_predict.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp]
     lib.aao_fno_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(dbl), vp, vp]
     lib.aao_fno_train_step.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_float, ctypes.POINTER(dbl), vp]
+    lib.aao_fno_train.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                  ctypes.c_uint64, vp, vp]
     lib.aao_plan_set_warm_start.argtypes = [vp, vp]
     lib.aao_plan_record_pairs.argtypes = [vp, i64, vp, vp, vp]
     lib.aao_plan_recorded_pairs.argtypes = [vp, ctypes.POINTER(i64)]
@@ -359,6 +361,18 @@ class Fno:
         _check(load().aao_fno_train_step(self.handle, B, pb, pl, pa, ctypes.c_void_p(x.data_ptr()), float(lr),
                                          ctypes.byref(loss), _stream_ptr(stream)))
         return loss.value
+
+
+    def train(self, b, lam, alpha, x, steps, batch=128, lr0=2e-3, seed=0, stream=None):
+        """aao_fno_train over all pairs in b, lam, alpha, x; returns the per-step batch losses."""
+        n, pb, pl, pa = self._args(b, lam, alpha)
+        if not (x.is_cuda and x.is_contiguous() and x.shape == b.shape and x.dtype == b.dtype):
+            raise ValueError("x must be like b")
+        losses = np.zeros(int(steps), dtype=np.float64)
+        _check(load().aao_fno_train(self.handle, n, pb, pl, pa, ctypes.c_void_p(x.data_ptr()), int(steps), int(batch),
+                                    float(lr0), int(seed), losses.ctypes.data_as(ctypes.c_void_p),
+                                    _stream_ptr(stream)))
+        return losses
 
 
 def solve_batched(plans, Fs, Us, max_workers=0, raise_on_error=True):

@@ -116,32 +116,37 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
     }
     const R thr = tol * tol * nb2[0];
     precond<R, KIND>(buf, r, M, logL, lam, tb, q);
-    R rho2[2] = {0, 0};
+    R rho2[3] = {0, 0, 0};  // r^T z, |z|^2
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       const C z = z_at<R, KIND>(buf, i);
       const C ri = r[i];
       rho2[0] += ri.x * z.x - ri.y * z.y;
       rho2[1] += ri.x * z.y + ri.y * z.x;
+      rho2[2] += z.x * z.x + z.y * z.y;
       p[i] = z;
     }
-    block_sum<R, 2>(rho2, red);
+    block_sum<R, 3>(rho2, red);
     C rho{rho2[0], rho2[1]};
     int it = 0, flag = 1;
-    while (it < maxit) {
+    const bool bd0 = near_breakdown(rho2[0], rho2[1], rho2[2], nb2[0]);  // z^T r of the first step
+    if (bd0) flag = 2;
+    while (!bd0 && it < maxit) {
       // q = (lambda I + c T) p
       for (int j = threadIdx.x; j < L; j += blockDim.x) buf[pad16(j)] = (j < M) ? p[j] : C{0, 0};
       convolve(buf, logL, q, [&](int q) { return C{__ldg(&tb.Ebr[q]), (R)0}; });
-      R pq2[2] = {0, 0};
+      R pq2[4] = {0, 0, 0, 0};  // p^T q, |p|^2, |q|^2
       for (int i = threadIdx.x; i < M; i += blockDim.x) {
         const C pi = p[i];
         const C q = cadd(buf[pad16(i)], cmul(lam, pi));
         buf[pad16(i)] = q;
         pq2[0] += pi.x * q.x - pi.y * q.y;
         pq2[1] += pi.x * q.y + pi.y * q.x;
+        pq2[2] += pi.x * pi.x + pi.y * pi.y;
+        pq2[3] += q.x * q.x + q.y * q.y;
       }
-      block_sum<R, 2>(pq2, red);
+      block_sum<R, 4>(pq2, red);
       const C pq{pq2[0], pq2[1]};
-      if (!(pq.x * pq.x + pq.y * pq.y > (R)0)) { flag = 2; break; }
+      if (near_breakdown(pq2[0], pq2[1], pq2[2], pq2[3])) { flag = 2; break; }
       const C a = cdiv(rho, pq);
       R rr[1] = {0};
       for (int i = threadIdx.x; i < M; i += blockDim.x) {
@@ -160,16 +165,17 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
       if (!(rr[0] == rr[0]) || rr[0] > (R)1e30 * nb2[0]) { flag = 3; break; }
       if (rr[0] <= thr) { flag = 0; break; }
       precond<R, KIND>(buf, r, M, logL, lam, tb, q);
-      R rn2[2] = {0, 0};
+      R rn2[3] = {0, 0, 0};  // r^T z, |z|^2
       for (int i = threadIdx.x; i < M; i += blockDim.x) {
         const C z = z_at<R, KIND>(buf, i);
         const C ri = r[i];
         rn2[0] += ri.x * z.x - ri.y * z.y;
         rn2[1] += ri.x * z.y + ri.y * z.x;
+        rn2[2] += z.x * z.x + z.y * z.y;
       }
-      block_sum<R, 2>(rn2, red);
+      block_sum<R, 3>(rn2, red);
       const C rho_new{rn2[0], rn2[1]};
-      if (!(rho.x * rho.x + rho.y * rho.y > (R)0)) { flag = 2; break; }
+      if (near_breakdown(rn2[0], rn2[1], rn2[2], rr[0])) { flag = 2; break; }
       const C beta = cdiv(rho_new, rho);
       rho = rho_new;
       for (int i = threadIdx.x; i < M; i += blockDim.x) p[i] = cadd(z_at<R, KIND>(buf, i), cmul(beta, p[i]));

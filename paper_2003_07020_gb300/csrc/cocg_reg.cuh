@@ -14,6 +14,18 @@ template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
   return C{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
 
+// COCG breakdown test for a bilinear product u^T w used as a divisor: it is treated as zero when
+// |u^T w| <= kappa ||u|| ||w||, kappa = 64 units of roundoff, i.e. below the rounding error of
+// the dot product itself, where its phase is no longer determined by the data.
+template <typename R> __host__ __device__ constexpr R breakdown_rel() {
+  return sizeof(R) == 4 ? (R)(64.0 / 16777216.0) : (R)(64.0 / 9007199254740992.0);
+}
+template <typename R>
+__device__ __forceinline__ bool near_breakdown(R re, R im, R uu, R ww) {
+  const R k = breakdown_rel<R>();
+  return !(re * re + im * im > k * k * uu * ww);
+}
+
 // ---- FP32 path with register-resident vectors -------------------------------------------
 // NT threads (64 .. 512, chosen per problem by the autotuner of plan creation); thread t owns
 // elements i = t + NT j, j < 16 (M <= 16 NT), so r and p live in registers for the whole solve
@@ -251,7 +263,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     }
     // z = P^{-1} r, p = z, rho = r^T z
     precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
-    float rho2[2] = {0, 0};
+    float rho2[4] = {0, 0, 0, 0};  // r^T z, |z|^2, |r|^2
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
@@ -260,14 +272,18 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       p[j] = z;
       rho2[0] += r[j].x * z.x - r[j].y * z.y;
       rho2[1] += r[j].x * z.y + r[j].y * z.x;
+      rho2[2] += z.x * z.x + z.y * z.y;
+      rho2[3] += r[j].x * r[j].x + r[j].y * r[j].y;
     }
-    block_sum<float, 2>(rho2, red);
+    block_sum<float, 4>(rho2, red);
     float2 rho{rho2[0], rho2[1]};
     int it = 0, flag = 1;
-    while (it < maxit) {
+    const bool bd0 = near_breakdown(rho2[0], rho2[1], rho2[2], rho2[3]);  // z^T r of the first step
+    if (bd0) flag = 2;
+    while (!bd0 && it < maxit) {
       // q = (lambda I + c T) p
       toeplitz_reg<NT>(buf, p, M, logL, tb, q, pt);
-      float pq2[2] = {0, 0};
+      float pq2[4] = {0, 0, 0, 0};  // p^T q, |p|^2, |q|^2
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
         const int i = t + NT * j;
@@ -275,11 +291,13 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
           const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
           pq2[0] += p[j].x * qq.x - p[j].y * qq.y;
           pq2[1] += p[j].x * qq.y + p[j].y * qq.x;
+          pq2[2] += p[j].x * p[j].x + p[j].y * p[j].y;
+          pq2[3] += qq.x * qq.x + qq.y * qq.y;
         }
       }
-      block_sum<float, 2>(pq2, red);
+      block_sum<float, 4>(pq2, red);
       const float2 pq{pq2[0], pq2[1]};
-      if (!(pq.x * pq.x + pq.y * pq.y > 0.0f)) { flag = 2; break; }
+      if (near_breakdown(pq2[0], pq2[1], pq2[2], pq2[3])) { flag = 2; break; }
       const float2 a = cdiv(rho, pq);
       float rr[1] = {0};
 #pragma unroll
@@ -297,7 +315,7 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
       if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
       if (rr[0] <= thr) { flag = 0; break; }
       precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
-      float rn2[2] = {0, 0};
+      float rn2[3] = {0, 0, 0};  // r^T z, |z|^2
 #pragma unroll
       for (int j = 0; j < kRegElems; ++j) {
         const int i = t + NT * j;
@@ -305,11 +323,13 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
           const float2 z = zval<KIND>(buf, tb, i);
           rn2[0] += r[j].x * z.x - r[j].y * z.y;
           rn2[1] += r[j].x * z.y + r[j].y * z.x;
+          rn2[2] += z.x * z.x + z.y * z.y;
         }
       }
-      block_sum<float, 2>(rn2, red);
+      block_sum<float, 3>(rn2, red);
       const float2 rho_new{rn2[0], rn2[1]};
-      if (!(rho.x * rho.x + rho.y * rho.y > 0.0f)) { flag = 2; break; }
+      // rho_new divides the next beta: |r^T z| at rounding level of ||r|| ||z|| is a breakdown
+      if (near_breakdown(rn2[0], rn2[1], rn2[2], rr[0])) { flag = 2; break; }
       const float2 beta = cdiv(rho_new, rho);
       rho = rho_new;
 #pragma unroll

@@ -529,6 +529,23 @@ __global__ void k_to_bf16(const float* __restrict__ p, bf16* __restrict__ p16, i
 
 inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Batch gather for aao_fno_train: sample j of the batch is pair idx[j] of the training set.
+__global__ void k_gather_pairs(const float2* __restrict__ b, const float2* __restrict__ x,
+                               const double2* __restrict__ lam, const float* __restrict__ alpha,
+                               const int64_t* __restrict__ idx, int M, int B, float2* __restrict__ gb,
+                               float2* __restrict__ gx, double2* __restrict__ glam, float* __restrict__ galpha) {
+  const int j = blockIdx.y;
+  const int64_t src = idx[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    gb[(size_t)j * M + i] = b[(size_t)src * M + i];
+    gx[(size_t)j * M + i] = x[(size_t)src * M + i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    glam[j] = lam[src];
+    galpha[j] = alpha[src];
+  }
+}
+
 }  // namespace
 
 }  // namespace aao
@@ -546,6 +563,12 @@ struct aao_fno {
   float2 *H[aao::FL] = {}, *G = nullptr, *gG = nullptr, *gH = nullptr, *part = nullptr;
   float* opart = nullptr;  // weight-gradient block partials
   int nch = 0;  // DFT chunks of aao::DT points
+  // batch gather buffers of aao_fno_train (allocated on its first shuffled call)
+  float2 *gb = nullptr, *gx = nullptr;
+  double2* glam = nullptr;
+  float* galpha = nullptr;
+  int64_t* gidx = nullptr;
+  size_t gidx_cap = 0;
   std::vector<void*> allocs;
   std::string err;
 };
@@ -782,6 +805,31 @@ aao_status aao_fno_loss_grad(aao_fno* f, int B, const void* b, const void* lambd
   return AAO_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// One Adam step on B samples without host synchronisation; the per-sample losses of the batch
+// (before the step) are copied to loss_out (device, B floats) when it is not NULL.
+aao_status fno_train_step_dev(aao_fno* f, int B, const float2* b, const double2* lam, const float* alpha,
+                              const float2* x_true, float lr, float* loss_out, cudaStream_t s) {
+  aao_status st = fno_forward(f, B, b, lam, alpha, s);
+  if (st != AAO_OK) return st;
+  aao::k_loss<<<B, 256, 0, s>>>(f->y, x_true, f->norms, f->M, B, f->dy, f->loss);
+  st = fno_backward(f, B, s);
+  if (st != AAO_OK) return st;
+  if (loss_out) FCK(cudaMemcpyAsync(loss_out, f->loss, (size_t)B * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  f->steps++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - std::pow(b1, (float)f->steps), c2 = 1.0f - std::pow(b2, (float)f->steps);
+  aao::k_adam<<<aao::nblk(aao::NPARAM), 256, 0, s>>>(f->P32, f->G32, f->Am, f->Av, f->P16, aao::NPARAM, lr, b1, b2,
+                                                     1e-8f, c1, c2);
+  FCK(cudaGetLastError());
+  return AAO_OK;
+}
+}  // namespace
+
+extern "C" {
+
 aao_status aao_fno_train_step(aao_fno* f, int B, const void* b, const void* lambda, const float* alpha,
                               const void* x_true, float lr, double* loss, void* stream) {
   aao_status st = aao_fno_loss_grad(f, B, b, lambda, alpha, x_true, loss, nullptr, stream);
@@ -793,6 +841,87 @@ aao_status aao_fno_train_step(aao_fno* f, int B, const void* b, const void* lamb
                                                                         aao::NPARAM, lr, b1, b2, 1e-8f, c1, c2);
   FCK(cudaGetLastError());
   return AAO_OK;
+}
+
+aao_status aao_fno_train(aao_fno* f, int64_t n_pairs, const void* b, const void* lambda, const float* alpha,
+                         const void* x_true, int steps, int batch, float lr0, uint64_t seed, double* losses_host,
+                         void* stream) {
+  aao_status st = check_batch(f, batch);
+  if (st != AAO_OK) return st;
+  if (!b || !lambda || !alpha || !x_true) return ffail(f, AAO_EINVAL, "null pointer");
+  if (steps < 0 || n_pairs < batch) return ffail(f, AAO_EINVAL, "need steps >= 0 and n_pairs >= batch");
+  if (steps == 0) return AAO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int M = f->M;
+  const float2* bp = (const float2*)b;
+  const float2* xp = (const float2*)x_true;
+  const double2* lp = (const double2*)lambda;
+  // per-sample losses of every step stay on the device until the end (no synchronisation per step)
+  float* loss_dev = nullptr;
+  if (losses_host && cudaMalloc(&loss_dev, (size_t)steps * batch * sizeof(float)) != cudaSuccess)
+    return ffail(f, AAO_ENOMEM, "cudaMalloc failed");
+  auto release = [&](aao_status r) {
+    if (loss_dev) cudaFree(loss_dev);
+    return r;
+  };
+  // seed != 0: batches are gathered through a per-epoch permutation (Fisher-Yates on SplitMix64)
+  std::vector<int64_t> perm;
+  const int64_t per_epoch = n_pairs / batch;
+  if (seed != 0) {
+    if (!f->gb) {
+      const size_t N = (size_t)f->maxB * M;
+      if (falloc(f, &f->gb, N) != AAO_OK || falloc(f, &f->gx, N) != AAO_OK ||
+          falloc(f, &f->glam, (size_t)f->maxB) != AAO_OK || falloc(f, &f->galpha, (size_t)f->maxB) != AAO_OK)
+        return release(ffail(f, AAO_ENOMEM, "cudaMalloc failed"));
+    }
+    if (f->gidx_cap < (size_t)n_pairs) {  // index buffers of earlier calls stay in f->allocs until destroy
+      if (falloc(f, &f->gidx, (size_t)n_pairs) != AAO_OK) return release(ffail(f, AAO_ENOMEM, "cudaMalloc failed"));
+      f->gidx_cap = (size_t)n_pairs;
+    }
+    perm.resize((size_t)n_pairs);
+  }
+  uint64_t rng = seed;
+  auto next = [&]() {
+    uint64_t z = (rng += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const double pi = 3.14159265358979323846;
+  for (int t = 0; t < steps; ++t) {
+    const float lr = (float)(lr0 * 0.5 * (1.0 + std::cos(pi * t / steps)));
+    float* lo = loss_dev ? loss_dev + (size_t)t * batch : nullptr;
+    if (seed == 0) {
+      const int64_t o = ((int64_t)t * batch) % (n_pairs - batch + (n_pairs == batch ? 1 : 0));
+      st = fno_train_step_dev(f, batch, bp + (size_t)o * M, lp + o, alpha + o, xp + (size_t)o * M, lr, lo, s);
+    } else {
+      const int64_t k = t % per_epoch;
+      if (k == 0) {  // a new epoch: a fresh permutation of all pairs
+        for (int64_t i = 0; i < n_pairs; ++i) perm[(size_t)i] = i;
+        for (int64_t i = n_pairs - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(next() % (uint64_t)(i + 1))]);
+        // pageable copy: staged before cudaMemcpyAsync returns, so perm may change afterwards
+        if (cudaMemcpyAsync(f->gidx, perm.data(), (size_t)n_pairs * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+          return release(ffail(f, AAO_ECUDA, "cudaMemcpyAsync failed"));
+      }
+      aao::k_gather_pairs<<<dim3((M + 255) / 256, batch), 256, 0, s>>>(bp, xp, lp, alpha, f->gidx + k * batch, M,
+                                                                       batch, f->gb, f->gx, f->glam, f->galpha);
+      st = fno_train_step_dev(f, batch, f->gb, f->glam, f->galpha, f->gx, lr, lo, s);
+    }
+    if (st != AAO_OK) return release(st);
+  }
+  if (losses_host) {
+    std::vector<float> l((size_t)steps * batch);
+    if (cudaMemcpyAsync(l.data(), loss_dev, l.size() * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return release(ffail(f, AAO_ECUDA, "loss readback failed"));
+    for (int t = 0; t < steps; ++t) {  // the batch mean of aao_fno_loss_grad, summed in the same order
+      double a = 0;
+      for (int j = 0; j < batch; ++j) a += l[(size_t)t * batch + j];
+      losses_host[t] = a / batch;
+    }
+  }
+  return release(AAO_OK);
 }
 
 aao_status aao_fno_save(aao_fno* f, const char* path) {

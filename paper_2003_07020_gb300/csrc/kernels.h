@@ -24,6 +24,10 @@ size_t matvec_smem_bytes(int logL);
 // ---- time DFT, Steps (a) and (c), tdft.cu -------------------------------------------
 // Step (a): out[n][i] = sum_k scale[k] theta^{nk} v[k][i], n = 0..Nt/2, theta = exp(2 pi i/Nt)
 // launch_tdft_fwd_f32_ff: the same with v a float-float vector (hi, lo per element; hi is used).
+// Shared memory of one time-DFT CTA (all Nt rows of an 8-column tile) and the largest power-of-two
+// Nt whose CTA fits in smem_limit bytes (the device's opt-in limit per block).
+size_t tdft_smem_bytes(int Nt, bool fp32);
+int tdft_max_Nt(bool fp32, size_t smem_limit);
 cudaError_t launch_tdft_fwd_f32_ff(const float2* v, float2* out, int M, int Nt, const float* scale,
                                    const float2* twNt, cudaStream_t s);
 cudaError_t launch_tdft_fwd_f32(const double* v, float2* out, int M, int Nt, const float* scale,

@@ -20,8 +20,15 @@
 // left there; nothing in it has to start at zero (each region is fully
 // written before it is read).  Two calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on the array.
+//
+// The tables (twiddles, spectra, shifts, scalings) are built on the host and
+// written into the array by small kernels that carry them in their launch
+// parameters (up to kChunkBytes per launch), so a call copies nothing from
+// pageable host memory and does not wait for work already queued on the
+// caller's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -37,6 +44,26 @@ constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// One launch's worth of table bytes, passed by value as the kernel's parameter (the kernel
+// parameter space holds up to 32764 bytes).
+constexpr unsigned kChunkBytes = 32 * 1024 - 64;
+struct __align__(16) TableChunk {
+  unsigned char* dst;
+  unsigned int bytes;
+  alignas(16) unsigned char data[kChunkBytes];
+};
+static_assert(sizeof(TableChunk) <= 32764 && kChunkBytes % 16 == 0, "one chunk must fit the parameter space");
+
+// dst[0 .. bytes) = data[0 .. bytes); dst and data are 16-byte aligned.
+__global__ void write_chunk_kernel(const __grid_constant__ TableChunk c) {
+  const unsigned n16 = c.bytes / 16;
+  const uint4* src = reinterpret_cast<const uint4*>(c.data);
+  uint4* dst = reinterpret_cast<uint4*>(c.dst);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x) dst[i] = src[i];
+  for (unsigned i = 16 * n16 + blockIdx.x * blockDim.x + threadIdx.x; i < c.bytes; i += gridDim.x * blockDim.x)
+    c.dst[i] = c.data[i];
+}
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
@@ -93,6 +120,16 @@ extern "C" aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, cons
   if (prob->M < 1 || prob->M > 8191) return noalloc_fail(AAO_EINVAL, "M must be in [1, 8191]");
   if (prob->Nt < 4 || prob->Nt > 65536 || (prob->Nt & (prob->Nt - 1)))
     return noalloc_fail(AAO_EINVAL, "Nt must be a power of two in [4, 65536]");
+  {  // a time-DFT CTA holds all Nt rows of its column tile in shared memory
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return noalloc_fail(AAO_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
+    const int lim = aao::tdft_max_Nt(true, (size_t)optin);
+    if (prob->Nt > lim)
+      return noalloc_fail(AAO_EINVAL, "Nt must be at most " + std::to_string(lim) +
+                                          " on this device (the time-DFT tile of Nt rows must fit in shared memory)");
+  }
   if (!(opts->inner_tol > 0) || opts->inner_maxit < 1) return noalloc_fail(AAO_EINVAL, "bad inner options");
   if (opts->inner != AAO_INNER_STRANG && opts->inner != AAO_INNER_TAU)
     return noalloc_fail(AAO_EINVAL, "bad inner preconditioner");
@@ -131,8 +168,20 @@ extern "C" aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, cons
   unsigned char* b = static_cast<unsigned char*>(base);
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
+  // region o of the array <- bytes of host memory, through kernel parameters (see the file comment)
+  TableChunk chunk;
   auto put = [&](size_t o, const void* src, size_t bytes) -> cudaError_t {
-    return bytes ? cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    const unsigned char* h = static_cast<const unsigned char*>(src);
+    for (size_t done = 0; done < bytes; done += kChunkBytes) {
+      const unsigned nb = (unsigned)std::min<size_t>(kChunkBytes, bytes - done);
+      chunk.dst = b + o + done;  // o is 256-aligned and kChunkBytes a multiple of 16
+      chunk.bytes = nb;
+      std::memcpy(chunk.data, h + done, nb);
+      write_chunk_kernel<<<8, 256, 0, s>>>(chunk);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   };
   const std::vector<float2> twL = to_f2(t.tw_L), twNt = to_f2(t.tw_Nt), chirp = to_f2(t.chirp),
                             chat = to_f2(t.chirp_hat_f);
@@ -151,7 +200,7 @@ extern "C" aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, cons
   if (e == cudaSuccess) e = put(o_chat, chat.data(), chat.size() * sizeof(float2));
   if (e == cudaSuccess) e = put(o_seig, seig.data(), seig.size() * sizeof(float));
   if (e == cudaSuccess) e = put(o_tau, tau.data(), tau.size() * sizeof(float));
-  if (e != cudaSuccess) return noalloc_fail(AAO_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return noalloc_fail(AAO_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
 
   float2* spec = reinterpret_cast<float2*>(b + o_spec);
   const float2* twNt_d = reinterpret_cast<const float2*>(b + o_twNt);
@@ -168,6 +217,5 @@ extern "C" aao_status aao_bc_precond_apply_noalloc(const aao_problem* prob, cons
   if (e == cudaSuccess)
     e = aao::launch_tdft_inv_f32_to_f64(spec, z_dev, M, Nt, reinterpret_cast<const float*>(b + o_sinv), twNt_d, s);
   if (e != cudaSuccess) return noalloc_fail(AAO_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-  // the host tables above are pageable: cudaMemcpyAsync has staged them before returning
   return AAO_OK;
 }

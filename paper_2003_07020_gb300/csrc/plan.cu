@@ -726,6 +726,17 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   }
   if (prob->Nt < 4 || prob->Nt > 65536 || (prob->Nt & (prob->Nt - 1)))
     return fail(nullptr, AAO_EINVAL, "Nt must be a power of two in [4, 65536]");
+  {  // a time-DFT CTA holds all Nt rows of its column tile in shared memory
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+      const int lim = aao::tdft_max_Nt(o->prec == AAO_PREC_MIXED, (size_t)optin);
+      if (prob->Nt > lim)
+        return fail(nullptr, AAO_EINVAL,
+                    "Nt must be at most " + std::to_string(lim) + " in this precision on this device (the time-DFT "
+                    "tile of Nt rows must fit in " + std::to_string(optin) + " bytes of shared memory)");
+    }
+  }
   if (o->restart < 1 || o->restart > kMaxRestart) return fail(nullptr, AAO_EINVAL, "restart must be in [1, 64]");
   if (o->max_cycles < 1) return fail(nullptr, AAO_EINVAL, "max_cycles must be >= 1");
   if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(nullptr, AAO_EINVAL, "tolerances must be > 0");

@@ -125,6 +125,15 @@ static size_t tdft_smem(int Nt) {
 
 static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
+size_t tdft_smem_bytes(int Nt, bool fp32) { return fp32 ? tdft_smem<float>(Nt) : tdft_smem<double>(Nt); }
+
+int tdft_max_Nt(bool fp32, size_t smem_limit) {
+  int best = 0;
+  for (int Nt = 4; Nt <= (1 << 16); Nt *= 2)
+    if (tdft_smem_bytes(Nt, fp32) <= smem_limit) best = Nt;
+  return best;
+}
+
 template <typename R, typename TV>
 static cudaError_t fwd(const TV* v, typename cplx_t<R>::type* out, int M, int Nt, const R* scale,
                        const typename cplx_t<R>::type* tw, cudaStream_t s) {

@@ -267,3 +267,31 @@ def test_training_lowers_loss_and_warm_start_solves_exactly():
     # iterations beyond run-to-run noise of the training (float atomics in the weight-gradient sums)
     assert warm_it <= 1.05 * cold_it, (warm_it, cold_it)
     net.close()
+
+
+def test_library_training_loop_equals_stepwise_calls():
+    # aao_fno_train with seed 0 runs the same Adam steps as aao_fno_train_step on contiguous batches of the
+    # stored pairs with the cosine schedule; the FNO kernels are deterministic, so losses and weights agree
+    # bit for bit.  With a seed it shuffles every epoch and must still lower the loss.
+    M, Nt = 127, 32
+    train = workloads.learned_instances(6, seed=31, M=M, Nt=Nt, first_seed=0)
+    b, x, lam, alpha = collect_pairs(train, applies=2)
+    P = b.shape[0]
+    perm = torch.randperm(P, generator=torch.Generator().manual_seed(1)).to(DEV)
+    b, x, lam, alpha = b[perm].contiguous(), x[perm].contiguous(), lam[perm].contiguous(), alpha[perm].contiguous()
+    B, steps, lr0 = 32, 60, 2e-3
+    with aao.Fno(M, max_batch=B, seed=3) as net_lib, aao.Fno(M, max_batch=B, seed=3) as net_step:
+        got = net_lib.train(b, lam, alpha, x, steps, batch=B, lr0=lr0, seed=0)
+        want = []
+        for t in range(steps):
+            o = (t * B) % (P - B)
+            lr = lr0 * 0.5 * (1 + np.cos(np.pi * t / steps))
+            want.append(net_step.train_step(b[o:o + B], lam[o:o + B], alpha[o:o + B], x[o:o + B], lr=lr))
+        np.testing.assert_array_equal(got, np.array(want))
+        np.testing.assert_array_equal(net_lib.get_params(), net_step.get_params())
+    with aao.Fno(M, max_batch=B, seed=3) as net:
+        losses = net.train(b, lam, alpha, x, 200, batch=B, lr0=lr0, seed=12345)
+        assert np.isfinite(losses).all()
+        assert np.mean(losses[-20:]) <= 0.6 * np.mean(losses[:10]), (losses[:10], losses[-20:])
+        with pytest.raises(aao.AaoError):
+            net.train(b[:8], lam[:8], alpha[:8], x[:8], 5, batch=B)  # fewer pairs than one batch

@@ -290,3 +290,48 @@ def test_gmres_parameter_extremes(alpha, kappa, T, prec):
     Useq = oaao.sequential_bdf2(K, tau, u0, f)
     bound = 1e-10 if prec == aao.AAO_PREC_FP64 else 1e-9
     assert rel(host(U), Useq) <= bound, rel(host(U), Useq)
+
+
+@pytest.mark.parametrize("prec,nt_max", [(aao.AAO_PREC_MIXED, 4096), (aao.AAO_PREC_FP64, 2048)])
+def test_largest_accepted_nt_solves_and_the_next_is_rejected(prec, nt_max):
+    # The time DFTs of Steps (a)/(c) keep all Nt rows of a column tile in shared memory (227 KB per block on
+    # this GPU): the largest accepted Nt solves like any other, the next power of two is refused up front.
+    M, alpha = 15, 1.6
+    u0, f, U, info = solve_case(M, nt_max, alpha, prec, aao.AAO_INNER_TAU, recipe="sine1_uniform")
+    K = jac(M, alpha)
+    tau = 1.0 / nt_max
+    Useq = oaao.sequential_bdf2(K, tau, u0, f)
+    assert info["true_rel_res"] <= 1e-10, info
+    assert rel(U, Useq) <= (1e-9 if prec == aao.AAO_PREC_MIXED else 1e-10), rel(U, Useq)
+    with pytest.raises(aao.AaoError) as e:
+        aao.Plan(M, 2 * nt_max, alpha, prec=prec)
+    assert e.value.status == aao.AAO_EINVAL and "at most %d" % nt_max in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [aao.AAO_PREC_MIXED, aao.AAO_PREC_FP64])
+def test_cocg_breakdown_is_detected_and_fgmres_still_converges(prec):
+    # A crafted right-hand side whose frequency-1 shifted system has b^T A^{-1} b = 0 (complex b): at
+    # M = 2 the Strang circulant equals T, so COCG's first rho = r^T z = b^T A^{-1} b vanishes up to
+    # rounding.  The relative breakdown test (|u^T w| <= 64 u ||u|| ||w||) must report it
+    # (status_detail = AAO_EBREAKDOWN), and flexible GMRES absorbs the failed inner solve.
+    Nt, M, alpha = 8, 2, 1.5
+    tau = 1.0 / Nt
+    c = tau / (1.0 / (M + 1)) ** alpha
+    eps = mixed_eps(tau) if prec == aao.AAO_PREC_MIXED else oprec.default_eps(tau)
+    lam = oprec.eigenvalues_C_eps(Nt, eps)[1]
+    g = fcd.fcd_weights(alpha, M)
+    a, cp = lam + c * g[0], c * g[1]
+    b = np.array([1.0, (cp + np.sqrt(cp * cp - a * a + 0j)) / a])  # a (b0^2 + b1^2) - 2 cp b0 b1 = 0
+    k = np.arange(Nt)
+    F = (eps ** (-k / Nt))[:, None] * (2.0 / Nt) * np.real(b[None, :] * np.exp(-2j * np.pi * k / Nt)[:, None])
+    zh = oprec.time_dft_half(F, eps)  # Step (a) gives b at n = 1 and zero elsewhere
+    np.testing.assert_allclose(zh[1], b, atol=1e-12)
+    assert np.abs(np.delete(zh, 1, axis=0)).max() < 1e-12
+    with aao.Plan(M, Nt, alpha, prec=prec, inner=aao.AAO_INNER_STRANG, matvec=aao.AAO_MATVEC_FFT64) as plan:
+        U = torch.zeros((Nt, M), dtype=torch.float64, device=DEV)
+        info = plan.gmres_solve(cu(F), U)
+    assert info["status_detail"] == aao.AAO_EBREAKDOWN, info
+    K = jac(M, alpha)
+    assert oaao.true_relative_residual(K, tau, F, host(U)) <= 1e-10, info
+    np.testing.assert_allclose(host(U), np.linalg.solve(oaao.assemble_all_at_once(K, Nt, tau), F.ravel()).reshape(Nt, M),
+                               rtol=1e-9, atol=1e-12)

@@ -144,3 +144,23 @@ def test_2d_three_steps_by_fast_diagonalisation_equal_dense():
     np.testing.assert_allclose(z.ravel(), want, rtol=1e-11, atol=1e-12)
     np.testing.assert_allclose(precond.P_eps_matvec_2d(Kx, Ky, tau, eps, z).ravel(),
                                precond.P_eps_dense(K, tau, Nt, eps) @ z.ravel(), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("M,Nt", [(5, 8), (9, 16), (4, 12)])
+@pytest.mark.parametrize("eps", [1.0, 0.5, 1 / 16])
+def test_P_eps_matvec_equals_the_assembled_preconditioner(M, Nt, eps):
+    # P_eps = C_eps (x) I_s - tau I_t (x) K (Sec. 3.1) assembled by Kronecker products against the
+    # row form of P_eps_matvec: a transposed C_eps or K, or a sign slip, fails here
+    K, tau, _ = setup(M, Nt, 1.6)
+    Z = np.random.default_rng(9).standard_normal((Nt, M))
+    want = precond.P_eps_dense(K, tau, Nt, eps) @ Z.ravel()
+    np.testing.assert_allclose(precond.P_eps_matvec(K, tau, eps, Z).ravel(), want, rtol=1e-13, atol=1e-13)
+    # P_eps - calA = (C_eps - C) (x) I (Thm 3.1): only time rows 0 and 1 differ from the all-at-once
+    # product, by (1/2) z_0 + (eps/2) z_{Nt-2} - 2 eps z_{Nt-1} and (eps/2) z_{Nt-1}
+    D = precond.P_eps_matvec(K, tau, eps, Z) - aao.matvec(K, tau, Z)
+    np.testing.assert_allclose(D[0], 0.5 * Z[0] + 0.5 * eps * Z[Nt - 2] - 2 * eps * Z[Nt - 1], atol=1e-13)
+    np.testing.assert_allclose(D[1], 0.5 * eps * Z[Nt - 1], atol=1e-13)
+    np.testing.assert_allclose(D[2:], 0.0, atol=1e-13)
+    # and it inverts the three-step apply: P_eps (P_eps^{-1} v) = v
+    z, _, _ = precond.precond_apply(K, tau, eps, Z)
+    np.testing.assert_allclose(precond.P_eps_matvec(K, tau, eps, z), Z, rtol=1e-11, atol=1e-11)

@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("M,Nt,alpha,inner", [(63, 64, 1.5, aao.AAO_INNER_STRANG),
-                                              (1023, 32, 1.8, aao.AAO_INNER_TAU)])
+                                              (1023, 32, 1.8, aao.AAO_INNER_TAU),
+                                              (8191, 256, 1.5, aao.AAO_INNER_STRANG)])  # about 9 of the 16 MiB
 def test_noalloc_matches_plan_apply_twice(M, Nt, alpha, inner):
     lib = aao.load()
     v = torch.from_numpy(workloads.random_vector(Nt, M, seed=11)).to("cuda:0")
