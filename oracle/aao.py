@@ -146,6 +146,23 @@ def sequential_bdf2_2d(Kx, Ky, tau, u0, f):
     return U
 
 
+def windowed_bdf2(K, tau, u0, f, n_windows):
+    """The windowed (restarted) scheme of Sec. 2.2 (the remark after Thm 2.1): [0, T_hat] is split into
+    n_windows windows of Nt = f.shape[0] / n_windows steps each; window q is the all-at-once system of
+    Eq. 12 with u^0 = the last snapshot of window q - 1 (u0 for q = 0), so every window starts again with
+    the BDF1 step.  Each window is solved exactly by :func:`sequential_bdf2`.  ``f`` holds the sources of
+    all n_windows * Nt levels; returns U of the same shape."""
+    f = np.asarray(f, dtype=np.float64)
+    Nt = f.shape[0] // n_windows
+    assert Nt * n_windows == f.shape[0]
+    U = np.empty_like(f)
+    start = np.asarray(u0, dtype=np.float64)
+    for q in range(n_windows):
+        U[q * Nt:(q + 1) * Nt] = sequential_bdf2(K, tau, start, f[q * Nt:(q + 1) * Nt])
+        start = U[(q + 1) * Nt - 1]
+    return U
+
+
 def true_relative_residual(K, tau, F, U):
     """TRR = ||F - calA U||_2 / ||F||_2 (Sec. 4), with the dense matvec."""
     R = F - matvec(K, tau, U)

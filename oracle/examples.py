@@ -31,17 +31,24 @@ def ex1_source(alpha, kappa, x, t):
     return c * x ** 3 * (1 - x) ** 3 + c * kappa / (2.0 * math.cos(alpha * math.pi / 2.0)) * br
 
 
-def ex1_err(alpha, Nt, N, kappa=0.01, T=1.0):
-    """Err = ||u* - u^{Nt}||_inf of Example 1 on (0,1) with h = 1/N, M = N-1
-    interior points, tau = T/Nt, solved exactly by sequential BDF2."""
+def ex1_inputs(alpha, Nt, N, kappa=0.01, T=1.0, t0=0.0):
+    """Example 1 on (0,1) with h = 1/N, M = N-1 interior points, tau = T/Nt: returns
+    (x, K, u0, f) with u0 = u(x, t0) and f[k] = f(x, t0 + (k+1) tau), k < Nt."""
     h = 1.0 / N
     M = N - 1
     tau = T / Nt
     x = h * np.arange(1, M + 1)
     K = fcd.jacobian_1d(alpha, kappa, M, h)
-    u0 = ex1_exact(alpha, x, 0.0)
-    f = np.stack([ex1_source(alpha, kappa, x, (k + 1) * tau) for k in range(Nt)])
-    U = aao.sequential_bdf2(K, tau, u0, f)
+    u0 = ex1_exact(alpha, x, t0)
+    f = np.stack([ex1_source(alpha, kappa, x, t0 + (k + 1) * tau) for k in range(Nt)])
+    return x, K, u0, f
+
+
+def ex1_err(alpha, Nt, N, kappa=0.01, T=1.0):
+    """Err = ||u* - u^{Nt}||_inf of Example 1 on (0,1) with h = 1/N, M = N-1
+    interior points, tau = T/Nt, solved exactly by sequential BDF2."""
+    x, K, u0, f = ex1_inputs(alpha, Nt, N, kappa, T)
+    U = aao.sequential_bdf2(K, T / Nt, u0, f)
     return float(np.max(np.abs(ex1_exact(alpha, x, T) - U[-1])))
 
 
@@ -73,18 +80,25 @@ def ex2_source(a1, a2, k1, k2, x, y, t):
             + k2 * e / (2.0 * math.cos(a2 * math.pi / 2.0)) * _phi1(x) * _riesz_part(a2, y))
 
 
-def ex2_err(a1, a2, Nt, N, kappa=0.01, T=2.0):
-    """Err of Example 2 on (0,2)^2 with N intervals per direction (mesh width
-    2/N, N-1 interior points each way), tau = T/Nt, solved exactly by
-    sequential BDF2 with fast diagonalisation."""
+def ex2_inputs(a1, a2, Nt, N, kappa=0.01, T=2.0):
+    """Example 2 on (0,2)^2 with N intervals per direction (mesh width 2/N, N-1 interior points
+    each way), tau = T/Nt: returns (X, Y, Kx, Ky, u0, f), X[j, i] = x_i, Y[j, i] = y_j."""
     h = 2.0 / N
     M = N - 1
     tau = T / Nt
     z = h * np.arange(1, M + 1)
-    X, Y = np.meshgrid(z, z)          # X[j, i] = x_i, Y[j, i] = y_j
+    X, Y = np.meshgrid(z, z)
     Kx = fcd.jacobian_1d(a1, kappa, M, h)
     Ky = fcd.jacobian_1d(a2, kappa, M, h)
     u0 = ex2_exact(X, Y, 0.0)
     f = np.stack([ex2_source(a1, a2, kappa, kappa, X, Y, (k + 1) * tau) for k in range(Nt)])
-    U = aao.sequential_bdf2_2d(Kx, Ky, tau, u0, f)
+    return X, Y, Kx, Ky, u0, f
+
+
+def ex2_err(a1, a2, Nt, N, kappa=0.01, T=2.0):
+    """Err of Example 2 on (0,2)^2 with N intervals per direction (mesh width
+    2/N, N-1 interior points each way), tau = T/Nt, solved exactly by
+    sequential BDF2 with fast diagonalisation."""
+    X, Y, Kx, Ky, u0, f = ex2_inputs(a1, a2, Nt, N, kappa, T)
+    U = aao.sequential_bdf2_2d(Kx, Ky, T / Nt, u0, f)
     return float(np.max(np.abs(ex2_exact(X, Y, T) - U[-1])))

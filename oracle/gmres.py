@@ -71,3 +71,49 @@ def fgmres(matvec, precond, F, tol=1e-10, restart=20, max_cycles=50, x0=None):
         cycles += 1
         trr = np.linalg.norm(b - A(x)) / nb
     return x.reshape(shape), {"iters": iters, "cycles": cycles, "trr": trr}
+
+
+def bicgstab(matvec, precond, F, tol=1e-9, maxit=500, x0=None):
+    """Left-preconditioned BiCGSTAB (van der Vorst; Saad's Algorithm 7.7 applied to P^{-1} calA U =
+    P^{-1} F), the outer solver of Example 2 in Sec. 4.  Stops when the preconditioned residual
+    r_k = P^{-1}(F - calA U_k), carried by the recurrence, has ||r_k||_2 / ||r_0||_2 < tol, checked
+    after each half step (the s vector) and each full step; the iteration count is in halves as in
+    the paper's Tables 4-6.  Returns (U, info) with ``iters`` (half steps / 2), ``applies``
+    (preconditioner applications after the first) and the true relative residual ``trr``."""
+    F = np.asarray(F, dtype=np.float64)
+    shape = F.shape
+    b = F.ravel()
+    A = lambda v: np.asarray(matvec(v.reshape(shape)), dtype=np.float64).ravel()
+    P = lambda v: np.asarray(precond(v.reshape(shape)), dtype=np.float64).ravel()
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64).ravel()
+    r = P(b - A(x))
+    rhat = r.copy()
+    n0 = np.linalg.norm(r)
+    rho = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    halves = applies = 0
+    done = n0 == 0.0
+    while not done and halves < 2 * maxit:
+        rho_new = rhat @ r
+        beta = (rho_new / rho) * (alpha / omega)
+        rho = rho_new
+        p = r + beta * (p - omega * v)
+        v = P(A(p))
+        applies += 1
+        alpha = rho / (rhat @ v)
+        s = r - alpha * v
+        halves += 1
+        if np.linalg.norm(s) / n0 < tol:
+            x = x + alpha * p
+            break
+        t = P(A(s))
+        applies += 1
+        omega = (t @ s) / (t @ t)
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        halves += 1
+        done = np.linalg.norm(r) / n0 < tol
+    nb = np.linalg.norm(b)
+    trr = np.linalg.norm(b - A(x)) / nb if nb > 0 else 0.0
+    return x.reshape(shape), {"iters": halves / 2.0, "applies": applies, "trr": trr}

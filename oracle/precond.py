@@ -218,6 +218,40 @@ def tau_inverse(g_scaled, M, lam):
     return lambda r: sla.lu_solve(lu, r)
 
 
+def jacobian_tau(alpha, kappa, M, h):
+    """tau(A) = -(kappa / h^alpha) tau(T): the Jacobian with T replaced by its natural tau-matrix
+    approximation (Sec. 3.2, Eq. 3.9; in 2D the Kronecker sum of two of these, Sec. 4 Ex. 2).  The paper's
+    own Step (b) solves (lambda_n I - tau tau(A)) z_2 = z_1 directly (by DSTs); with this matrix in place
+    of K, :func:`precond_apply` (1D) and :func:`precond_apply_2d` (2D) apply that preconditioner."""
+    from . import fcd
+    return -(kappa / h ** alpha) * tau_matrix(fcd.fcd_weights(alpha, M), M)
+
+
+def time_S_eps(Nt, eps):
+    """C_eps - C (Sec. 3.1, the remark on the polynomial preconditioner: S_eps = (C_eps - C) (x) I):
+    nonzero only in time rows 0 and 1 (rank 2)."""
+    from . import aao
+    return C_eps(Nt, eps) - aao.time_matrix_C(Nt)
+
+
+def P_eps_poly_apply(K, tau, eps, V, m, K_pre=None):
+    """The m-step polynomial preconditioner of Sec. 3.1 (the remark after Thm 3.1):
+    P_eps(m) v = sum_{k=0}^{m} (P_eps^{-1} S_eps)^k P_eps^{-1} v, S_eps = (C_eps - C) (x) I_s, a truncation
+    of calA^{-1} = (I - P_eps^{-1} S_eps)^{-1} P_eps^{-1} since calA = P_eps - S_eps (the printed sum starts
+    at k = 1; the truncation it defines starts at k = 0).  Evaluated by Horner's rule
+    z <- P_eps^{-1} (v + S_eps z), m times after z = P_eps^{-1} v; P_eps^{-1} by :func:`precond_apply`
+    (exact; with K_pre in place of K in Step (b) when given, e.g. :func:`jacobian_tau`)."""
+    V = np.asarray(V, dtype=np.float64)
+    Nt = V.shape[0]
+    Kp = K if K_pre is None else K_pre
+    S = time_S_eps(Nt, eps)
+    z, _, _ = precond_apply(Kp, tau, eps, V)
+    for _ in range(m):
+        w = V.reshape(Nt, -1) + S @ z.reshape(Nt, -1)
+        z, _, _ = precond_apply(Kp, tau, eps, w.reshape(V.shape))
+    return z
+
+
 def P_eps_matvec(K, tau, eps, Z):
     """P_eps z = vec(Z C_eps^T) - tau vec(K Z) in the row layout (dense C_eps and
     K; library matmuls).  For checking a computed z ~= P_eps^{-1} v by its

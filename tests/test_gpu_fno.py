@@ -283,9 +283,10 @@ def test_library_training_loop_equals_stepwise_calls():
     with aao.Fno(M, max_batch=B, seed=3) as net_lib, aao.Fno(M, max_batch=B, seed=3) as net_step:
         got = net_lib.train(b, lam, alpha, x, steps, batch=B, lr0=lr0, seed=0)
         want = []
+        lr0_f32 = float(np.float32(lr0))  # the entry point takes lr0 as a float
         for t in range(steps):
             o = (t * B) % (P - B)
-            lr = lr0 * 0.5 * (1 + np.cos(np.pi * t / steps))
+            lr = lr0_f32 * 0.5 * (1 + np.cos(np.pi * t / steps))
             want.append(net_step.train_step(b[o:o + B], lam[o:o + B], alpha[o:o + B], x[o:o + B], lr=lr))
         np.testing.assert_array_equal(got, np.array(want))
         np.testing.assert_array_equal(net_lib.get_params(), net_step.get_params())
