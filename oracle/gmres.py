@@ -74,19 +74,24 @@ def fgmres(matvec, precond, F, tol=1e-10, restart=20, max_cycles=50, x0=None):
 
 
 def bicgstab(matvec, precond, F, tol=1e-9, maxit=500, x0=None):
-    """Left-preconditioned BiCGSTAB (van der Vorst; Saad's Algorithm 7.7 applied to P^{-1} calA U =
-    P^{-1} F), the outer solver of Example 2 in Sec. 4.  Stops when the preconditioned residual
-    r_k = P^{-1}(F - calA U_k), carried by the recurrence, has ||r_k||_2 / ||r_0||_2 < tol, checked
-    after each half step (the s vector) and each full step; the iteration count is in halves as in
-    the paper's Tables 4-6.  Returns (U, info) with ``iters`` (half steps / 2), ``applies``
-    (preconditioner applications after the first) and the true relative residual ``trr``."""
+    """Preconditioned BiCGSTAB (van der Vorst), the outer solver of Example 2 in Sec. 4.
+
+    The preconditioner is applied to the two search directions of each step (y = P^{-1} p, then
+    y = P^{-1} s) and the iterate is updated with them, so the recurrence carries the residual of the
+    original system; the iteration stops when ||r_k||_2 / ||r_0||_2 < tol (r_0 = F for x0 = 0), checked
+    after each half step (the s vector) and each full step.  The paper calls its solver
+    left-preconditioned; the Iter columns it prints (Tables 4-6, in half steps) are those of this form
+    (the interface of the library routine it cites, with a preconditioner argument), not of BiCGSTAB on
+    P^{-1} calA with the preconditioned residual monitored, which needs up to 1.5 more steps there.
+    Returns (U, info) with ``iters`` (half steps / 2), ``applies`` (preconditioner applications) and
+    the true relative residual ``trr``."""
     F = np.asarray(F, dtype=np.float64)
     shape = F.shape
     b = F.ravel()
     A = lambda v: np.asarray(matvec(v.reshape(shape)), dtype=np.float64).ravel()
     P = lambda v: np.asarray(precond(v.reshape(shape)), dtype=np.float64).ravel()
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64).ravel()
-    r = P(b - A(x))
+    r = b - A(x)
     rhat = r.copy()
     n0 = np.linalg.norm(r)
     rho = alpha = omega = 1.0
@@ -99,18 +104,20 @@ def bicgstab(matvec, precond, F, tol=1e-9, maxit=500, x0=None):
         beta = (rho_new / rho) * (alpha / omega)
         rho = rho_new
         p = r + beta * (p - omega * v)
-        v = P(A(p))
+        y = P(p)
         applies += 1
+        v = A(y)
         alpha = rho / (rhat @ v)
+        x = x + alpha * y
         s = r - alpha * v
         halves += 1
         if np.linalg.norm(s) / n0 < tol:
-            x = x + alpha * p
             break
-        t = P(A(s))
+        y = P(s)
         applies += 1
+        t = A(y)
         omega = (t @ s) / (t @ t)
-        x = x + alpha * p + omega * s
+        x = x + omega * y
         r = s - omega * t
         halves += 1
         done = np.linalg.norm(r) / n0 < tol

@@ -71,7 +71,7 @@ def test_bicgstab_solves_and_stops_after_half_a_step_with_the_exact_precondition
     U, info = gmres.bicgstab(lambda V: aao.matvec(K, tau, V), lambda V: np.linalg.solve(P, V.ravel()).reshape(V.shape),
                              F, tol=1e-12)
     np.testing.assert_allclose(U.ravel(), np.linalg.solve(A, F.ravel()), rtol=1e-9, atol=1e-11)
-    assert info["trr"] <= 1e-10 and info["iters"] <= 2 * M + 1
+    assert info["trr"] <= 1e-11 and info["iters"] <= 2 * M + 1
     # with P = calA itself the first half step ends it (s = r - alpha v = 0)
     U1, info1 = gmres.bicgstab(lambda V: aao.matvec(K, tau, V),
                                lambda V: np.linalg.solve(A, V.ravel()).reshape(V.shape), F, tol=1e-12)
@@ -80,9 +80,9 @@ def test_bicgstab_solves_and_stops_after_half_a_step_with_the_exact_precondition
 
 
 def test_example2_bicgstab_iterations_and_err(golden):
-    # Tables 4-6 at N = 64, Nt = 64 (the rows the oracle finishes in seconds): BiCGSTAB with P_eps and P_1 on
-    # the left-preconditioned system, Step (b) by the 2D tau matrix.  Iter within one of the printed value
-    # (in half steps), P_eps below P_1, Err as printed.
+    # Tables 4-6 at N = 64, Nt = 64 (the rows the oracle finishes in seconds): preconditioned BiCGSTAB with
+    # P_eps and P_1, Step (b) by the 2D tau matrix.  Iter as printed (half steps), P_eps below P_1, Err as
+    # printed.
     errs = {(r[0], r[1], r[2], r[3]): (float(r[4]), float(r[5])) for r in golden("ex2_err.txt")}
     for a1, a2, Nt, N, it_e, it_1, _src in rows(golden, "ex2_iter.txt", lambda r: r[2] == "64" and r[3] == "64"):
         a1f, a2f, Nti, Ni = float(a1), float(a2), int(Nt), int(N)
@@ -97,7 +97,7 @@ def test_example2_bicgstab_iterations_and_err(golden):
                                      lambda V: precond.precond_apply_2d(Ktx, Kty, tau, eps, V), F, tol=1e-9)
             got.append((info["iters"], np.abs(examples.ex2_exact(X, Y, 2.0) - U[-1]).max()))
         (ie, ee), (i1, e1) = got
-        assert abs(ie - float(it_e)) <= 1.0 and abs(i1 - float(it_1)) <= 1.0, (a1, a2, got)
+        assert ie == float(it_e) and i1 == float(it_1), (a1, a2, got)
         assert ie < i1
         pe, p1 = errs[(a1, a2, Nt, N)]
         assert abs(ee - pe) <= 2e-4 * pe and abs(e1 - p1) <= 2e-4 * p1, (ee, pe, e1, p1)
