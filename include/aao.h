@@ -56,7 +56,15 @@ typedef enum {
                            (lambda_n I + c S)^{-1} as a precomputed L-point circulant spectrum per
                            shifted system (2 FFTs of L); the FP64 path and larger M apply it by
                            Bluestein FFTs of the M-point circulant (4 FFTs of L) */
-  AAO_INNER_TAU = 1     /* natural tau-matrix T - H(T), applied by DST-I (Sec. 3.2) */
+  AAO_INNER_TAU = 1,    /* natural tau-matrix T - H(T), applied by DST-I (Sec. 3.2), as the COCG
+                           preconditioner: Step (b) still solves with T to inner_tol */
+  AAO_INNER_TAU_DIRECT = 2 /* the paper's own Step (b) (Sec. 3.2, Eq. 3.9; 2D: Example 2, Eq. 4.5):
+                           each shifted system solved once, directly, with T replaced by its natural
+                           tau matrix, x_n = (lambda_n I + c tau(T))^{-1} zhat_n by one DST-I pair; no
+                           inner iterations (inner_tol and inner_maxit are ignored).  The
+                           preconditioner is then P_eps with tau(A) in place of A, a fixed linear
+                           operator (usable with aao_bicgstab_solve).  Needs M + 1 (and My + 1) to be
+                           powers of two */
 } aao_inner_precond;
 
 /* How the Toeplitz product c T v of the matvec (Sec. 3.2) is computed (1D). */
@@ -100,15 +108,23 @@ typedef struct {
   int inner_maxit;      /* COCG iteration cap per system [200] */
   aao_precision prec;   /* [AAO_PREC_MIXED] */
   aao_inner_precond inner; /* [AAO_INNER_STRANG] */
-  int use_graphs;       /* [1] 1D: run each restart cycle as one CUDA graph (the Arnoldi steps as
+  int use_graphs;       /* [1] run each restart cycle as one CUDA graph (the Arnoldi steps as
                            conditional nodes, Givens rotations on the device, one host synchronisation
-                           per cycle instead of one per step); ignored in 2D, while profiling, or
-                           while recording pairs.  0: host-driven steps. */
+                           per cycle instead of one per step; in 2D the COCG iterations of Step (b)
+                           are a conditional WHILE node inside each step); ignored while profiling
+                           or while recording pairs.  0: host-driven steps (2D Step (b) then still
+                           runs as one graph launch with its WHILE loop, except while profiling) */
   aao_matvec_kind matvec; /* [AAO_MATVEC_NTT] 1D matvec arithmetic; 2D always uses FP64 FFTs */
   int cocg_threads;     /* [0] mixed 1D, M <= 8192: CTA size of the register-resident COCG kernel
                            (64, 128, 256 or 512, at least M / 16); 0 lets plan creation time the
                            admissible sizes on the plan's own systems and keep the fastest (cached
                            per problem shape for the process) */
+  int poly_m;           /* [0] 0..16: apply the m-step polynomial preconditioner of Sec. 3.1 (the
+                           remark after Thm 3.1) instead of P_eps:
+                           P(m) v = sum_{k=0}^{m} (P_eps^{-1} S_eps)^k P_eps^{-1} v,
+                           S_eps = (C_eps - C) (x) I, by Horner's rule z <- P_eps^{-1}(v + S_eps z):
+                           m + 1 applications of Steps (a)-(c) per preconditioner call (plus n
+                           doubles of plan workspace) */
 } aao_opts;
 
 /* Result of a solve. */
@@ -211,6 +227,42 @@ aao_status aao_gmres_solve(aao_plan* plan, const double* F_dev, double* U_dev, a
  * memory (pinned memory gives the fastest copies).
  */
 aao_status aao_gmres_solve_host(aao_plan* plan, const double* F_host, double* U_host, aao_info* info);
+
+/*
+ * Solves calA U = F by preconditioned BiCGSTAB (van der Vorst; the outer
+ * solver of Example 2, Sec. 4) with the preconditioner of
+ * aao_bc_precond_apply (use AAO_INNER_TAU_DIRECT, or a tight inner_tol, so
+ * that P is a fixed operator; opts.poly_m applies as well).  P^{-1} is applied
+ * to the two search directions of each step and U is updated with them, so
+ * the recurrence carries the residual of calA U = F; the iteration stops when
+ * ||r_k||_2 <= opts.tol ||r_0||_2, tested after every half step (the paper's
+ * stopping rule, x0 = U_dev on entry; its Tables 4-6 count these half steps).
+ * At most opts.max_cycles * opts.restart iterations (AAO_ENOCONV beyond).
+ * The plan's Krylov workspace holds the seven BiCGSTAB vectors, so
+ * opts.restart must be >= 7.  U_dev: initial guess on entry, solution on
+ * exit.  info (may be NULL): outer_iters = half steps (one preconditioner
+ * application each; the paper's Iter is outer_iters / 2), true_rel_res =
+ * ||F - calA U||_2 / ||F||_2 recomputed in FP64 at exit, inner statistics as
+ * for aao_gmres_solve.  A zero denominator (rho, (r0^, v) or (t, t)) returns
+ * AAO_EBREAKDOWN with U at its last update.  Synchronises the stream (several
+ * times per iteration: the scalars live on the host).
+ */
+aao_status aao_bicgstab_solve(aao_plan* plan, const double* F_dev, double* U_dev, aao_info* info);
+
+/*
+ * The windowed restart of Sec. 2.2 (the remark after Thm 2.1): the interval
+ * [0, n_windows T] is covered by n_windows all-at-once systems of the plan's
+ * size (Nt steps of tau = T/Nt each); window q solves Eq. 12 with u^0 = the
+ * last time level of window q - 1 (u0_dev for q = 0) by aao_gmres_solve from
+ * x0 = 0.  f_dev: double[n_windows Nt][M] holding f at every time level
+ * t_k = (k+1) tau, k < n_windows Nt; U_dev: double[n_windows Nt][M], the
+ * solution at those levels (must not alias f_dev).  info (may be NULL):
+ * outer_iters, matvecs, cycles, inner_iters_* summed over the windows,
+ * true_rel_res the largest window's.  Stops at the first window that fails.
+ * Synchronises the stream.
+ */
+aao_status aao_solve_windows(aao_plan* plan, int n_windows, const double* u0_dev, const double* f_dev,
+                             double* U_dev, aao_info* info);
 
 /*
  * Solves n independent problems (different M, Nt, alpha, kappa, precision)

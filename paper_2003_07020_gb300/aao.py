@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libaao.so")
 
 AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOCONV, AAO_EBREAKDOWN, AAO_ENONFINITE = range(7)
 AAO_PREC_FP64, AAO_PREC_MIXED = 0, 1
-AAO_INNER_STRANG, AAO_INNER_TAU = 0, 1
+AAO_INNER_STRANG, AAO_INNER_TAU, AAO_INNER_TAU_DIRECT = 0, 1, 2
 AAO_MATVEC_FFT64, AAO_MATVEC_NTT = 0, 1
 STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4: "AAO_ENOCONV",
                 5: "AAO_EBREAKDOWN", 6: "AAO_ENONFINITE"}
@@ -29,7 +29,7 @@ EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan
             "aao_fno_num_params", "aao_fno_create", "aao_fno_destroy", "aao_fno_set_params",
             "aao_fno_get_params", "aao_fno_save", "aao_fno_load", "aao_fno_predict", "aao_fno_loss_grad",
             "aao_fno_train_step", "aao_fno_train", "aao_plan_set_warm_start", "aao_plan_record_pairs",
-            "aao_plan_recorded_pairs", "aao_plan_get_tuning")
+            "aao_plan_recorded_pairs", "aao_plan_get_tuning", "aao_bicgstab_solve", "aao_solve_windows")
 STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector", "fno")
 
 
@@ -43,7 +43,7 @@ class AaoOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("inner_maxit", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner", ctypes.c_int), ("use_graphs", ctypes.c_int), ("matvec", ctypes.c_int),
-                ("cocg_threads", ctypes.c_int)]
+                ("cocg_threads", ctypes.c_int), ("poly_m", ctypes.c_int)]
 
 
 class AaoInfo(ctypes.Structure):
@@ -86,6 +86,8 @@ def load():
     lib.aao_bc_precond_apply.argtypes = [vp, vp, vp]
     lib.aao_gmres_solve.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
     lib.aao_gmres_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
+    lib.aao_bicgstab_solve.argtypes = [vp, vp, vp, ctypes.POINTER(AaoInfo)]
+    lib.aao_solve_windows.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(AaoInfo)]
     lib.aao_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.aao_plan_get_profile.argtypes = [vp, vp, vp, ctypes.c_int]
     lib.aao_solve_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int]
@@ -231,6 +233,29 @@ class Plan:
         st = load().aao_gmres_solve(self.handle, self._vec(F, "F"), self._vec(U, "U"), ctypes.byref(info))
         if st != AAO_OK and (raise_on_noconv or st != AAO_ENOCONV):
             _check(st, self.handle)
+        return info.as_dict()
+
+    def bicgstab_solve(self, F, U, raise_on_noconv=True):
+        """aao_bicgstab_solve: left-preconditioned BiCGSTAB; U is the initial guess on entry."""
+        info = AaoInfo()
+        st = load().aao_bicgstab_solve(self.handle, self._vec(F, "F"), self._vec(U, "U"), ctypes.byref(info))
+        if st != AAO_OK and (raise_on_noconv or st != AAO_ENOCONV):
+            _check(st, self.handle)
+        return info.as_dict()
+
+    def solve_windows(self, u0, f, U):
+        """aao_solve_windows: f and U hold n_windows * Nt time levels (shape (n_windows * Nt, ...))."""
+        n = self.M * self.My * self.Nt
+        for t, name in ((f, "f"), (U, "U")):
+            if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+                    and t.numel() % n == 0 and t.numel() > 0):
+                raise ValueError("%s must be a contiguous float64 CUDA tensor of n_windows * Nt * M elements" % name)
+        if f.numel() != U.numel() or not (u0.is_cuda and u0.numel() == self.M * self.My):
+            raise ValueError("f and U must match and u0 must hold one time level")
+        info = AaoInfo()
+        _check(load().aao_solve_windows(self.handle, f.numel() // n, ctypes.c_void_p(u0.data_ptr()),
+                                        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                        ctypes.byref(info)), self.handle)
         return info.as_dict()
 
     def gmres_solve_host(self, F_host, U_host, raise_on_noconv=True):

@@ -362,6 +362,42 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restri
     out[e] = (double)in[e];
 }
 
+// out = a x + b y + c z (z unused when null); each element is read before it is written, so out may
+// alias any input
+__global__ void lincomb3_kernel(double* out, double a, const double* x, double b, const double* y, double c,
+                                const double* z, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = a * x[e] + b * y[e];
+    if (z) v += c * z[e];
+    out[e] = v;
+  }
+}
+
+template <typename TV> __device__ __forceinline__ double ld_any(const TV* p, size_t e);
+template <> __device__ __forceinline__ double ld_any<double>(const double* p, size_t e) { return p[e]; }
+template <> __device__ __forceinline__ double ld_any<float>(const float* p, size_t e) { return f2d_bits(p[e]); }
+template <> __device__ __forceinline__ double ld_any<float2>(const float2* p, size_t e) {
+  const float2 v = p[e];
+  return f2d_bits(v.x) + f2d_bits(v.y);
+}
+
+// w = v + ((C_eps - C) (x) I) z: rows 0 and 1 carry the wrap-around terms of C_eps (Eq. 1.11) and the
+// difference 3/2 - 1 of the first diagonal entry; every other row is v.
+template <typename TV, typename TZ>
+__global__ void poly_rhs_kernel(double* __restrict__ w, const TV* __restrict__ v, const TZ* __restrict__ z,
+                                double eps, size_t Ms, int Nt) {
+  const size_t n = Ms * (size_t)Nt;
+  const size_t r2 = (size_t)(Nt - 2) * Ms, r1 = (size_t)(Nt - 1) * Ms;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double val = ld_any<TV>(v, e);
+    if (e < Ms)
+      val += 0.5 * ld_any<TZ>(z, e) + 0.5 * eps * ld_any<TZ>(z, r2 + e) - 2.0 * eps * ld_any<TZ>(z, r1 + e);
+    else if (e < 2 * Ms)
+      val += 0.5 * eps * ld_any<TZ>(z, r1 + (e - Ms));
+    w[e] = val;
+  }
+}
+
 // Dispatch on the number of vectors with a few compile-time caps.
 #define AAO_NV_DISPATCH(KERNEL, nv, ...)                                                          \
   do {                                                                                            \
@@ -438,6 +474,27 @@ cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int
 cudaError_t launch_build_rhs(const double* u0, const double* f, double* F, double tau, int M, int Nt,
                              cudaStream_t s) {
   build_rhs_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(u0, f, F, tau, M, (size_t)M * Nt);
+  return cudaGetLastError();
+}
+cudaError_t launch_lincomb3(double* out, double a, const double* x, double b, const double* y, double c,
+                            const double* z, size_t n, cudaStream_t s) {
+  lincomb3_kernel<<<kBlasBlocks, kBlasThreads, 0, s>>>(out, a, x, b, y, c, z, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_poly_rhs(double* w, const void* v, bool v_ff, const void* z, bool z_f32, double eps, size_t Ms,
+                            int Nt, cudaStream_t s) {
+  if (v_ff && z_f32)
+    poly_rhs_kernel<float2, float><<<kBlasBlocks, kBlasThreads, 0, s>>>(w, (const float2*)v, (const float*)z, eps,
+                                                                         Ms, Nt);
+  else if (v_ff)
+    poly_rhs_kernel<float2, double><<<kBlasBlocks, kBlasThreads, 0, s>>>(w, (const float2*)v, (const double*)z, eps,
+                                                                          Ms, Nt);
+  else if (z_f32)
+    poly_rhs_kernel<double, float><<<kBlasBlocks, kBlasThreads, 0, s>>>(w, (const double*)v, (const float*)z, eps,
+                                                                         Ms, Nt);
+  else
+    poly_rhs_kernel<double, double><<<kBlasBlocks, kBlasThreads, 0, s>>>(w, (const double*)v, (const double*)z, eps,
+                                                                          Ms, Nt);
   return cudaGetLastError();
 }
 cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s) {

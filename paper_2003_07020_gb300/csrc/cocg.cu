@@ -188,6 +188,32 @@ __global__ void __launch_bounds__(512) cocg_kernel(typename cplx_t<R>::type* __r
 }
 
 
+// The paper's own Step (b) (Sec. 3.2, Eq. 3.9; Example 2, Eq. 4.5): every shifted system solved
+// directly with the tau-matrix approximation, x_n = (lambda_n I + c tau(T))^{-1} zhat_n, by one DST-I
+// pair (the odd extension of length L = 2(M+1), one FFT convolution).  One CTA per system; no
+// inner iterations (iters[n] = 0, flags[n] = 0).
+template <typename R, bool GBUF>
+__global__ void __launch_bounds__(512) tau_direct_kernel(typename cplx_t<R>::type* __restrict__ xb,
+                                                         typename cplx_t<R>::type* __restrict__ gbuf, int M,
+                                                         int logL, int nsys, typename Tabs<R>::type tb,
+                                                         int* __restrict__ iters, int* __restrict__ flags) {
+  using C = typename cplx_t<R>::type;
+  extern __shared__ unsigned char smraw[];
+  C* buf = GBUF ? gbuf + (size_t)blockIdx.x * padded_size(1 << logL) : reinterpret_cast<C*>(smraw);
+  C* q = GBUF ? reinterpret_cast<C*>(smraw) : reinterpret_cast<C*>(smraw) + padded_size(1 << logL);
+  const int L = 1 << logL;
+  load_quarter(q, tb.twL, L / 4);
+  for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
+    const double2 lamd = tb.lambda[n];
+    const C lam = C{(R)lamd.x, (R)lamd.y};
+    C* x = xb + (size_t)n * M;
+    __syncthreads();  // the previous system's readers of buf are done
+    precond<R, 1>(buf, x, M, logL, lam, tb, q);  // ends synchronised
+    for (int i = threadIdx.x; i < M; i += blockDim.x) x[i] = z_at<R, 1>(buf, i);
+    if (threadIdx.x == 0) { iters[n] = 0; flags[n] = 0; }
+  }
+}
+
 static const size_t kSmemLimit = 200 * 1024;
 
 size_t cocg_gbuf_elems_f64(int logL, int grid) {
@@ -304,6 +330,32 @@ cudaError_t launch_cocg_f32(float2* xb, float2* rws, float2* pws, int M, int log
   if (inner == 0)
     return launch_k<float, 0, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
   return launch_k<float, 1, false>(xb, rws, pws, nullptr, M, logL, nsys, tb, tol, maxit, iters, flags, grid, s);
+}
+
+cudaError_t launch_tau_direct_f32(float2* xb, int M, int logL, int nsys, const CocgTables32& tb, int* iters,
+                                  int* flags, cudaStream_t s) {
+  const size_t smem = cocg_smem<float>(logL) + cocg_table_bytes<float>(logL);
+  cudaError_t e = allow_max_dynamic_smem(tau_direct_kernel<float, false>);
+  if (e != cudaSuccess) return e;
+  tau_direct_kernel<float, false><<<nsys, 512, smem, s>>>(xb, nullptr, M, logL, nsys, tb, iters, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tau_direct_f64(double2* xb, double2* gbuf, int M, int logL, int nsys, const CocgTables64& tb,
+                                  int* iters, int* flags, int grid, cudaStream_t s) {
+  const bool g = cocg_smem<double>(logL) > kSmemLimit;
+  if (g && !gbuf) return cudaErrorInvalidValue;
+  const size_t smem = (g ? 0 : cocg_smem<double>(logL)) + cocg_table_bytes<double>(logL);
+  if (g) {
+    cudaError_t e = allow_max_dynamic_smem(tau_direct_kernel<double, true>);
+    if (e != cudaSuccess) return e;
+    tau_direct_kernel<double, true><<<grid, 512, smem, s>>>(xb, gbuf, M, logL, nsys, tb, iters, flags);
+  } else {
+    cudaError_t e = allow_max_dynamic_smem(tau_direct_kernel<double, false>);
+    if (e != cudaSuccess) return e;
+    tau_direct_kernel<double, false><<<nsys, 512, smem, s>>>(xb, nullptr, M, logL, nsys, tb, iters, flags);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gbuf, int M, int logL, int nsys,

@@ -86,6 +86,13 @@ cudaError_t launch_cocg_f64(double2* xb, double2* rws, double2* pws, double2* gb
                             int nsys, int inner, const CocgTables64& tb, double tol, int maxit,
                             int* iters, int* flags, int grid, cudaStream_t s);
 size_t cocg_gbuf_elems_f64(int logL, int grid);
+// The direct tau-matrix Step (b): xb[n] <- (lambda_n I + c tau(T))^{-1} xb[n] for every n by one DST-I
+// convolution (L = 2(M+1)); iters[n] = flags[n] = 0.  FP64 uses gbuf (grid CTAs) when the transform
+// does not fit in shared memory (cocg_gbuf_elems_f64 != 0).
+cudaError_t launch_tau_direct_f32(float2* xb, int M, int logL, int nsys, const CocgTables32& tb, int* iters,
+                                  int* flags, cudaStream_t s);
+cudaError_t launch_tau_direct_f64(double2* xb, double2* gbuf, int M, int logL, int nsys, const CocgTables64& tb,
+                                  int* iters, int* flags, int grid, cudaStream_t s);
 int cocg_reg_min_threads(int M);
 // x[i] = deterministic pseudo-random values in [-1, 1)^2 (autotuner inputs)
 cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s);
@@ -163,11 +170,21 @@ template <typename R> struct Cocg2dArgs {
   int *iters, *flags;          // per system
   double tol;
   int maxit;
+  int* it_dev;                 // device int: iterations of the current graph-driven loop
+  long long* loops_total;      // device counter of graph-driven iterations (launch accounting)
 };
 size_t cocg2d_state_bytes(int nsys);
 int cocg2d_max_partials(int Mx, int My, int logLx, int logLy, int csize);
 cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* iters_run);
 cudaError_t launch_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, int* iters_run);
+// The same COCG recorded into the graph that s is capturing, its iterations as a conditional WHILE node
+// (body captured on body_stream): 7 start kernels + 1, then 13 kernels per iteration, no host wait.
+cudaError_t capture_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, cudaStream_t body_stream);
+cudaError_t capture_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, cudaStream_t body_stream);
+// The direct 2D tau-matrix Step (b) (Example 2, Eq. 4.5): X[n] <- (lambda_n I + c_x tau(T_x) (x) I +
+// I (x) c_y tau(T_y))^{-1} X[n] by 2D DSTs (uses Tm, Q, state; iters = flags = 0).
+cudaError_t launch_tau2d_direct_f32(const Cocg2dArgs<float>& a, cudaStream_t s);
+cudaError_t launch_tau2d_direct_f64(const Cocg2dArgs<double>& a, cudaStream_t s);
 
 // ---- vector kernels (FP64), blas.cu ----------------------------------------------------
 int blas_partial_blocks();
@@ -205,6 +222,15 @@ cudaError_t launch_zy_update_f64(double* U, const double* Z, size_t zstride, int
                                  const double* y, cudaStream_t s);
 cudaError_t launch_build_rhs(const double* u0, const double* f, double* F, double tau, int M, int Nt,
                              cudaStream_t s);
+// out = a x + b y + c z elementwise (z may be null when c = 0); out may alias x, y or z
+cudaError_t launch_lincomb3(double* out, double a, const double* x, double b, const double* y, double c,
+                            const double* z, size_t n, cudaStream_t s);
+// The right-hand side of one Horner step of the polynomial preconditioner (Sec. 3.1):
+// w = v + ((C_eps - C) (x) I) z, i.e. w = v except in time rows 0 and 1:
+//   w_0 = v_0 + z_0 / 2 + (eps/2) z_{Nt-2} - 2 eps z_{Nt-1},   w_1 = v_1 + (eps/2) z_{Nt-1}.
+// v: FP64 or float-float (hi + lo); z: FP64 or FP32; Ms unknowns per time level.
+cudaError_t launch_poly_rhs(double* w, const void* v, bool v_ff, const void* z, bool z_f32, double eps, size_t Ms,
+                            int Nt, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
 
 // Message reported by aao_last_error(NULL) (calls without a plan).

@@ -193,6 +193,12 @@ struct aao_plan {
   double2* part2d = nullptr;
   int* active2d = nullptr;
   int* host_count = nullptr;
+  // 2D COCG as a graph with a conditional WHILE loop (no host synchronisation per iteration)
+  cudaStream_t cap3 = nullptr, c2d_cap = nullptr;
+  cudaGraphExec_t c2d_exec = nullptr;
+  int* c2d_it = nullptr;
+  long long* c2d_loops = nullptr;  // device count of graph-driven COCG iterations
+  long long c2d_loops_seen = 0;
   size_t nsq = 0;  // partial sums produced by the residual matvec
   bool mixed = true;
   std::vector<void*> allocs;
@@ -229,6 +235,8 @@ struct aao_plan {
   double2* gbuf = nullptr;
   int cocg_grid = 0;
   int cocg_threads = 0;  // CTA size of the register-resident FP32 COCG kernel (0: not used)
+  bool direct = false;     // Step (b) by the direct tau-matrix solve (AAO_INNER_TAU_DIRECT)
+  double* polyw = nullptr; // n doubles: right-hand side of a Horner step of P_eps(m) (opts.poly_m > 0)
   float2* sconv = nullptr;  // mixed Strang: per-system spectra of (lambda_n I + c S)^{-1} as L-point circulants
   // exact-integer matvec (opts.matvec == AAO_MATVEC_NTT, 1D)
   bool ntt = false;
@@ -430,18 +438,57 @@ aao_status cocg2d_any(aao_plan* p, void* spec) {
   a.flags = p->flags;
   a.tol = p->opts.inner_tol;
   a.maxit = p->opts.inner_maxit;
-  int its = 0;
-  prof_begin(p);
-  cudaError_t e = sizeof(R) == 4 ? aao::launch_cocg2d_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream, &its)
-                                 : aao::launch_cocg2d_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, p->stream, &its);
-  if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("cocg2d: ") + cudaGetErrorString(e));
-  prof_end(p, ST_COCG, 4 + its * 11);
+  a.it_dev = p->c2d_it;
+  a.loops_total = p->c2d_loops;
+  if (p->direct) {
+    prof_begin(p);
+    cudaError_t e = sizeof(R) == 4 ? aao::launch_tau2d_direct_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream)
+                                   : aao::launch_tau2d_direct_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, p->stream);
+    if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("tau2d direct: ") + cudaGetErrorString(e));
+    prof_end(p, ST_COCG, 4);
+    return AAO_OK;
+  }
+  auto capture = [&](cudaStream_t cs) {
+    return sizeof(R) == 4 ? aao::capture_cocg2d_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, cs, p->cap3)
+                          : aao::capture_cocg2d_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, cs, p->cap3);
+  };
+  if (p->prof_on) {  // host-driven iterations, so that every launch can be counted and timed
+    int its = 0;
+    prof_begin(p);
+    cudaError_t e = sizeof(R) == 4 ? aao::launch_cocg2d_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream, &its)
+                                   : aao::launch_cocg2d_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, p->stream, &its);
+    if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("cocg2d: ") + cudaGetErrorString(e));
+    prof_end(p, ST_COCG, 7 + its * 9);
+    return AAO_OK;
+  }
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(p->stream, &cst));
+  if (cst == cudaStreamCaptureStatusActive) {  // inside a restart-cycle graph: the loop becomes a WHILE node
+    cudaError_t e = capture(p->stream);
+    if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("cocg2d capture: ") + cudaGetErrorString(e));
+    prof_end(p, ST_COCG, 8);
+    return AAO_OK;
+  }
+  if (!p->c2d_exec) {  // the standalone graph of the whole Step (b), built once per plan
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(p->c2d_cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = capture(p->c2d_cap);
+    cudaError_t e2 = cudaStreamEndCapture(p->c2d_cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->c2d_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->c2d_exec = nullptr;
+      return fail(p, AAO_ECUDA, std::string("cocg2d graph: ") + cudaGetErrorString(e));
+    }
+  }
+  LAUNCH(ST_COCG, 8, cudaGraphLaunch(p->c2d_exec, p->stream));
   return AAO_OK;
 }
 
-// out = P^{-1} v.  out_kind: 0 float (mixed Z basis), 1 double; v_ff: v is a float-float vector
-// (the mixed Arnoldi basis).
-aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind, bool v_ff = false) {
+// out = P_eps^{-1} v (Steps (a)-(c)).  out_kind: 0 float (mixed Z basis), 1 double; v_ff: v is a
+// float-float vector (the mixed Arnoldi basis).
+aao_status precond_once(aao_plan* p, const double* v, void* out, int out_kind, bool v_ff) {
   const int Ms = (int)p->Msp;
   if (p->mixed) {
     float2* spec = (float2*)p->spec;
@@ -467,10 +514,14 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind, bo
         if (fs != AAO_OK) return fail(p, fs, std::string("warm start: ") + aao_last_error(nullptr));
         prof_end(p, ST_FNO, kFnoLaunches);
       }
-      LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
-                                              (int)p->opts.inner, tb, (float)p->opts.inner_tol, p->opts.inner_maxit,
-                                              p->iters, p->flags, p->cocg_grid, p->stream,
-                                              p->fno ? p->x0buf : nullptr, p->cocg_threads));
+      if (p->direct)
+        LAUNCH(ST_COCG, 1, aao::launch_tau_direct_f32(spec, p->M, p->logL, p->nsys, tb, p->iters, p->flags,
+                                                      p->stream));
+      else
+        LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
+                                                (int)p->opts.inner, tb, (float)p->opts.inner_tol,
+                                                p->opts.inner_maxit, p->iters, p->flags, p->cocg_grid, p->stream,
+                                                p->fno ? p->x0buf : nullptr, p->cocg_threads));
       if (nrec > 0) {
         CK(cudaMemcpyAsync(p->rec_x + p->rec_count * p->M, spec, nrec * p->M * sizeof(float2),
                            cudaMemcpyDeviceToDevice, p->stream));
@@ -490,12 +541,29 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind, bo
       TRY(cocg2d_any<double>(p, spec));
     } else {
       aao::CocgTables64 tb{p->twL64, p->Ebr64, p->lambda, p->chirp64, p->chat64, p->seig64, p->tau64};
-      LAUNCH(ST_COCG, 1, aao::launch_cocg_f64(spec, (double2*)p->rws, (double2*)p->pws, p->gbuf, p->M, p->logL,
-                                              p->nsys, (int)p->opts.inner, tb, p->opts.inner_tol,
-                                              p->opts.inner_maxit, p->iters, p->flags, p->cocg_grid, p->stream));
+      if (p->direct)
+        LAUNCH(ST_COCG, 1, aao::launch_tau_direct_f64(spec, p->gbuf, p->M, p->logL, p->nsys, tb, p->iters, p->flags,
+                                                      p->cocg_grid, p->stream));
+      else
+        LAUNCH(ST_COCG, 1, aao::launch_cocg_f64(spec, (double2*)p->rws, (double2*)p->pws, p->gbuf, p->M, p->logL,
+                                                p->nsys, (int)p->opts.inner, tb, p->opts.inner_tol,
+                                                p->opts.inner_maxit, p->iters, p->flags, p->cocg_grid, p->stream));
     }
     LAUNCH(ST_TDFT_INV, 1, aao::launch_tdft_inv_f64(spec, (double*)out, Ms, p->Nt, p->sinv64, p->twNt64,
                                                     p->stream));
+  }
+  return AAO_OK;
+}
+
+// out = P(m) v with P(m) = sum_{k<=m} (P_eps^{-1} S_eps)^k P_eps^{-1}, m = opts.poly_m, the polynomial
+// preconditioner of Sec. 3.1 (the remark after Thm 3.1), by Horner's rule z <- P_eps^{-1} (v + S_eps z);
+// S_eps = (C_eps - C) (x) I touches only time rows 0 and 1.  m = 0: out = P_eps^{-1} v.
+aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind, bool v_ff = false) {
+  TRY(precond_once(p, v, out, out_kind, v_ff));
+  for (int k = 0; k < p->opts.poly_m; ++k) {
+    LAUNCH(ST_VEC, 1, aao::launch_poly_rhs(p->polyw, v, v_ff, out, out_kind == 0, p->ht.eps, p->Msp, p->Nt,
+                                           p->stream));
+    TRY(precond_once(p, p->polyw, out, out_kind, false));
   }
   return AAO_OK;
 }
@@ -721,8 +789,9 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
       return fail(nullptr, AAO_EINVAL, "2D: M and My must be in [1, 2047]");
     if (((prob->M + 1) & prob->M) || ((prob->My + 1) & prob->My))
       return fail(nullptr, AAO_EINVAL, "2D: M+1 and My+1 must be powers of two");
-    if (o->inner != AAO_INNER_TAU)
-      return fail(nullptr, AAO_EINVAL, "2D: the inner preconditioner must be AAO_INNER_TAU (2D tau matrix)");
+    if (o->inner != AAO_INNER_TAU && o->inner != AAO_INNER_TAU_DIRECT)
+      return fail(nullptr, AAO_EINVAL,
+                  "2D: the inner preconditioner must be AAO_INNER_TAU or AAO_INNER_TAU_DIRECT (2D tau matrix)");
   }
   if (prob->Nt < 4 || prob->Nt > 65536 || (prob->Nt & (prob->Nt - 1)))
     return fail(nullptr, AAO_EINVAL, "Nt must be a power of two in [4, 65536]");
@@ -742,9 +811,11 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(nullptr, AAO_EINVAL, "tolerances must be > 0");
   if (o->inner_maxit < 1) return fail(nullptr, AAO_EINVAL, "inner_maxit must be >= 1");
   if (o->prec != AAO_PREC_FP64 && o->prec != AAO_PREC_MIXED) return fail(nullptr, AAO_EINVAL, "bad precision");
-  if (o->inner != AAO_INNER_STRANG && o->inner != AAO_INNER_TAU) return fail(nullptr, AAO_EINVAL, "bad inner");
-  if (o->inner == AAO_INNER_TAU && ((prob->M + 1) & prob->M))
+  if (o->inner != AAO_INNER_STRANG && o->inner != AAO_INNER_TAU && o->inner != AAO_INNER_TAU_DIRECT)
+    return fail(nullptr, AAO_EINVAL, "bad inner");
+  if (o->inner != AAO_INNER_STRANG && ((prob->M + 1) & prob->M))
     return fail(nullptr, AAO_EINVAL, "the tau preconditioner needs M+1 to be a power of two");
+  if (o->poly_m < 0 || o->poly_m > 16) return fail(nullptr, AAO_EINVAL, "poly_m must be in [0, 16]");
   if (o->use_graphs != 0 && o->use_graphs != 1) return fail(nullptr, AAO_EINVAL, "use_graphs must be 0 or 1");
   if (o->matvec != AAO_MATVEC_FFT64 && o->matvec != AAO_MATVEC_NTT) return fail(nullptr, AAO_EINVAL, "bad matvec");
   if (o->cocg_threads != 0 && o->cocg_threads != 64 && o->cocg_threads != 128 && o->cocg_threads != 256 &&
@@ -834,6 +905,7 @@ void aao_default_opts(aao_opts* o, aao_precision prec) {
   o->use_graphs = 1;
   o->matvec = AAO_MATVEC_NTT;
   o->cocg_threads = 0;
+  o->poly_m = 0;
 }
 
 aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host) {
@@ -858,6 +930,9 @@ aao_status aao_plan_destroy(aao_plan* p) {
   release_cycle_graph(p);
   if (p->cap1) cudaStreamDestroy(p->cap1);
   if (p->cap2) cudaStreamDestroy(p->cap2);
+  if (p->c2d_exec) cudaGraphExecDestroy(p->c2d_exec);
+  if (p->cap3) cudaStreamDestroy(p->cap3);
+  if (p->c2d_cap) cudaStreamDestroy(p->c2d_cap);
   if (p->gd_host) cudaFreeHost(p->gd_host);
   for (void* q : p->allocs) cudaFree(q);
   if (p->pinned) cudaFreeHost(p->pinned);
@@ -875,6 +950,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   p->opts = *opts;
   p->stream = (cudaStream_t)cuda_stream;
   p->mixed = opts->prec == AAO_PREC_MIXED;
+  p->direct = opts->inner == AAO_INNER_TAU_DIRECT;
   const char* emsg = nullptr;
   const double eps = prob->eps > 0 ? prob->eps : aao::default_eps(prob->T / (double)prob->Nt, p->mixed);
   if (!aao::build_tables(prob->M, prob->Nt, prob->T, prob->alpha, prob->kappa, eps, p->ht, &emsg)) {
@@ -985,6 +1061,14 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     const int np = aao::cocg2d_max_partials(p->M, p->My, p->logL, p->logLy, (int)csz);
     TRYP(dalloc(p, &p->part2d, (size_t)p->nsys * np));
     TRYP(dalloc(p, &p->active2d, 1));
+    TRYP(dalloc(p, &p->c2d_it, 1));
+    TRYP(dalloc(p, &p->c2d_loops, 1));
+    if (cudaMemset(p->c2d_loops, 0, sizeof(long long)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->c2d_cap, cudaStreamNonBlocking) != cudaSuccess) {
+      p->err = "2D COCG graph setup failed";
+      return bail(AAO_ECUDA);
+    }
     p->nsq = aao::mv2d_partials(p->M, p->Nt, p->logLy);
   }
   int dev = 0, sms = 0;
@@ -1030,7 +1114,8 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
       return bail(AAO_ECUDA);
     }
   }
-  if (p->mixed && p->dim == 1 && aao::cocg_reg_min_threads(p->M) > 0) {
+  if (opts->poly_m > 0) TRYP(dalloc(p, &p->polyw, p->n));
+  if (p->mixed && p->dim == 1 && !p->direct && aao::cocg_reg_min_threads(p->M) > 0) {
     if (opts->cocg_threads)
       p->cocg_threads = opts->cocg_threads;
     else
@@ -1064,6 +1149,12 @@ aao_status aao_plan_get_profile(aao_plan* p, double* ms, int64_t* launches, int 
     p->ev_pool.push_back(pr.second.second);
   }
   p->ev_pending.clear();
+  if (p->c2d_loops) {  // graph-driven 2D COCG iterations: 10 kernels each
+    long long loops = 0;
+    CK(cudaMemcpy(&loops, p->c2d_loops, sizeof loops, cudaMemcpyDeviceToHost));
+    p->prof_launches[ST_COCG] += 10 * (loops - p->c2d_loops_seen);
+    p->c2d_loops_seen = loops;
+  }
   for (int i = 0; i < AAO_NUM_STAGES; ++i) {
     if (ms) ms[i] = p->prof_ms[i];
     if (launches) launches[i] = p->prof_launches[i];
@@ -1079,8 +1170,8 @@ aao_status aao_plan_set_warm_start(aao_plan* p, aao_fno* fno) {
     p->fno = nullptr;
     return AAO_OK;
   }
-  if (p->dim != 1 || !p->mixed || p->M > 8191)
-    return fail(p, AAO_EINVAL, "the warm start needs a 1D AAO_PREC_MIXED plan");
+  if (p->dim != 1 || !p->mixed || p->M > 8191 || p->direct)
+    return fail(p, AAO_EINVAL, "the warm start needs a 1D AAO_PREC_MIXED plan with an iterative Step (b)");
   if (aao::fno_grid_size(fno) != p->M || aao::fno_max_batch(fno) < p->nsys)
     return fail(p, AAO_EINVAL, "the model's M must equal the plan's and its max_batch must be >= Nt/2 + 1");
   if (!p->x0buf) {
@@ -1156,7 +1247,7 @@ aao_status aao_gmres_solve(aao_plan* p, const double* F, double* U, aao_info* in
     if (info) *info = inf;
     return AAO_OK;
   }
-  if (p->opts.use_graphs && p->dim == 1 && !p->prof_on && p->rec_cap <= p->rec_count)
+  if (p->opts.use_graphs && !p->prof_on && p->rec_cap <= p->rec_count)
     return gmres_solve_graph(p, F, U, info, nF, zero_guess);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
@@ -1263,6 +1354,157 @@ aao_status aao_gmres_solve_host(aao_plan* p, const double* F_host, double* U_hos
   CK(cudaMemcpyAsync(U_host, p->Uh, p->n * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   return st;
+}
+
+namespace {
+// Dot products of w with nv vectors V + i vstride, reduced on the device and read back to out (host).
+aao_status dots_to_host(aao_plan* p, const double* w, const double* V, size_t vstride, int nv, double* out) {
+  const int nb = aao::blas_partial_blocks();
+  LAUNCH(ST_VEC, 1, aao::launch_dots(w, V, vstride, nv, p->n, p->partial, p->stream));
+  return reduce_to_host(p, p->partial, nb, nv, out);
+}
+
+// COCG statistics of the last preconditioner application, accumulated into inf (synchronises).
+aao_status add_inner_stats(aao_plan* p, aao_info& inf) {
+  LAUNCH(ST_VEC, 1, (iter_stats_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->stats),
+                     cudaGetLastError()));
+  CK(cudaMemcpyAsync(p->pinned + 200, p->stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  int st[4];
+  std::memcpy(st, p->pinned + 200, sizeof st);
+  inf.inner_iters_max = std::max(inf.inner_iters_max, st[0]);
+  inf.inner_iters_sum += st[2];
+  inf.warm_accepted += st[3];
+  if (st[1] != 0 && inf.status_detail == 0)
+    inf.status_detail = st[1] == 1 ? AAO_ENOCONV : (st[1] == 2 ? AAO_EBREAKDOWN : AAO_ENONFINITE);
+  return AAO_OK;
+}
+}  // namespace
+
+aao_status aao_bicgstab_solve(aao_plan* p, const double* F, double* U, aao_info* info) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (!F || !U || F == U) return fail(p, AAO_EINVAL, "null or aliased pointers");
+  if (p->m < 7) return fail(p, AAO_EINVAL, "BiCGSTAB keeps 7 vectors in the Krylov workspace: restart must be >= 7");
+  const size_t n = p->n;
+  // FP64 views of the plan's Krylov workspace (V holds m + 1 >= 8 vectors of 8-byte elements)
+  double* r = p->V;             // residual F - calA U; r and rh adjacent for one dots call
+  double* rh = p->V + n;        // the shadow residual r0^
+  double* pv = p->V + 2 * n;
+  double* v = p->V + 3 * n;
+  double* sv = p->V + 4 * n;    // s and t adjacent
+  double* tv = p->V + 5 * n;
+  double* y = p->V + 6 * n;     // P^{-1} p, then P^{-1} s
+  aao_info inf{};
+  double h[2];
+  TRY(dots_to_host(p, F, F, 0, 1, h));
+  const double nF = std::sqrt(h[0]);
+  if (!std::isfinite(nF)) return fail(p, AAO_ENONFINITE, "non-finite right-hand side");
+  if (nF == 0.0) {
+    CK(cudaMemsetAsync(U, 0, n * sizeof(double), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (info) *info = inf;
+    return AAO_OK;
+  }
+  TRY(matvec_any(p, U, false, F, r, nullptr));  // r = F - calA U
+  inf.matvecs++;
+  CK(cudaMemcpyAsync(rh, r, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemsetAsync(pv, 0, n * sizeof(double), p->stream));
+  CK(cudaMemsetAsync(v, 0, n * sizeof(double), p->stream));
+  TRY(dots_to_host(p, r, r, 0, 1, h));
+  const double n0 = std::sqrt(h[0]);
+  aao_status result = AAO_ENOCONV;
+  if (!std::isfinite(n0)) { result = AAO_ENONFINITE; p->err = "non-finite residual"; }
+  const double thr = p->opts.tol * n0;
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  const long maxit = (long)p->opts.max_cycles * p->m;
+  if (n0 <= thr) result = AAO_OK;
+  for (long it = 0; result == AAO_ENOCONV && it < maxit; ++it) {
+    TRY(dots_to_host(p, r, r, n, 2, h));  // (r, r), (r, r0^)
+    const double rho_new = h[1];
+    if (!std::isfinite(rho_new)) { result = AAO_ENONFINITE; p->err = "non-finite BiCGSTAB scalar"; break; }
+    if (rho_new == 0.0 || omega == 0.0) { result = AAO_EBREAKDOWN; p->err = "BiCGSTAB breakdown (rho = 0)"; break; }
+    const double beta = (rho_new / rho) * (alpha / omega);
+    rho = rho_new;
+    LAUNCH(ST_VEC, 1, aao::launch_lincomb3(pv, 1.0, r, beta, pv, -beta * omega, v, n, p->stream));  // p = r + beta (p - omega v)
+    TRY(precond_any(p, pv, y, 1));  // y = P^{-1} p
+    TRY(add_inner_stats(p, inf));
+    TRY(matvec_any(p, y, false, nullptr, v, nullptr));  // v = calA y
+    inf.matvecs++;
+    inf.outer_iters++;
+    TRY(dots_to_host(p, v, rh, 0, 1, h));
+    if (h[0] == 0.0 || !std::isfinite(h[0])) {
+      result = std::isfinite(h[0]) ? AAO_EBREAKDOWN : AAO_ENONFINITE;
+      p->err = "BiCGSTAB breakdown ((r0^, v) = 0)";
+      break;
+    }
+    alpha = rho / h[0];
+    LAUNCH(ST_VEC, 1, aao::launch_lincomb3(U, 1.0, U, alpha, y, 0.0, nullptr, n, p->stream));   // U += alpha y
+    LAUNCH(ST_VEC, 1, aao::launch_lincomb3(sv, 1.0, r, -alpha, v, 0.0, nullptr, n, p->stream));  // s = r - alpha v
+    TRY(dots_to_host(p, sv, sv, 0, 1, h));
+    if (std::sqrt(h[0]) <= thr) { result = AAO_OK; break; }  // converged at the half step
+    TRY(precond_any(p, sv, y, 1));  // y = P^{-1} s
+    TRY(add_inner_stats(p, inf));
+    TRY(matvec_any(p, y, false, nullptr, tv, nullptr));  // t = calA y
+    inf.matvecs++;
+    inf.outer_iters++;
+    TRY(dots_to_host(p, tv, sv, n, 2, h));  // (t, s), (t, t)
+    if (!(h[1] > 0.0) || !std::isfinite(h[0])) {
+      result = std::isfinite(h[1]) ? AAO_EBREAKDOWN : AAO_ENONFINITE;
+      p->err = "BiCGSTAB breakdown ((t, t) = 0)";
+      break;
+    }
+    omega = h[0] / h[1];
+    LAUNCH(ST_VEC, 1, aao::launch_lincomb3(U, 1.0, U, omega, y, 0.0, nullptr, n, p->stream));    // U += omega y
+    LAUNCH(ST_VEC, 1, aao::launch_lincomb3(r, 1.0, sv, -omega, tv, 0.0, nullptr, n, p->stream));  // r = s - omega t
+    TRY(dots_to_host(p, r, r, 0, 1, h));
+    inf.cycles = (int)it + 1;
+    if (std::sqrt(h[0]) <= thr) result = AAO_OK;
+  }
+  // true relative residual in FP64
+  TRY(matvec_any(p, U, false, F, y, p->sq));
+  inf.matvecs++;
+  double rr = 0;
+  TRY(reduce_to_host(p, p->sq, (int)p->nsq, 1, &rr));
+  inf.true_rel_res = std::sqrt(rr) / nF;
+  if (info) *info = inf;
+  if (result == AAO_ENOCONV) p->err = "BiCGSTAB did not reach the tolerance within max_cycles * restart iterations";
+  return result;
+}
+
+aao_status aao_solve_windows(aao_plan* p, int n_windows, const double* u0, const double* f, double* U,
+                             aao_info* info) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (n_windows < 1 || !u0 || !f || !U || f == U) return fail(p, AAO_EINVAL, "bad windowed-solve arguments");
+  if (!p->Fh) {
+    TRY(dalloc(p, &p->Fh, p->n));
+    TRY(dalloc(p, &p->Uh, p->n));
+  }
+  aao_info tot{};
+  const size_t n = p->n;
+  for (int q = 0; q < n_windows; ++q) {
+    const double* start = q == 0 ? u0 : U + (size_t)q * n - p->Msp;  // last level of window q - 1
+    double* Uq = U + (size_t)q * n;
+    LAUNCH(ST_VEC, 1, aao::launch_build_rhs(start, f + (size_t)q * n, p->Fh, p->ht.tau, (int)p->Msp, p->Nt,
+                                            p->stream));
+    CK(cudaMemsetAsync(Uq, 0, n * sizeof(double), p->stream));
+    aao_info inf{};
+    const aao_status st = aao_gmres_solve(p, p->Fh, Uq, &inf);
+    tot.outer_iters += inf.outer_iters;
+    tot.cycles += inf.cycles;
+    tot.matvecs += inf.matvecs;
+    tot.inner_iters_max = std::max(tot.inner_iters_max, inf.inner_iters_max);
+    tot.inner_iters_sum += inf.inner_iters_sum;
+    tot.warm_accepted += inf.warm_accepted;
+    tot.true_rel_res = std::max(tot.true_rel_res, inf.true_rel_res);
+    if (inf.status_detail && !tot.status_detail) tot.status_detail = inf.status_detail;
+    if (st != AAO_OK) {
+      if (info) *info = tot;
+      p->err = "window " + std::to_string(q) + ": " + p->err;
+      return st;
+    }
+  }
+  if (info) *info = tot;
+  return AAO_OK;
 }
 
 }  // extern "C"

@@ -508,58 +508,152 @@ int cocg2d_max_partials(int Mx, int My, int logLx, int logLy, int csize) {
   return std::max(ne, std::max((My + Bx - 1) / Bx, (Mx + By - 1) / By));
 }
 
+// The kernels of the 2D COCG: the start (r = b, x = 0, z = P^{-1} r, rho) and one iteration (q = A p, alpha,
+// x and r updates, convergence check, z = P^{-1} r, beta and p).  Converged systems skip every kernel.
+template <typename R>
+struct Cocg2dRun {
+  using C = Cx<R>;
+  const Cocg2dArgs<R>& A;
+  int Mx, My, nsys, Bx, By, ne;
+  size_t Ms, smx, smy;
+  dim3 g_rows, g_cols, g_elem;
+  SysState* st;
+  R sx;
+
+  explicit Cocg2dRun(const Cocg2dArgs<R>& a) : A(a) {
+    Mx = A.Mx; My = A.My; nsys = A.nsys;
+    Ms = (size_t)Mx * My;
+    const int Lx = 1 << A.logLx, Ly = 1 << A.logLy;
+    Bx = lines_per_cta(Lx, (int)sizeof(C));
+    By = lines_per_cta(Ly, (int)sizeof(C));
+    smx = line_smem<R>(Lx, Bx);
+    smy = line_smem<R>(Ly, By);
+    st = reinterpret_cast<SysState*>(A.state);
+    g_rows = dim3((My + Bx - 1) / Bx, nsys);
+    g_cols = dim3((Mx + By - 1) / By, nsys);
+    ne = (int)std::min<size_t>((Ms + kElemThreads - 1) / kElemThreads, 64);
+    g_elem = dim3(ne, nsys);
+    sx = (R)(2.0 / (Mx + 1));
+  }
+  cudaError_t prepare() const {
+    cudaError_t e;
+    if ((e = allow_smem(c2d_rows_dst<R, 0>, smx)) != cudaSuccess) return e;
+    if ((e = allow_smem(c2d_rows_dst<R, 1>, smx)) != cudaSuccess) return e;
+    if ((e = allow_smem(c2d_rows_conv<R>, smx)) != cudaSuccess) return e;
+    if ((e = allow_smem(c2d_cols_dst_div<R>, smy)) != cudaSuccess) return e;
+    return allow_smem(c2d_cols_conv<R>, smy);
+  }
+  void precond(cudaStream_t s) const {
+    c2d_rows_dst<R, 0><<<g_rows, kLineThreads, smx, s>>>(A.Rr, A.Tm, nullptr, Mx, My, A.logLx, A.twx, (R)1, Bx, st,
+                                                         A.part);
+    c2d_cols_dst_div<R><<<g_cols, kLineThreads, smy, s>>>(A.Tm, A.Q, Mx, My, A.logLy, A.twy, A.sxn, A.syf, A.lambda,
+                                                          By, st);
+    c2d_rows_dst<R, 1><<<g_rows, kLineThreads, smx, s>>>(A.Q, A.Z, A.Rr, Mx, My, A.logLx, A.twx, sx, Bx, st, A.part);
+  }
+  void start(cudaStream_t s) const {  // 4 kernels + the preconditioner (3)
+    c2d_init<R><<<g_elem, kElemThreads, 0, s>>>(A.X, A.Rr, Ms, A.part);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_INIT, st, A.part, ne, A.tol, A.active_count, A.iters, A.flags);
+    precond(s);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_RHO0, st, A.part, g_rows.x, A.tol, A.active_count, A.iters, A.flags);
+  }
+  void iter_until_check(cudaStream_t s) const {  // 5 kernels
+    c2d_rows_conv<R><<<g_rows, kLineThreads, smx, s>>>(A.Z, A.P, A.Tm, Mx, My, A.logLx, A.twx, A.Exf, Bx, st);
+    c2d_cols_conv<R><<<g_cols, kLineThreads, smy, s>>>(A.P, A.Tm, A.Q, Mx, My, A.logLy, A.twy, A.Eyf, A.lambda, By,
+                                                       st, A.part);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_ALPHA, st, A.part, g_cols.x, A.tol, A.active_count, A.iters, A.flags);
+    c2d_update<R><<<g_elem, kElemThreads, 0, s>>>(A.X, A.Rr, A.P, A.Q, Ms, st, A.part);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_CHECK, st, A.part, ne, A.tol, A.active_count, A.iters, A.flags);
+  }
+  void iter_after_check(cudaStream_t s) const {  // 4 kernels
+    precond(s);
+    c2d_scalars<<<nsys, 256, 0, s>>>(S_BETA, st, A.part, g_rows.x, A.tol, A.active_count, A.iters, A.flags);
+  }
+};
+
+// Before the loop: counters to zero, and the loop runs if any system is still active.
+__global__ void c2d_loop_start(const SysState* __restrict__ st, int nsys, int* __restrict__ it_dev,
+                               int* __restrict__ active_count, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  for (int n = 0; n < nsys; ++n) any |= st[n].active;
+  *it_dev = 0;
+  *active_count = 0;
+  cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// End of one iteration: continue while some system was still active at its check and fewer than maxit
+// iterations have run; the count of systems still active is reset for the next check.
+__global__ void c2d_loop_next(int* __restrict__ it_dev, int* __restrict__ active_count, int maxit,
+                              long long* __restrict__ loops_total, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const int a = *active_count;
+  *active_count = 0;
+  const int it = ++*it_dev;
+  ++*loops_total;
+  cudaGraphSetConditional(h, (a > 0 && it < maxit) ? 1u : 0u);
+}
+
+// Host-driven loop (one host synchronisation per iteration); used while profiling each launch.
 template <typename R>
 static cudaError_t cocg2d(const Cocg2dArgs<R>& A, cudaStream_t s, int* inner_iters_out) {
-  using C = Cx<R>;
-  const int Mx = A.Mx, My = A.My, nsys = A.nsys;
-  const size_t Ms = (size_t)Mx * My;
-  const int Lx = 1 << A.logLx, Ly = 1 << A.logLy;
-  const int Bx = lines_per_cta(Lx, (int)sizeof(C)), By = lines_per_cta(Ly, (int)sizeof(C));
-  const size_t smx = line_smem<R>(Lx, Bx), smy = line_smem<R>(Ly, By);
-  SysState* st = reinterpret_cast<SysState*>(A.state);
-  cudaError_t e;
-  if ((e = allow_smem(c2d_rows_dst<R, 0>, smx)) != cudaSuccess) return e;
-  if ((e = allow_smem(c2d_rows_dst<R, 1>, smx)) != cudaSuccess) return e;
-  if ((e = allow_smem(c2d_rows_conv<R>, smx)) != cudaSuccess) return e;
-  if ((e = allow_smem(c2d_cols_dst_div<R>, smy)) != cudaSuccess) return e;
-  if ((e = allow_smem(c2d_cols_conv<R>, smy)) != cudaSuccess) return e;
-  const dim3 g_rows((My + Bx - 1) / Bx, nsys), g_cols((Mx + By - 1) / By, nsys);
-  const int ne = (int)std::min<size_t>((Ms + kElemThreads - 1) / kElemThreads, 64);
-  const dim3 g_elem(ne, nsys);
-  C *X = A.X, *Rr = A.Rr, *P = A.P, *Z = A.Z, *Q = A.Q, *Tm = A.Tm;
-  const R sx = (R)(2.0 / (Mx + 1));
-  auto precond = [&](bool with_rho) {
-    c2d_rows_dst<R, 0><<<g_rows, kLineThreads, smx, s>>>(Rr, Tm, nullptr, Mx, My, A.logLx, A.twx, (R)1, Bx, st,
-                                                         A.part);
-    c2d_cols_dst_div<R><<<g_cols, kLineThreads, smy, s>>>(Tm, Q, Mx, My, A.logLy, A.twy, A.sxn, A.syf, A.lambda, By,
-                                                          st);
-    if (with_rho)
-      c2d_rows_dst<R, 1><<<g_rows, kLineThreads, smx, s>>>(Q, Z, Rr, Mx, My, A.logLx, A.twx, sx, Bx, st, A.part);
-    else
-      c2d_rows_dst<R, 0><<<g_rows, kLineThreads, smx, s>>>(Q, Z, Rr, Mx, My, A.logLx, A.twx, sx, Bx, st, A.part);
-  };
-  c2d_init<R><<<g_elem, kElemThreads, 0, s>>>(X, Rr, Ms, A.part);
-  c2d_scalars<<<nsys, 256, 0, s>>>(S_INIT, st, A.part, ne, A.tol, A.active_count, A.iters, A.flags);
-  precond(true);
-  c2d_scalars<<<nsys, 256, 0, s>>>(S_RHO0, st, A.part, g_rows.x, A.tol, A.active_count, A.iters, A.flags);
+  Cocg2dRun<R> run(A);
+  cudaError_t e = run.prepare();
+  if (e != cudaSuccess) return e;
+  run.start(s);
   int it = 0;
   for (; it < A.maxit; ++it) {
-    c2d_rows_conv<R><<<g_rows, kLineThreads, smx, s>>>(Z, P, Tm, Mx, My, A.logLx, A.twx, A.Exf, Bx, st);
-    c2d_cols_conv<R><<<g_cols, kLineThreads, smy, s>>>(P, Tm, Q, Mx, My, A.logLy, A.twy, A.Eyf, A.lambda, By, st,
-                                                       A.part);
-    c2d_scalars<<<nsys, 256, 0, s>>>(S_ALPHA, st, A.part, g_cols.x, A.tol, A.active_count, A.iters, A.flags);
-    c2d_update<R><<<g_elem, kElemThreads, 0, s>>>(X, Rr, P, Q, Ms, st, A.part);
     if ((e = cudaMemsetAsync(A.active_count, 0, sizeof(int), s)) != cudaSuccess) return e;
-    c2d_scalars<<<nsys, 256, 0, s>>>(S_CHECK, st, A.part, ne, A.tol, A.active_count, A.iters, A.flags);
+    run.iter_until_check(s);
     if ((e = cudaMemcpyAsync(A.host_count, A.active_count, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     if (*A.host_count == 0) { ++it; break; }
-    precond(true);
-    c2d_scalars<<<nsys, 256, 0, s>>>(S_BETA, st, A.part, g_rows.x, A.tol, A.active_count, A.iters, A.flags);
+    run.iter_after_check(s);
   }
   if (inner_iters_out) *inner_iters_out = it;
   return cudaGetLastError();
+}
+
+// Records the whole 2D COCG into the graph that `s` is capturing: the start kernels, then a conditional
+// WHILE node whose body (captured on body_stream) is one iteration followed by c2d_loop_next, so that the
+// iterations run without any host synchronisation.
+template <typename R>
+static cudaError_t cocg2d_capture(const Cocg2dArgs<R>& A, cudaStream_t s, cudaStream_t body_stream) {
+  Cocg2dRun<R> run(A);
+  cudaError_t e = run.prepare();
+  if (e != cudaSuccess) return e;
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &g)) != cudaSuccess) return e;
+  if (cst != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureUnsupported;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+  run.start(s);
+  c2d_loop_start<<<1, 32, 0, s>>>(run.st, A.nsys, A.it_dev, A.active_count, h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+      cudaSuccess)
+    return e;
+  run.iter_until_check(body_stream);
+  run.iter_after_check(body_stream);
+  c2d_loop_next<<<1, 32, 0, body_stream>>>(A.it_dev, A.active_count, A.maxit, A.loops_total, h);
+  cudaError_t e2 = cudaGetLastError();
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(body_stream, &out);
+  return e2 != cudaSuccess ? e2 : e;
 }
 
 cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* launches) {
@@ -567,6 +661,12 @@ cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* l
 }
 cudaError_t launch_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, int* launches) {
   return cocg2d<double>(a, s, launches);
+}
+cudaError_t capture_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, cudaStream_t body_stream) {
+  return cocg2d_capture<float>(a, s, body_stream);
+}
+cudaError_t capture_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, cudaStream_t body_stream) {
+  return cocg2d_capture<double>(a, s, body_stream);
 }
 
 }  // namespace aao
