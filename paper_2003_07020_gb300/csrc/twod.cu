@@ -656,6 +656,37 @@ static cudaError_t cocg2d_capture(const Cocg2dArgs<R>& A, cudaStream_t s, cudaSt
   return e2 != cudaSuccess ? e2 : e;
 }
 
+// every system active, no iterations: the state the line kernels test before the direct solve
+__global__ void c2d_activate(SysState* __restrict__ st, int nsys, int* __restrict__ iters, int* __restrict__ flags) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nsys) return;
+  st[n].active = 1;
+  st[n].iters = 0;
+  st[n].flag = 0;
+  iters[n] = 0;
+  flags[n] = 0;
+}
+
+// X[n] <- (lambda_n I + c_x tau(T_x) (x) I + I (x) c_y tau(T_y))^{-1} X[n]: the 2D DST diagonalisation of
+// Example 2 (Eq. 4.5), i.e. the three line passes of the COCG preconditioner applied once to the rhs.
+template <typename R>
+static cudaError_t tau2d_direct(const Cocg2dArgs<R>& A, cudaStream_t s) {
+  Cocg2dRun<R> run(A);
+  cudaError_t e = run.prepare();
+  if (e != cudaSuccess) return e;
+  c2d_activate<<<(A.nsys + 255) / 256, 256, 0, s>>>(run.st, A.nsys, A.iters, A.flags);
+  c2d_rows_dst<R, 0><<<run.g_rows, kLineThreads, run.smx, s>>>(A.X, A.Tm, nullptr, A.Mx, A.My, A.logLx, A.twx, (R)1,
+                                                               run.Bx, run.st, A.part);
+  c2d_cols_dst_div<R><<<run.g_cols, kLineThreads, run.smy, s>>>(A.Tm, A.Q, A.Mx, A.My, A.logLy, A.twy, A.sxn, A.syf,
+                                                                A.lambda, run.By, run.st);
+  c2d_rows_dst<R, 0><<<run.g_rows, kLineThreads, run.smx, s>>>(A.Q, A.X, nullptr, A.Mx, A.My, A.logLx, A.twx, run.sx,
+                                                               run.Bx, run.st, A.part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tau2d_direct_f32(const Cocg2dArgs<float>& a, cudaStream_t s) { return tau2d_direct<float>(a, s); }
+cudaError_t launch_tau2d_direct_f64(const Cocg2dArgs<double>& a, cudaStream_t s) { return tau2d_direct<double>(a, s); }
+
 cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* launches) {
   return cocg2d<float>(a, s, launches);
 }
