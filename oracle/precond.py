@@ -285,6 +285,18 @@ def precond_apply_2d(Kx, Ky, tau, eps, V):
     return Z.real.reshape(V.shape)
 
 
+def strang2d_inverse(gx_scaled, gy_scaled, Mx, My, lam):
+    """The map r -> (lambda I + I (x) S_x + S_y (x) I)^{-1} r for the 2D Strang (BCCB) preconditioner of the
+    Kronecker-sum system (x fastest, r of shape (My, Mx)): S_x, S_y the Strang circulants of the scaled
+    Toeplitz matrices with first columns gx_scaled, gy_scaled (:func:`strang_symbol`).  A BCCB matrix is
+    diagonalised by the 2D DFT, so the solve divides the 2D DFT of r by lambda + eig_x[k] + eig_y[l] (library
+    FFT routine)."""
+    _, ex = strang_symbol(gx_scaled, Mx)
+    _, ey = strang_symbol(gy_scaled, My)
+    E = lam + ey[:, None] + ex[None, :]
+    return lambda r: np.fft.ifft2(np.fft.fft2(np.asarray(r, dtype=np.complex128)) / E)
+
+
 def P_eps_matvec_2d(Kx, Ky, tau, eps, Z):
     """P_eps z for the 2D system: row k is sum_j C_eps[k, j] Z[j] - tau (Z[k] Kx^T + Ky Z[k])."""
     Z = np.asarray(Z, dtype=np.float64)

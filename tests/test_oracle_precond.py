@@ -164,3 +164,21 @@ def test_P_eps_matvec_equals_the_assembled_preconditioner(M, Nt, eps):
     # and it inverts the three-step apply: P_eps (P_eps^{-1} v) = v
     z, _, _ = precond.precond_apply(K, tau, eps, Z)
     np.testing.assert_allclose(precond.P_eps_matvec(K, tau, eps, z), Z, rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("Mx,My", [(7, 5), (15, 15), (9, 4)])
+def test_strang2d_inverse_is_the_dense_circulant_sum_solve(Mx, My):
+    # the BCCB Strang preconditioner I (x) S_x + S_y (x) I, assembled densely from scipy's circulant matrices
+    gx = 40.0 * fcd.fcd_weights(1.3, Mx)
+    gy = 25.0 * fcd.fcd_weights(1.8, My)
+    lam = precond.eigenvalues_C_eps(16, 1 / 32)[3]
+    sx, _ = precond.strang_symbol(gx, Mx)
+    sy, _ = precond.strang_symbol(gy, My)
+    P = lam * np.eye(Mx * My) + np.kron(np.eye(My), sla.circulant(sx)) + np.kron(sla.circulant(sy), np.eye(Mx))
+    rng = np.random.default_rng(Mx * My)
+    r = rng.standard_normal((My, Mx)) + 1j * rng.standard_normal((My, Mx))
+    z = precond.strang2d_inverse(gx, gy, Mx, My, lam)(r)
+    np.testing.assert_allclose(z.ravel(), np.linalg.solve(P, r.ravel()), rtol=1e-12, atol=1e-12)
+    # and it keeps the central band of the 2D Toeplitz operator: for My = 1 it is the 1D Strang inverse
+    z1 = precond.strang2d_inverse(gx, np.array([0.0]), Mx, 1, lam)(r[:1])
+    np.testing.assert_allclose(z1.ravel(), precond.strang_inverse(gx, Mx, lam)(r[0]), rtol=1e-12, atol=1e-13)
