@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--inner", default="strang", choices=["strang", "tau"])
+    ap.add_argument("--inner", default=None, choices=["strang", "tau"],
+                    help="Step (b) preconditioner (default: strang in 1D, tau in 2D: the 2D Strang BCCB circulant "
+                         "needs up to 46 COCG iterations at 255 x 255 where the 2D tau matrix needs 7)")
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="COCG relative tolerance per shifted system (library default: 1e-6 mixed, 1e-12 fp64)")
     ap.add_argument("--matvec", default="ntt", choices=["fft64", "ntt"],
@@ -314,12 +316,16 @@ def matvec2d_flops(Mx, My, Nt):
     return Nt * (rows + cols + 7.0 * Mx * My)
 
 
-def cocg2d_flops(Mx, My, inner_iters_sum, n_apply, nsys):
+def cocg2d_flops(Mx, My, inner_iters_sum, n_apply, nsys, inner="tau"):
     """2D Step (b): per COCG iteration the Toeplitz product (My row and Mx column convolutions, 2 FFTs
-    each) and the tau preconditioner (a DST per row twice, two FFTs per column), ~50 flops per point of
+    each) and the preconditioner (tau: a DST per row twice, two FFTs per column; 2D Strang: a forward and
+    an inverse FFT per row, two FFTs for each of the Lx columns of the row spectra), ~50 flops per point of
     updates and dots; the preconditioner is also applied once per system before the first iteration."""
     Lx, Ly = 2 * (Mx + 1), 2 * (My + 1)
-    pre = 2 * My * fft_flops(Lx) + 2 * Mx * fft_flops(Ly)
+    if inner == "strang":
+        pre = 2 * My * fft_flops(Lx) + 2 * Lx * fft_flops(Ly)
+    else:
+        pre = 2 * My * fft_flops(Lx) + 2 * Mx * fft_flops(Ly)
     per_it = 2 * My * fft_flops(Lx) + 2 * Mx * fft_flops(Ly) + pre + 50.0 * Mx * My
     return inner_iters_sum * per_it + n_apply * nsys * pre
 
@@ -400,13 +406,13 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     M, Nt = args.M, args.Nt
     prec = aao.AAO_PREC_MIXED if args.prec == "mixed" else aao.AAO_PREC_FP64
+    if args.inner is None:
+        args.inner = "strang" if args.dim == 1 else "tau"
     inner = aao.AAO_INNER_STRANG if args.inner == "strang" else aao.AAO_INNER_TAU
     plans, Fs = [], []
     if args.dim == 2:
         M, My, Nt = 255, 255, 256
-        args.inner = "tau"
-        p = aao.Plan(M, Nt, ALPHAS_2D[0], My=My, alpha_y=ALPHAS_2D[1], kappa=1.0, T=1.0, prec=prec,
-                     inner=aao.AAO_INNER_TAU)
+        p = aao.Plan(M, Nt, ALPHAS_2D[0], My=My, alpha_y=ALPHAS_2D[1], kappa=1.0, T=1.0, prec=prec, inner=inner)
         for i in range(3):
             u0, f = workloads.make_inputs_2d(M, My, Nt, seed=1000 * rank + i)
             F = torch.empty((Nt, My, M), dtype=torch.float64, device=dev)
@@ -521,7 +527,7 @@ def run_ours(args):
         t_launch = prof["cocg"][0] / max(n_apply, 1)  # per preconditioner apply
         reg = args.dim == 1 and args.prec == "mixed" and M <= 8192  # register kernel, Strang spectra
         fl = (cocg_flops(M, args.inner, inner_sum, n_apply, nsys, strang_ffts=2 if reg else 4) if args.dim == 1
-              else cocg2d_flops(M, My, inner_sum, n_apply, nsys)) / max(n_apply, 1)
+              else cocg2d_flops(M, My, inner_sum, n_apply, nsys, args.inner)) / max(n_apply, 1)
         pkv = FP32_PEAK_TFLOPS if args.prec == "mixed" else FP64_PEAK_TFLOPS
         achieved = fl / (t_launch * 1e-3) / 1e12
         traffic = (COCG_DRAM_BYTES_PER_SYSTEM_M8191 * nsys
@@ -555,7 +561,8 @@ def run_ours(args):
                    "outer_iters": [i["outer_iters"] for i in infos],
                    "inner_iters_max": max(i["inner_iters_max"] for i in infos),
                    "true_rel_res_max": max(i["true_rel_res"] for i in infos),
-                   "fgmres_cycles": "CUDA graph per restart cycle" if args.dim == 1 else "host-driven steps",
+                   "fgmres_cycles": "CUDA graph per restart cycle" + ("" if args.dim == 1 else
+                                                                       ", COCG iterations as a WHILE node"),
                    "cocg_threads": plans[0].cocg_threads,
                    "stage_ms_profiled_pass": {k: round(v[0], 3) for k, v in prof.items()},
                    "stage_launches_profiled_pass": {k: v[1] for k, v in prof.items()}},

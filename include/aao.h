@@ -80,7 +80,11 @@ typedef enum {
  * 1D: unknowns per time level M, vectors double[Nt][M].
  * 2D: K = I (x) K_x + K_y (x) I with x fastest, unknowns per time level
  *     M * My, vectors double[Nt][My][M]; M + 1 and My + 1 must be powers of
- *     two (the 2D inner preconditioner is the tau matrix, applied by DSTs).
+ *     two.  Inner preconditioners in 2D: AAO_INNER_STRANG, the 2D Strang
+ *     (BCCB) circulant I (x) S_x + S_y (x) I (2D FFTs of the embedding, with
+ *     per-system spectra of the BCCB inverses built at plan creation: about
+ *     (Nt/2+1) (2 M + 2) (2 My + 2 + My) complex of workspace); AAO_INNER_TAU,
+ *     the 2D tau matrix by DSTs; AAO_INNER_TAU_DIRECT (no COCG).
  */
 typedef struct {
   int dim;              /* 1 or 2 */

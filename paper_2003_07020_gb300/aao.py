@@ -160,8 +160,6 @@ class Plan:
         self.problem = AaoProblem(dim, self.M, self.Nt, float(T), float(alpha), float(kappa), float(eps),
                                   self.My if dim == 2 else 0, float(alpha if alpha_y is None else alpha_y),
                                   float(kappa if kappa_y is None else kappa_y))
-        if dim == 2 and "inner" not in opt_kw and opts is None:
-            opt_kw["inner"] = AAO_INNER_TAU
         self.opts = opts if opts is not None else default_opts(**opt_kw)
         self._stream = stream
         h = ctypes.c_void_p()

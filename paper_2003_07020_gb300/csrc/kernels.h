@@ -172,8 +172,18 @@ template <typename R> struct Cocg2dArgs {
   int maxit;
   int* it_dev;                 // device int: iterations of the current graph-driven loop
   long long* loops_total;      // device counter of graph-driven iterations (launch accounting)
+  C* W2;                       // 2D Strang: [nsys][My][Lx] row spectra (null: the tau preconditioner)
+  const C* G2;                 // 2D Strang: [nsys][Lx][Ly] spectra of the BCCB inverses (fused y order, / (Lx Ly))
 };
 size_t cocg2d_state_bytes(int nsys);
+// The 2D Strang spectra G[n][p][f] = sum_{l,k} Qy[f][l] Qx[p][k] / (lambda_n + sy[l] + sx[k]) (Bt: nsys My Lx
+// complex scratch); Qx: [Lx][Mx], Qy: [Ly][My] (host-built, see build_strang2d_q).
+cudaError_t launch_strang2d_setup_f32(const float2* Qx, const float2* Qy, const float* sx, const float* sy,
+                                      const double2* lambda, int Mx, int My, int logLx, int logLy, int nsys,
+                                      float2* Bt, float2* G, cudaStream_t s);
+cudaError_t launch_strang2d_setup_f64(const double2* Qx, const double2* Qy, const double* sx, const double* sy,
+                                      const double2* lambda, int Mx, int My, int logLx, int logLy, int nsys,
+                                      double2* Bt, double2* G, cudaStream_t s);
 int cocg2d_max_partials(int Mx, int My, int logLx, int logLy, int csize);
 cudaError_t launch_cocg2d_f32(const Cocg2dArgs<float>& a, cudaStream_t s, int* iters_run);
 cudaError_t launch_cocg2d_f64(const Cocg2dArgs<double>& a, cudaStream_t s, int* iters_run);

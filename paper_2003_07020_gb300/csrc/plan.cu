@@ -193,6 +193,10 @@ struct aao_plan {
   double2* part2d = nullptr;
   int* active2d = nullptr;
   int* host_count = nullptr;
+  // 2D Strang (BCCB) preconditioner: row spectra scratch [nsys][My][Lx] and the per-system spectra of
+  // the BCCB inverses [nsys][Lx][Ly], complex in the plan's Step (b) precision
+  void* W2d = nullptr;
+  void* G2d = nullptr;
   // 2D COCG as a graph with a conditional WHILE loop (no host synchronisation per iteration)
   cudaStream_t cap3 = nullptr, c2d_cap = nullptr;
   cudaGraphExec_t c2d_exec = nullptr;
@@ -440,6 +444,8 @@ aao_status cocg2d_any(aao_plan* p, void* spec) {
   a.maxit = p->opts.inner_maxit;
   a.it_dev = p->c2d_it;
   a.loops_total = p->c2d_loops;
+  a.W2 = (C*)p->W2d;
+  a.G2 = (const C*)p->G2d;
   if (p->direct) {
     prof_begin(p);
     cudaError_t e = sizeof(R) == 4 ? aao::launch_tau2d_direct_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream)
@@ -789,9 +795,7 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
       return fail(nullptr, AAO_EINVAL, "2D: M and My must be in [1, 2047]");
     if (((prob->M + 1) & prob->M) || ((prob->My + 1) & prob->My))
       return fail(nullptr, AAO_EINVAL, "2D: M+1 and My+1 must be powers of two");
-    if (o->inner != AAO_INNER_TAU && o->inner != AAO_INNER_TAU_DIRECT)
-      return fail(nullptr, AAO_EINVAL,
-                  "2D: the inner preconditioner must be AAO_INNER_TAU or AAO_INNER_TAU_DIRECT (2D tau matrix)");
+
   }
   if (prob->Nt < 4 || prob->Nt > 65536 || (prob->Nt & (prob->Nt - 1)))
     return fail(nullptr, AAO_EINVAL, "Nt must be a power of two in [4, 65536]");
@@ -1070,6 +1074,40 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
       return bail(AAO_ECUDA);
     }
     p->nsq = aao::mv2d_partials(p->M, p->Nt, p->logLy);
+    if (opts->inner == AAO_INNER_STRANG) {
+      // 2D Strang (BCCB): per-direction spectral maps on the host, the per-system spectra on the device
+      std::vector<aao::cd> qx, qy;
+      aao::build_strang2d_q(p->M, p->logL, false, qx);
+      aao::build_strang2d_q(p->My, p->logLy, true, qy);
+      const size_t Lx = (size_t)1 << p->logL, Ly = (size_t)1 << p->logLy;
+      TRYP(dalloc(p, &q, (size_t)p->nsys * p->My * Lx * csz)); p->W2d = q;
+      TRYP(dalloc(p, &q, (size_t)p->nsys * Lx * Ly * csz)); p->G2d = q;
+      cudaError_t e;
+      if (p->mixed) {
+        float2 *Qx, *Qy;
+        float *sx, *sy;
+        TRYP(upload_c(p, &Qx, qx));
+        TRYP(upload_c(p, &Qy, qy));
+        TRYP(upload(p, &sx, t.strang_eig));
+        TRYP(upload(p, &sy, ty.strang_eig));
+        e = aao::launch_strang2d_setup_f32(Qx, Qy, sx, sy, p->lambda, p->M, p->My, p->logL, p->logLy, p->nsys,
+                                           (float2*)p->W2d, (float2*)p->G2d, p->stream);
+      } else {
+        double2 *Qx, *Qy;
+        double *sx, *sy;
+        TRYP(upload_c(p, &Qx, qx));
+        TRYP(upload_c(p, &Qy, qy));
+        TRYP(upload(p, &sx, t.strang_eig));
+        TRYP(upload(p, &sy, ty.strang_eig));
+        e = aao::launch_strang2d_setup_f64(Qx, Qy, sx, sy, p->lambda, p->M, p->My, p->logL, p->logLy, p->nsys,
+                                           (double2*)p->W2d, (double2*)p->G2d, p->stream);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+      if (e != cudaSuccess) {
+        p->err = std::string("2D Strang spectra: ") + cudaGetErrorString(e);
+        return bail(AAO_ECUDA);
+      }
+    }
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -80,6 +80,34 @@ int64_t fused_to_freq(int64_t p, int logN) {
   return bitrev64(pos, logN);
 }
 
+void build_strang2d_q(int64_t M, int logL, bool fused_order, std::vector<cd>& Q) {
+  const int64_t L = int64_t(1) << logL, ML = M * L;
+  Q.assign((size_t)(L * M), cd(0, 0));
+  for (int64_t row = 0; row < L; ++row) {
+    const int64_t K = fused_order ? fused_to_freq(row, logL) : bitrev64(row, logL);
+    // phase of the wrapped copy: exp(-2 pi i K (L - M) / L)
+    const cd ph = unit_root(K * (L - M), L, -1);
+    int64_t r2 = (-K * M) % L;  // z^M = exp(2 pi i r2 / L)
+    if (r2 < 0) r2 += L;
+    if (2 * r2 > L) r2 -= L;
+    const double phi = 2.0 * kPi * (double)r2 / (double)L;
+    for (int64_t k = 0; k < M; ++k) {
+      // S = sum_{j<M} z^j, z = exp(2 pi i (kL - KM) / (ML)), by the half-angle form of (1 - z^M) / (1 - z)
+      int64_t r1 = (k * L - K * M) % ML;
+      if (r1 < 0) r1 += ML;
+      if (2 * r1 > ML) r1 -= ML;
+      cd S;
+      if (r1 == 0) {
+        S = cd((double)M, 0.0);
+      } else {
+        const double th = 2.0 * kPi * (double)r1 / (double)ML;
+        S = std::polar(std::sin(0.5 * phi) / std::sin(0.5 * th), 0.5 * (phi - th));
+      }
+      Q[(size_t)(row * M + k)] = (S + ph * (S - 1.0)) / (double)ML;
+    }
+  }
+}
+
 bool build_tables(int64_t M, int64_t Nt, double T, double alpha, double kappa, double eps,
                   HostTables& t, const char** err) {
   if (M < 1) { *err = "M must be >= 1"; return false; }

@@ -60,6 +60,14 @@ void build_ntt_tables(HostTables& t);
 // r = min(4, logN).  Returns the natural frequency for fused index p.
 int64_t fused_to_freq(int64_t p, int logN);
 
+// The 2D Strang preconditioner's per-direction map from the reciprocal eigenvalues of an M-point
+// circulant to the spectrum of its kernel wrapped into L = 2^logL points (L >= 2M - 1):
+//   Q[K][k] = (1/(L M)) sum_{j<M} A[K][j] exp(+2 pi i j k / M),
+//   A[K][j] = exp(-2 pi i K j / L) + [j >= 1] exp(-2 pi i K (L - M + j) / L),
+// the sum over j in closed form (a geometric series).  Row r of Q (r < L, M entries each) is frequency
+// K = bitrev(r) (the order of a DIF transform's output) or, if fused_order, K = fused_to_freq(r).
+void build_strang2d_q(int64_t M, int logL, bool fused_order, std::vector<cd>& Q);
+
 // Default circulant parameter when the caller passes eps <= 0: the paper's
 // min(0.5, 0.5 tau) (Sec. 4) for the FP64 path; for the mixed path at least
 // 1/16, which bounds cond(V_eps) = 1/eps, the factor by which Step (c)

@@ -10,7 +10,9 @@
 //    circulant-embedding convolutions; two real lines share one complex
 //    transform (the embedding spectrum is real and even); the BDF band of
 //    Eq. 1.7 is added in the column pass.
-//  * Step (b): preconditioned COCG on all systems at once, with the 2D tau
+//  * Step (b): preconditioned COCG on all systems at once, with either the 2D
+//    Strang (BCCB) circulant I (x) c_x S_x + c_y S_y (x) I (precomputed 2D
+//    spectra, FFTs of the embedding) or the 2D tau
 //    matrix tau(T_x) (x) I + I (x) tau(T_y) (Sec. 4, Ex. 2) as preconditioner:
 //    P^{-1} = (2/(Mx+1)) S_x [ (2/(My+1)) S_y D S_y ] S_x with the DST-I
 //    matrices S and D = 1/(lambda_n + c_x sigma^x_i + c_y sigma^y_j).
@@ -392,6 +394,214 @@ __global__ void __launch_bounds__(kElemThreads) c2d_update(Cx<R>* __restrict__ X
   write_partial<R>(s, 0, part, n, gridDim.x, red);
 }
 
+// ---- 2D Strang (BCCB) preconditioner (lambda_n I + I (x) c_x S_x + c_y S_y (x) I)^{-1} ------------------
+// A BCCB inverse is a 2D cyclic convolution of period (Mx, My) with its first column h_n; it equals the
+// first Mx x My outputs of a (Lx, Ly)-periodic convolution with the wrapped kernel (Lx >= 2 Mx - 1), done as
+// a forward FFT along x of every zero-padded row, then per x-frequency a convolution along y with the
+// precomputed spectrum G_n (fused order, 1/(Lx Ly) folded in), then an inverse FFT along x.
+
+// W[n][j][p] = forward DIF FFT along x of the zero-padded row j of X[n] (position p holds frequency bitrev(p))
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) c2d_rows_fft_fwd(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ W,
+                                                                 int Mx, int My, int logLx,
+                                                                 const Cx<R>* __restrict__ twx, int B,
+                                                                 const SysState* __restrict__ st) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  const int n = blockIdx.y;
+  if (st && !st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Lx = 1 << logLx, bs = padded_size(Lx);
+  C* q = buf + B * bs;
+  load_quarter(q, twx, Lx / 4);
+  const size_t slab = (size_t)n * Mx * My;
+  const int j0 = blockIdx.x * B;
+  for (int base = threadIdx.x; base < B * Lx; base += kLU * blockDim.x) {
+    C y[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int b = idx / Lx, i = idx - b * Lx, j = j0 + b;
+      y[u] = (idx < B * Lx && j < My && i < Mx) ? in[slab + (size_t)j * Mx + i] : C{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= B * Lx) break;
+      const int b = idx / Lx, i = idx - b * Lx;
+      buf[b * bs + pad16(i)] = y[u];
+    }
+  }
+  fft_forward(buf, logLx, B, bs, q, logLx);
+  const size_t wslab = (size_t)n * My * Lx;
+  for (int idx = threadIdx.x; idx < B * Lx; idx += blockDim.x) {
+    const int b = idx / Lx, p = idx - b * Lx, j = j0 + b;
+    if (j < My) W[wslab + (size_t)j * Lx + p] = buf[b * bs + pad16(p)];
+  }
+}
+
+// Along y for every x-position p: W[n][:][p] <- first My outputs of the Ly-periodic convolution of the
+// zero-padded column with the spectrum G[n][p][:] (fused order)
+template <typename R>
+__global__ void __launch_bounds__(kLineThreads) c2d_cols_conv_g(Cx<R>* __restrict__ W, int Lx, int My, int logLy,
+                                                                const Cx<R>* __restrict__ twy,
+                                                                const Cx<R>* __restrict__ G, int B,
+                                                                const SysState* __restrict__ st) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  const int n = blockIdx.y;
+  if (st && !st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Ly = 1 << logLy, bs = padded_size(Ly);
+  C* q = buf + B * bs;
+  load_quarter(q, twy, Ly / 4);
+  const size_t wslab = (size_t)n * My * Lx;
+  const int p0 = blockIdx.x * B;
+  for (int base = threadIdx.x; base < Ly * B; base += kLU * blockDim.x) {
+    C y[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int j = idx / B, b = idx - j * B, p = p0 + b;
+      y[u] = (idx < Ly * B && j < My && p < Lx) ? W[wslab + (size_t)j * Lx + p] : C{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= Ly * B) break;
+      const int j = idx / B, b = idx - j * B;
+      buf[b * bs + pad16(j)] = y[u];
+    }
+  }
+  const C* Gn = G + (size_t)n * Lx * Ly;
+  fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int b, int pf) {
+    const int p = p0 + b;
+    return p < Lx ? Gn[(size_t)p * Ly + pf] : C{0, 0};
+  });
+  for (int idx = threadIdx.x; idx < My * B; idx += blockDim.x) {
+    const int j = idx / B, b = idx - j * B, p = p0 + b;
+    if (p < Lx) W[wslab + (size_t)j * Lx + p] = buf[b * bs + pad16(j)];
+  }
+}
+
+// out[n][j][i] = inverse DIT FFT along x of W[n][j][:] (bit-reversed in), first Mx outputs; MODE 1 also
+// accumulates the bilinear partial sum_e r_e out_e (rho of COCG)
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kLineThreads) c2d_rows_fft_inv(const Cx<R>* __restrict__ W, Cx<R>* __restrict__ out,
+                                                                 const Cx<R>* __restrict__ rr, int Mx, int My,
+                                                                 int logLx, const Cx<R>* __restrict__ twx, int B,
+                                                                 const SysState* __restrict__ st,
+                                                                 double2* __restrict__ part) {
+  using C = Cx<R>;
+  extern __shared__ unsigned char smraw[];
+  __shared__ R red[64];
+  const int n = blockIdx.y;
+  if (!st[n].active) return;
+  C* buf = reinterpret_cast<C*>(smraw);
+  const int Lx = 1 << logLx, bs = padded_size(Lx);
+  C* q = buf + B * bs;
+  load_quarter(q, twx, Lx / 4);
+  const size_t wslab = (size_t)n * My * Lx, slab = (size_t)n * Mx * My;
+  const int j0 = blockIdx.x * B;
+  for (int base = threadIdx.x; base < B * Lx; base += kLU * blockDim.x) {
+    C y[kLU];
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int b = idx / Lx, p = idx - b * Lx, j = j0 + b;
+      y[u] = (idx < B * Lx && j < My) ? W[wslab + (size_t)j * Lx + p] : C{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < kLU; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= B * Lx) break;
+      const int b = idx / Lx, p = idx - b * Lx;
+      buf[b * bs + pad16(p)] = y[u];
+    }
+  }
+  fft_backward(buf, logLx, B, bs, q, logLx);
+  R sre = 0, sim = 0;
+  for (int idx = threadIdx.x; idx < B * Mx; idx += blockDim.x) {
+    const int b = idx / Mx, i = idx - b * Mx, j = j0 + b;
+    if (j >= My) continue;
+    const C z = buf[b * bs + pad16(i)];
+    const size_t e = slab + (size_t)j * Mx + i;
+    out[e] = z;
+    if (MODE == 1) {
+      const C r = rr[e];
+      sre += r.x * z.x - r.y * z.y;
+      sim += r.x * z.y + r.y * z.x;
+    }
+  }
+  if (MODE == 1) write_partial<R>(sre, sim, part, n, gridDim.x, red);
+}
+
+// Spectra of the 2D Strang inverses, G[n][p][pf] = sum_{l,k} Qy[pf][l] Qx[p][k] / (lambda_n + sy[l] + sx[k]),
+// in two tiled complex products: Bt[n][l][p] = sum_k Qx[p][k] / E_n[l][k] (pass 1), then
+// G[n][p][pf] = sum_l Qy[pf][l] Bt[n][l][p] (pass 2).  Q* carry the wrap of the kernel, the DFT sizes and
+// the orders the apply kernels read; computed in the plan's precision.
+constexpr int kGT = 16;
+template <typename R>
+__global__ void __launch_bounds__(kGT * kGT) strang2d_spec_pass1(const Cx<R>* __restrict__ Qx, const R* __restrict__ sx,
+                                                                 const R* __restrict__ sy,
+                                                                 const double2* __restrict__ lambda, int Mx, int My,
+                                                                 int Lx, Cx<R>* __restrict__ Bt) {
+  using C = Cx<R>;
+  __shared__ C sa[kGT][kGT + 1], sb[kGT][kGT + 1];
+  const int n = blockIdx.z;
+  const int l = blockIdx.y * kGT + threadIdx.y;   // row of Bt
+  const int p = blockIdx.x * kGT + threadIdx.x;   // column of Bt
+  const C lam{(R)lambda[n].x, (R)lambda[n].y};
+  C acc{0, 0};
+  for (int k0 = 0; k0 < Mx; k0 += kGT) {
+    {  // sa[ty][tx] = 1 / E[l][k0 + tx]
+      const int k = k0 + threadIdx.x;
+      C v{0, 0};
+      if (l < My && k < Mx) {
+        const C d{lam.x + sy[l] + sx[k], lam.y};
+        const R den = d.x * d.x + d.y * d.y;
+        v = C{d.x / den, -d.y / den};
+      }
+      sa[threadIdx.y][threadIdx.x] = v;
+    }
+    {  // sb[ty][tx] = Qx[p' = blockIdx.x kGT + tx][k0 + ty]
+      const int k = k0 + threadIdx.y, pp = blockIdx.x * kGT + threadIdx.x;
+      sb[threadIdx.y][threadIdx.x] = (pp < Lx && k < Mx) ? Qx[(size_t)pp * Mx + k] : C{0, 0};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kGT; ++t) acc = cadd(acc, cmul(sa[threadIdx.y][t], sb[t][threadIdx.x]));
+    __syncthreads();
+  }
+  if (l < My && p < Lx) Bt[((size_t)n * My + l) * Lx + p] = acc;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kGT * kGT) strang2d_spec_pass2(const Cx<R>* __restrict__ Qy, const Cx<R>* __restrict__ Bt,
+                                                                 int My, int Lx, int Ly, Cx<R>* __restrict__ G) {
+  using C = Cx<R>;
+  __shared__ C sa[kGT][kGT + 1], sb[kGT][kGT + 1];
+  const int n = blockIdx.z;
+  const int p = blockIdx.y * kGT + threadIdx.y;   // row of G_n
+  const int f = blockIdx.x * kGT + threadIdx.x;   // column of G_n (fused y index)
+  C acc{0, 0};
+  for (int l0 = 0; l0 < My; l0 += kGT) {
+    {  // sa[ty][tx] = Bt[n][l0 + tx][p]
+      const int l = l0 + threadIdx.x;
+      sa[threadIdx.y][threadIdx.x] = (p < Lx && l < My) ? Bt[((size_t)n * My + l) * Lx + p] : C{0, 0};
+    }
+    {  // sb[ty][tx] = Qy[f' = blockIdx.x kGT + tx][l0 + ty]
+      const int l = l0 + threadIdx.y, ff = blockIdx.x * kGT + threadIdx.x;
+      sb[threadIdx.y][threadIdx.x] = (ff < Ly && l < My) ? Qy[(size_t)ff * My + l] : C{0, 0};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kGT; ++t) acc = cadd(acc, cmul(sa[threadIdx.y][t], sb[t][threadIdx.x]));
+    __syncthreads();
+  }
+  if (p < Lx && f < Ly) G[((size_t)n * Lx + p) * Ly + f] = acc;
+}
+
 enum { S_INIT = 0, S_RHO0 = 1, S_ALPHA = 2, S_CHECK = 3, S_BETA = 4 };
 
 // one block per system: reduce the partials of the last kernel and update the scalars
@@ -541,9 +751,21 @@ struct Cocg2dRun {
     if ((e = allow_smem(c2d_rows_dst<R, 1>, smx)) != cudaSuccess) return e;
     if ((e = allow_smem(c2d_rows_conv<R>, smx)) != cudaSuccess) return e;
     if ((e = allow_smem(c2d_cols_dst_div<R>, smy)) != cudaSuccess) return e;
+    if ((e = allow_smem(c2d_rows_fft_fwd<R>, smx)) != cudaSuccess) return e;
+    if ((e = allow_smem(c2d_rows_fft_inv<R, 1>, smx)) != cudaSuccess) return e;
+    if ((e = allow_smem(c2d_cols_conv_g<R>, smy)) != cudaSuccess) return e;
     return allow_smem(c2d_cols_conv<R>, smy);
   }
   void precond(cudaStream_t s) const {
+    if (A.G2) {  // 2D Strang (BCCB): Z = P_n^{-1} Rr through W2, and rho's partials
+      const int Lx = 1 << A.logLx;
+      const dim3 g_colsg((Lx + By - 1) / By, nsys);
+      c2d_rows_fft_fwd<R><<<g_rows, kLineThreads, smx, s>>>(A.Rr, A.W2, Mx, My, A.logLx, A.twx, Bx, st);
+      c2d_cols_conv_g<R><<<g_colsg, kLineThreads, smy, s>>>(A.W2, Lx, My, A.logLy, A.twy, A.G2, By, st);
+      c2d_rows_fft_inv<R, 1><<<g_rows, kLineThreads, smx, s>>>(A.W2, A.Z, A.Rr, Mx, My, A.logLx, A.twx, Bx, st,
+                                                               A.part);
+      return;
+    }
     c2d_rows_dst<R, 0><<<g_rows, kLineThreads, smx, s>>>(A.Rr, A.Tm, nullptr, Mx, My, A.logLx, A.twx, (R)1, Bx, st,
                                                          A.part);
     c2d_cols_dst_div<R><<<g_cols, kLineThreads, smy, s>>>(A.Tm, A.Q, Mx, My, A.logLy, A.twy, A.sxn, A.syf, A.lambda,
@@ -682,6 +904,28 @@ static cudaError_t tau2d_direct(const Cocg2dArgs<R>& A, cudaStream_t s) {
   c2d_rows_dst<R, 0><<<run.g_rows, kLineThreads, run.smx, s>>>(A.Q, A.X, nullptr, A.Mx, A.My, A.logLx, A.twx, run.sx,
                                                                run.Bx, run.st, A.part);
   return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t strang2d_setup(const Cx<R>* Qx, const Cx<R>* Qy, const R* sx, const R* sy, const double2* lambda,
+                                  int Mx, int My, int logLx, int logLy, int nsys, Cx<R>* Bt, Cx<R>* G,
+                                  cudaStream_t s) {
+  const int Lx = 1 << logLx, Ly = 1 << logLy;
+  const dim3 blk(kGT, kGT);
+  strang2d_spec_pass1<R><<<dim3((Lx + kGT - 1) / kGT, (My + kGT - 1) / kGT, nsys), blk, 0, s>>>(Qx, sx, sy, lambda, Mx,
+                                                                                               My, Lx, Bt);
+  strang2d_spec_pass2<R><<<dim3((Ly + kGT - 1) / kGT, (Lx + kGT - 1) / kGT, nsys), blk, 0, s>>>(Qy, Bt, My, Lx, Ly, G);
+  return cudaGetLastError();
+}
+cudaError_t launch_strang2d_setup_f32(const float2* Qx, const float2* Qy, const float* sx, const float* sy,
+                                      const double2* lambda, int Mx, int My, int logLx, int logLy, int nsys,
+                                      float2* Bt, float2* G, cudaStream_t s) {
+  return strang2d_setup<float>(Qx, Qy, sx, sy, lambda, Mx, My, logLx, logLy, nsys, Bt, G, s);
+}
+cudaError_t launch_strang2d_setup_f64(const double2* Qx, const double2* Qy, const double* sx, const double* sy,
+                                      const double2* lambda, int Mx, int My, int logLx, int logLy, int nsys,
+                                      double2* Bt, double2* G, cudaStream_t s) {
+  return strang2d_setup<double>(Qx, Qy, sx, sy, lambda, Mx, My, logLx, logLy, nsys, Bt, G, s);
 }
 
 cudaError_t launch_tau2d_direct_f32(const Cocg2dArgs<float>& a, cudaStream_t s) { return tau2d_direct<float>(a, s); }

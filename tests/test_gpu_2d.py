@@ -52,12 +52,16 @@ def test_matvec_2d(Mx, My, Nt, ax, ay):
     assert rel(host(w), oaao.matvec_2d(Kx, Ky, 1.0 / Nt, v)) <= 1e-13
 
 
+INNERS = [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU]
+
+
 @pytest.mark.parametrize("Mx,My,Nt,ax,ay", CASES[:3])
-def test_precond_2d_fp64(Mx, My, Nt, ax, ay):
+@pytest.mark.parametrize("inner", INNERS)
+def test_precond_2d_fp64(Mx, My, Nt, ax, ay, inner):
     v = np.random.default_rng(3).standard_normal((Nt, My, Mx))
     tau = 1.0 / Nt
     eps = oprec.default_eps(tau)
-    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=aao.AAO_PREC_FP64) as plan:
+    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=aao.AAO_PREC_FP64, inner=inner) as plan:
         z = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
         plan.bc_precond_apply(cu(v), z)
         torch.cuda.synchronize()
@@ -68,11 +72,12 @@ def test_precond_2d_fp64(Mx, My, Nt, ax, ay):
 
 
 @pytest.mark.parametrize("Mx,My,Nt,ax,ay", CASES[:3])
-def test_precond_2d_mixed(Mx, My, Nt, ax, ay):
+@pytest.mark.parametrize("inner", INNERS)
+def test_precond_2d_mixed(Mx, My, Nt, ax, ay, inner):
     v = np.random.default_rng(4).standard_normal((Nt, My, Mx))
     tau = 1.0 / Nt
     eps = mixed_eps(tau)
-    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=aao.AAO_PREC_MIXED) as plan:
+    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=aao.AAO_PREC_MIXED, inner=inner) as plan:
         z = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
         plan.bc_precond_apply(cu(v), z)
         torch.cuda.synchronize()
@@ -83,10 +88,12 @@ def test_precond_2d_mixed(Mx, My, Nt, ax, ay):
 
 @pytest.mark.parametrize("prec,bound", [(aao.AAO_PREC_FP64, 1e-10), (aao.AAO_PREC_MIXED, 1e-9)])
 @pytest.mark.parametrize("Mx,My,Nt,ax,ay", [(31, 15, 16, 1.3, 1.7), (63, 63, 32, 1.5, 1.2)])
-def test_gmres_2d_matches_time_stepping(Mx, My, Nt, ax, ay, prec, bound):
+@pytest.mark.parametrize("inner", INNERS)
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_gmres_2d_matches_time_stepping(Mx, My, Nt, ax, ay, prec, bound, inner, graphs):
     u0, f = workloads.make_inputs_2d(Mx, My, Nt, seed=5)
     tau = 1.0 / Nt
-    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=prec) as plan:
+    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=prec, inner=inner, use_graphs=graphs) as plan:
         F = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
         plan.build_rhs(cu(u0), cu(f), F)
         U = torch.zeros_like(F)
@@ -118,3 +125,35 @@ def test_gmres_2d_full_size_config():
     assert info["true_rel_res"] <= 1e-10 and trr <= 1e-10, (info, trr)
     Useq = oaao.sequential_bdf2_2d(Kx, Ky, tau, u0, f)
     assert rel(host(U), Useq) <= 1e-9, (rel(host(U), Useq), info)
+
+
+@pytest.mark.parametrize("Mx,My,Nt", [(15, 7, 8), (31, 63, 4)])
+def test_strang2d_preconditioner_after_one_cocg_step(Mx, My, Nt):
+    # With one COCG iteration per system the GPU's Step (b) returns x_n = a_n P_n^{-1} b_n with
+    # P_n = lambda_n I + I (x) c_x S_x + c_y S_y (x) I (the 2D Strang BCCB circulant) and
+    # a_n = (b_n^T z_n) / (z_n^T A_n z_n), z_n = P_n^{-1} b_n: this pins the BCCB inverse itself against the
+    # oracle's (FP64 throughout, so to rounding).
+    ax, ay = 1.4, 1.8
+    tau = 1.0 / Nt
+    eps = oprec.default_eps(tau)
+    v = np.random.default_rng(Mx + My).standard_normal((Nt, My, Mx))
+    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, prec=aao.AAO_PREC_FP64, inner=aao.AAO_INNER_STRANG,
+                  inner_maxit=1) as plan:
+        z = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z)
+        torch.cuda.synchronize()
+    Kx, Ky = jacs(Mx, My, ax, ay)
+    hx, hy = 1.0 / (Mx + 1), 1.0 / (My + 1)
+    gx = (tau / hx ** ax) * fcd.fcd_weights(ax, Mx)
+    gy = (tau / hy ** ay) * fcd.fcd_weights(ay, My)
+    zh = oprec.time_dft_half(v, eps).reshape(Nt // 2 + 1, My, Mx)
+    lam = oprec.eigenvalues_C_eps(Nt, eps)
+    K = np.kron(np.eye(My), Kx) + np.kron(Ky, np.eye(Mx))
+    xh = np.empty_like(zh)
+    for n in range(Nt // 2 + 1):
+        b = zh[n]
+        zz = oprec.strang2d_inverse(gx, gy, Mx, My, lam[n])(b)
+        Az = (lam[n] * np.eye(Mx * My) - tau * K) @ zz.ravel()
+        xh[n] = (b.ravel() @ zz.ravel()) / (zz.ravel() @ Az) * zz
+    want = oprec.time_idft_half(xh, eps, Nt)
+    assert rel(host(z), want) <= 1e-11, rel(host(z), want)
