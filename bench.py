@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--held-out", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paper-examples", action="store_true",
+                    help="Examples 1 and 2 of Sec. 4 at every size of Tables 1-6 (FP64, the paper's tau-matrix "
+                         "Step (b), FGMRES / BiCGSTAB to 1e-9): Iter, TRR, Err and GPU time per row")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the comparison arms of the default run (plain FP64, the paper's eps, config 1)")
     return ap.parse_args()
@@ -392,6 +395,80 @@ def comparison_arms(args, plans, Fs, rank, dev, barrier):
     out["config1_mixed"]["workload"] = "M=63, Nt=64, alpha=1.5, kappa=1, T=1, sine1_uniform (seeds 0-3)"
     p1.close()
     return out
+
+
+def run_paper_examples(args):
+    """Tables 1-6 of Sec. 4 on the GPU: Example 1 by right-preconditioned FGMRES, Example 2 by preconditioned
+    BiCGSTAB, each with P_eps (eps = min(0.5, 0.5 tau)) and P_1, FP64, Step (b) by the direct tau-matrix solve,
+    tolerance 1e-9 from x0 = 0.  One JSON line with a row per (example, size, preconditioner): iterations,
+    true relative residual, Err = max |u* - u^Nt| and the solve time (CUDA events, after one untimed solve).
+    Example 2 lives on (0,2)^2 with mesh width 2/N: the library's (0,1) mesh with kappa scaled by 2^-alpha
+    per direction gives the same discrete operator."""
+    import torch
+    from paper_2003_07020_gb300 import aao, workloads
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        info = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return info, ev0.elapsed_time(ev1)
+
+    rows = []
+    for alpha in (1.2, 1.5, 1.9):
+        for Nt in (64, 256, 1024):
+            for N in (128, 256, 512, 1024):
+                x, u0, f = workloads.ex1_problem(alpha, Nt, N)
+                ue = workloads.ex1_exact(alpha, x, 1.0)
+                for name, eps in (("P_eps", min(0.5, 0.5 / Nt)), ("P_1", 1.0)):
+                    with aao.Plan(N - 1, Nt, alpha, kappa=0.01, T=1.0, eps=eps, prec=aao.AAO_PREC_FP64,
+                                  inner=aao.AAO_INNER_TAU_DIRECT, tol=1e-9, restart=50) as p:
+                        F = torch.empty((Nt, N - 1), dtype=torch.float64, device=dev)
+                        U = torch.zeros_like(F)
+                        p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
+
+                        def solve():
+                            U.zero_()
+                            return p.gmres_solve(F, U)
+                        info, ms = timed(solve)
+                        err = float(np.abs(ue - U[-1].cpu().numpy()).max())
+                    rows.append({"example": 1, "alpha": alpha, "Nt": Nt, "h": "1/%d" % N, "dof": Nt * (N - 1),
+                                 "precond": name, "iter": info["outer_iters"],
+                                 "trr_log10": round(float(np.log10(info["true_rel_res"])), 3),
+                                 "err": float("%.4e" % err), "ms": round(ms, 3)})
+    for a1, a2 in ((1.4, 1.2), (1.5, 1.5), (1.7, 1.9)):
+        for Nt in (64, 256, 1024):
+            for N in (64, 128, 256, 512):
+                X, Y, u0, f = workloads.ex2_problem(a1, a2, Nt, N)
+                ue = workloads.ex2_exact(X, Y, 2.0)
+                M = N - 1
+                for name, eps in (("P_eps", min(0.5, 0.5 * 2.0 / Nt)), ("P_1", 1.0)):
+                    with aao.Plan(M, Nt, a1, kappa=0.01 * 0.5 ** a1, T=2.0, eps=eps, My=M, alpha_y=a2,
+                                  kappa_y=0.01 * 0.5 ** a2, prec=aao.AAO_PREC_FP64, inner=aao.AAO_INNER_TAU_DIRECT,
+                                  tol=1e-9, restart=8, max_cycles=100) as p:
+                        F = torch.empty((Nt, M, M), dtype=torch.float64, device=dev)
+                        U = torch.zeros_like(F)
+                        p.build_rhs(torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev), F)
+
+                        def solve():
+                            U.zero_()
+                            return p.bicgstab_solve(F, U)
+                        info, ms = timed(solve)
+                        err = float(np.abs(ue - U[-1].cpu().numpy()).max())
+                        del F, U
+                    rows.append({"example": 2, "alpha": [a1, a2], "Nt": Nt, "h": "1/%d" % N, "dof": Nt * M * M,
+                                 "precond": name, "iter": info["outer_iters"] / 2.0,
+                                 "trr_log10": round(float(np.log10(info["true_rel_res"])), 3),
+                                 "err": float("%.4e" % err), "ms": round(ms, 3)})
+                del f
+                torch.cuda.empty_cache()
+    print(json.dumps({"mode": "paper_examples", "precision": "f64", "inner": "tau-matrix direct",
+                      "rows": rows}), flush=True)
 
 
 def run_ours(args):
@@ -904,6 +981,8 @@ def main():
         run_batched(args)
     elif args.learned:
         run_learned(args)
+    elif args.paper_examples:
+        run_paper_examples(args)
     else:
         run_ours(args)
 

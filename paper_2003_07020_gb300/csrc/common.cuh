@@ -171,37 +171,6 @@ template <int DIR, int r, typename T> __device__ __forceinline__ void dft(T (&v)
 }
 
 // ---- passes ----------------------------------------------------------------------------------
-// External twiddles of a 16-point table pass: v[m] *= W^{j0 m} (CONJ: its conjugate), m = 1..15, from two
-// table entries only, W^{j0} and W^{4 j0} (pt rows m = 1 and m = 4), and products W^{j0 (4a + c)} =
-// (W^{4 j0})^a W^{j0 c}: 13 complex products instead of 13 more shared-memory loads, at most five
-// roundings per twiddle.  AAO_TWIDDLE_LOADS reads all 15 table entries instead.
-template <bool CONJ, typename T>
-__device__ __forceinline__ void table_twiddles16(T (&v)[16], const T* pt, int S, int j0) {
-#ifdef AAO_TWIDDLE_LOADS
-#pragma unroll
-  for (int m = 1; m < 16; ++m) v[m] = CONJ ? cmulc(v[m], pt[(m - 1) * S + j0]) : cmul(v[m], pt[(m - 1) * S + j0]);
-#else
-  const T w1 = pt[j0], w4 = pt[3 * S + j0];
-  const T w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-  T base = w4;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    if (a > 0) {
-      v[4 * a] = CONJ ? cmulc(v[4 * a], base) : cmul(v[4 * a], base);
-      const T b1 = cmul(base, w1), b2 = cmul(base, w2), b3 = cmul(base, w3);
-      v[4 * a + 1] = CONJ ? cmulc(v[4 * a + 1], b1) : cmul(v[4 * a + 1], b1);
-      v[4 * a + 2] = CONJ ? cmulc(v[4 * a + 2], b2) : cmul(v[4 * a + 2], b2);
-      v[4 * a + 3] = CONJ ? cmulc(v[4 * a + 3], b3) : cmul(v[4 * a + 3], b3);
-      if (a < 3) base = cmul(base, w4);
-    } else {
-      v[1] = CONJ ? cmulc(v[1], w1) : cmul(v[1], w1);
-      v[2] = CONJ ? cmulc(v[2], w2) : cmul(v[2], w2);
-      v[3] = CONJ ? cmulc(v[3], w3) : cmul(v[3], w3);
-    }
-  }
-#endif
-}
-
 // One DIF pass of r stages (global stages s0 .. s0+r-1) over `batch`
 // transforms of length N = 2^logN at buf[b*bstride + pad16(i)].
 template <typename T, int r>
@@ -222,12 +191,8 @@ __device__ __forceinline__ void dif_pass(T* buf, int logN, int s0, int batch, in
     dft<-1, r>(v);
     if (j0 != 0) {
       if (pt) {
-        if constexpr (r == 4) {
-          table_twiddles16<false>(v, pt, S, j0);
-        } else {
 #pragma unroll
-          for (int m = 1; m < R; ++m) v[m] = cmul(v[m], pt[(m - 1) * S + j0]);
-        }
+        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], pt[(m - 1) * S + j0]);
       } else {
 #pragma unroll
         for (int m = 1; m < R; ++m) v[m] = cmul(v[m], twiddle<-1>(q, (j0 * m) << tshift, logNq));
@@ -256,12 +221,8 @@ __device__ __forceinline__ void dit_pass(T* buf, int logN, int s0, int batch, in
     for (int m = 0; m < R; ++m) v[m] = buf[b * bstride + pad16(start + j0 + brev_c<r>(m) * S)];
     if (j0 != 0) {
       if (pt) {
-        if constexpr (r == 4) {
-          table_twiddles16<true>(v, pt, S, j0);
-        } else {
 #pragma unroll
-          for (int m = 1; m < R; ++m) v[m] = cmulc(v[m], pt[(m - 1) * S + j0]);
-        }
+        for (int m = 1; m < R; ++m) v[m] = cmulc(v[m], pt[(m - 1) * S + j0]);
       } else {
 #pragma unroll
         for (int m = 1; m < R; ++m) v[m] = cmul(v[m], twiddle<+1>(q, (j0 * m) << tshift, logNq));

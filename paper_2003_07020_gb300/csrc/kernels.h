@@ -131,10 +131,15 @@ struct NttTables {
   uint2 crt[10];        // Garner constants (c, floor(c 2^32 / p_b)): p0^-1 mod p1..p4, p1^-1 mod p2..p4,
                         // p2^-1 mod p3, p4, p3^-1 mod p4
   double c_gscale;      // c 2^(e_g - 58)
+  const uint2* ghat4;   // [4][L] spectrum of the 52-bit stencil for the four-prime convolution of FP32 rows
+  double c_gscale4;     // c 2^(e_g - 52)
 };
 // w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the quantised row
-// (same contract as launch_matvec_f64).  res: 7 n uint32 scratch (5 n residues, then n int64
-// quantised entries, 8-byte aligned when res is); rowscale: Nt doubles.
+// (same contract as launch_matvec_f64; sq_partial gets ntt_partials(M, Nt) per-CTA sums).  FP64 rows
+// are quantised to 58 bits and convolved modulo five primes; FP32 rows (the Arnoldi step's z) to 52 bits
+// and four primes (|Y| < 2^117 below half their product).  res: 7 n uint32 scratch (residues, then n
+// int64 quantised entries, 8-byte aligned when res is); rowscale: Nt doubles.
+int ntt_partials(int M, int Nt);
 cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                               int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
 cudaError_t launch_matvec_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,

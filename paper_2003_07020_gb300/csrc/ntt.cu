@@ -30,9 +30,15 @@
 // (stride 1, no external twiddles), and the last inverse pass writes the
 // residues straight to global memory, so shared memory sees 2 (log2 L / 4) - 1
 // read-write sweeps per row.  Shared memory is padded by one word per 32.
-// Kernel 2 (ntt_epilogue_kernel): one CTA per row: Garner CRT of the five
+// Kernel 2 (ntt_epilogue_kernel): a few CTAs per row: Garner CRT of the
 // residues, scaling, the BDF band of C (Eq. 1.7), optional residual rhs - w and
-// per-row sums of squares (as the FP64 matvec).
+// per-CTA sums of squares.
+//
+// FP64 rows (the true residual and aao_matvec) use 58-bit quantisation and five
+// primes; FP32 rows (the Arnoldi step's z_j, whose 24-bit significands lose
+// nothing at 52 bits unless the row spans more than 2^28 in magnitude) use 52
+// bits and four primes: |Y| < M 2^104 <= 2^117, below half the four primes'
+// product (~2^119.5), one transform in five fewer.
 //
 // Modular arithmetic: Shoup multiplication by a constant w with precomputed
 // w' = floor(w 2^32 / p), lazy values in [0, 2p) (p < 2^30 keeps all sums
@@ -291,10 +297,11 @@ __global__ void __launch_bounds__(512) ntt_quant_kernel(const TIn* __restrict__ 
   for (int i = threadIdx.x; i < M; i += blockDim.x) Vk[i] = __double2ll_rn(ldd(vk + i) * qs);  // exact scaling
 }
 
-// The quantisation pre-pass for FP32 rows, in integer arithmetic on the bit patterns: the row's largest
-// magnitude as bits (monotone for finite values) gives e_v, and each entry m 2^E (24-bit significand m) becomes
-// m 2^(E + 58 - e_v), shifted left exactly or right with rounding half to even -- the same integers as the FP64
-// form round(v 2^(58 - e_v)), without FP64<->FP32 conversions.
+// The quantisation pre-pass for FP32 rows (to QB bits), in integer arithmetic on the bit patterns: the row's
+// largest magnitude as bits (monotone for finite values) gives e_v, and each entry m 2^E (24-bit significand m)
+// becomes m 2^(E + QB - e_v), shifted left exactly or right with rounding half to even -- the same integers as
+// round(v 2^(QB - e_v)), without FP64<->FP32 conversions.
+template <int QB>
 __global__ void __launch_bounds__(512) ntt_quant_f32_kernel(const float* __restrict__ v, int M,
                                                             long long* __restrict__ V, double* __restrict__ rowscale) {
   __shared__ unsigned int redu[32];
@@ -310,7 +317,7 @@ __global__ void __launch_bounds__(512) ntt_quant_f32_kernel(const float* __restr
   const bool bad = amax >= 0x7f800000u;
   int ev = 0;  // largest magnitude < 2^ev
   if (amax) ev = (amax >> 23) ? (int)(amax >> 23) - 126 : (32 - __clz((int)amax)) - 149;
-  if (threadIdx.x == 0) rowscale[k] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (amax ? ldexp(1.0, ev - QBITS) : 0.0);
+  if (threadIdx.x == 0) rowscale[k] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (amax ? ldexp(1.0, ev - QB) : 0.0);
   long long* Vk = V + (size_t)k * M;
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     const unsigned int u = __ldg(vk + i), a = u & 0x7fffffffu;
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(512) ntt_quant_f32_kernel(const float* __restr
     if (!bad && a) {
       const unsigned int ex = a >> 23;
       const unsigned int m = ex ? ((a & 0x7fffffu) | 0x800000u) : a;
-      const int sh = (ex ? (int)ex - 150 : -149) + QBITS - ev;  // <= 34
+      const int sh = (ex ? (int)ex - 150 : -149) + QB - ev;  // <= QB - 24
       if (sh >= 0) {
         q = (long long)m << sh;
       } else if (sh > -26) {  // m < 2^24: a shift by 26 or more rounds to 0
@@ -336,13 +343,13 @@ __global__ void __launch_bounds__(512) ntt_quant_f32_kernel(const float* __restr
 
 template <int Q>
 __device__ __forceinline__ void conv_row(const long long* __restrict__ Vk, int M, int logL, const NttTables& t,
-                                         uint32_t* buf, uint32_t* __restrict__ out) {
+                                         const uint2* __restrict__ ghat, uint32_t* buf, uint32_t* __restrict__ out) {
   constexpr uint32_t P = Prime<Q>::p;
   const int L = 1 << logL;
   const size_t tsz = (size_t)ntt_tw_size(logL);
   const uint2* twf = t.twf + Q * tsz;
   const uint2* twi = t.twi + Q * tsz;
-  const uint2* gh = t.ghat + (size_t)Q * L;
+  const uint2* gh = ghat + (size_t)Q * L;
   const int sl = ntt_last_pass(logL);
   if (sl == 0) {  // L <= 16: one pass
     for (int i = threadIdx.x; i < L; i += blockDim.x) buf[pad32(i)] = i < M ? residue<P>(__ldg(Vk + i)) : 0u;
@@ -377,19 +384,22 @@ __device__ __forceinline__ void conv_row(const long long* __restrict__ Vk, int M
   dit_last<P>(buf, logL, M, twi + 8, w, out);
 }
 
-// grid (Nt, NP): blockIdx.y selects the prime.  V: the quantised rows; res: [NP][Nt][M] residues.
+// grid (Nt, NPR): blockIdx.y selects the prime.  V: the quantised rows; res: [NPR][Nt][M] residues.  NPR = 5:
+// the 58-bit stencil spectrum; NPR = 4: the 52-bit one.
+template <int NPR>
 __global__ void __launch_bounds__(512, 2) ntt_conv_kernel(const long long* __restrict__ V, int M, int Nt, int logL,
                                                        NttTables t, uint32_t* __restrict__ res) {
   extern __shared__ uint32_t nbuf[];
   const int k = blockIdx.x, q = blockIdx.y;
   const long long* Vk = V + (size_t)k * M;
   uint32_t* out = res + ((size_t)q * Nt + k) * M;
+  const uint2* gh = NPR == 5 ? t.ghat : t.ghat4;
   switch (q) {
-    case 0: conv_row<0>(Vk, M, logL, t, nbuf, out); break;
-    case 1: conv_row<1>(Vk, M, logL, t, nbuf, out); break;
-    case 2: conv_row<2>(Vk, M, logL, t, nbuf, out); break;
-    case 3: conv_row<3>(Vk, M, logL, t, nbuf, out); break;
-    default: conv_row<4>(Vk, M, logL, t, nbuf, out); break;
+    case 0: conv_row<0>(Vk, M, logL, t, gh, nbuf, out); break;
+    case 1: conv_row<1>(Vk, M, logL, t, gh, nbuf, out); break;
+    case 2: conv_row<2>(Vk, M, logL, t, gh, nbuf, out); break;
+    case 3: conv_row<3>(Vk, M, logL, t, gh, nbuf, out); break;
+    default: if (NPR == 5) conv_row<4>(Vk, M, logL, t, gh, nbuf, out); break;
   }
 }
 
@@ -403,26 +413,30 @@ template <int B> __device__ __forceinline__ uint32_t gstep(uint32_t r, uint32_t 
   return red1<P>(mulsh<P>(a, c));
 }
 
-// Garner's mixed-radix digits d_q of the residues r_q, then
-// Y = d0 + p0 (d1 + p1 (d2 + p2 (d3 + p3 d4))) in integer arithmetic, converted to FP64 once
-// (correctly rounded); negative when d4 > p4 / 2 (|Y| < 2^129, far below half the product).
-__device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint2* c) {
+// Garner's mixed-radix digits d_q of the NPR residues r_q, then
+// Y = d0 + p0 (d1 + p1 (d2 + ...)) in integer arithmetic, converted to FP64 once (correctly rounded);
+// negative when the last digit exceeds half its prime (|Y| < 2^129 for five primes, 2^117 for four: far
+// below half the product).
+template <int NPR>
+__device__ __forceinline__ double crt(const uint32_t (&rq)[NP], const uint2* c) {
   constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p, p4 = Prime<4>::p;
   // c: p0^-1 mod p1..p4 (c[0..3]), p1^-1 mod p2..p4 (c[4..6]), p2^-1 mod p3, p4 (c[7..8]), p3^-1 mod p4 (c[9])
-  const uint32_t d0 = rq[0];
-  const uint32_t d1 = gstep<1>(rq[1], d0, c[0]);
-  const uint32_t d2 = gstep<2>(gstep<2>(rq[2], d0, c[1]), d1, c[4]);
-  const uint32_t d3 = gstep<3>(gstep<3>(gstep<3>(rq[3], d0, c[2]), d1, c[5]), d2, c[7]);
-  const uint32_t d4 = gstep<4>(gstep<4>(gstep<4>(gstep<4>(rq[4], d0, c[3]), d1, c[6]), d2, c[8]), d3, c[9]);
-  // Y (|Y| < 2^129) as a 3-limb integer from the mixed-radix digits, negative when d4 > p4 / 2
-  // (then |Y| = (P - 1 - Y) + 1 with the complemented digits p_q - 1 - d_q), converted once.
-  const bool neg = d4 > p4 / 2;
-  const uint64_t e[NP] = {neg ? p0 - 1 - d0 : d0, neg ? p1 - 1 - d1 : d1, neg ? p2 - 1 - d2 : d2,
-                          neg ? p3 - 1 - d3 : d3, neg ? p4 - 1 - d4 : d4};
-  const uint64_t pm[4] = {p0, p1, p2, p3};
-  uint64_t l0 = e[4], l1 = 0, l2 = 0;
+  uint32_t d[NP];
+  d[0] = rq[0];
+  d[1] = gstep<1>(rq[1], d[0], c[0]);
+  d[2] = gstep<2>(gstep<2>(rq[2], d[0], c[1]), d[1], c[4]);
+  d[3] = gstep<3>(gstep<3>(gstep<3>(rq[3], d[0], c[2]), d[1], c[5]), d[2], c[7]);
+  if (NPR == 5) d[4] = gstep<4>(gstep<4>(gstep<4>(gstep<4>(rq[4], d[0], c[3]), d[1], c[6]), d[2], c[8]), d[3], c[9]);
+  // Y as a 3-limb integer from the mixed-radix digits; when negative, |Y| = (P - 1 - Y) + 1 with the
+  // complemented digits p_q - 1 - d_q, converted once.
+  const uint64_t pm[NP] = {p0, p1, p2, p3, p4};
+  const bool neg = d[NPR - 1] > pm[NPR - 1] / 2;
+  uint64_t e[NP];
 #pragma unroll
-  for (int q = 3; q >= 0; --q) {  // (l2, l1, l0) = (l2, l1, l0) * p_q + e_q
+  for (int q = 0; q < NPR; ++q) e[q] = neg ? pm[q] - 1 - d[q] : d[q];
+  uint64_t l0 = e[NPR - 1], l1 = 0, l2 = 0;
+#pragma unroll
+  for (int q = NPR - 2; q >= 0; --q) {  // (l2, l1, l0) = (l2, l1, l0) * p_q + e_q
     const uint64_t m = pm[q];
     const uint64_t lo0 = l0 * m, hi0 = __umul64hi(l0, m);
     const uint64_t lo1 = l1 * m, hi1 = __umul64hi(l1, m);
@@ -438,9 +452,9 @@ __device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint2* c)
   }
   if (neg) {  // + 1
     l0 += 1;
-    const uint64_t c = l0 == 0;
-    l1 += c;
-    l2 += (c && l1 == 0);
+    const uint64_t cc = l0 == 0;
+    l1 += cc;
+    l2 += (cc && l1 == 0);
   }
   // top 64 significant bits with a sticky bit (correct rounding), times 2^shift
   uint64_t top;
@@ -464,14 +478,22 @@ __device__ __forceinline__ double crt5(const uint32_t (&rq)[NP], const uint2* c)
   return neg ? -mag : mag;
 }
 
-template <typename TIn>
+// Chunks per row of the epilogue: about 8 elements per thread of a 256-thread CTA, so that a matvec's
+// epilogue launches several waves of CTAs instead of one CTA per row.
+inline int epi_chunks(int M) { return (M + 256 * 8 - 1) / (256 * 8); }
+
+// grid (Nt, chunks): CTA (k, c) finishes elements [c chunk, (c + 1) chunk) of row k.
+template <typename TIn, int NPR>
 __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict__ v, const double* __restrict__ rhs,
                                                            double* __restrict__ w, double* __restrict__ sq_partial,
                                                            int M, int Nt, const uint32_t* __restrict__ res,
                                                            const double* __restrict__ rowscale, NttTables t) {
   __shared__ double redb[32];
   const int k = blockIdx.x;
-  const double f = t.c_gscale * rowscale[k];  // c 2^(e_g - 58) 2^(e_v - 58)
+  const int chunk = (M + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * chunk, i1 = min(M, i0 + chunk);
+  // c 2^(e_g - QB) 2^(e_v - QB)
+  const double f = (NPR == 5 ? t.c_gscale : t.c_gscale4) * rowscale[k];
   const TIn* vk = v + (size_t)k * M;
   const TIn* vk1 = vk - M;
   const TIn* vk2 = vk - 2 * M;
@@ -479,11 +501,11 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
   const double* rk = rhs ? rhs + (size_t)k * M : nullptr;
   const size_t n = (size_t)Nt * M, base = (size_t)k * M;
   double sq = 0.0;
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     uint32_t rq[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) rq[q] = res[q * n + base + i];
-    const double y = f * crt5(rq, t.crt);
+    for (int q = 0; q < NP; ++q) rq[q] = q < NPR ? res[q * n + base + i] : 0u;
+    const double y = f * crt<NPR>(rq, t.crt);
     double band;
     if (k == 0) band = ldd(vk + i);
     else if (k == 1) band = 1.5 * ldd(vk + i) - 2.0 * ldd(vk1 + i);
@@ -496,30 +518,35 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
   if (sq_partial) {
     double a[1] = {sq};
     block_sum<double, 1>(a, redb);
-    if (threadIdx.x == 0) sq_partial[k] = a[0];
+    if (threadIdx.x == 0) sq_partial[(size_t)k * gridDim.y + blockIdx.y] = a[0];
   }
 }
 
+// FP64 rows: 58-bit quantisation, five primes; FP32 rows: 52-bit, four primes.
 template <typename TIn>
 cudaError_t launch_ntt(const TIn* v, const double* rhs, double* w, double* sq_partial, int M, int Nt, int logL,
                        const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s) {
+  constexpr int NPR = sizeof(TIn) == 4 ? 4 : 5;
   const int L = 1 << logL;
   const size_t smem = (size_t)(L + L / 32 + 1) * sizeof(uint32_t);
-  cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel);
+  cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel<NPR>);
   if (e != cudaSuccess) return e;
   long long* V = reinterpret_cast<long long*>(res + (size_t)NP * Nt * M);  // after the residues
-  if constexpr (sizeof(TIn) == 4) ntt_quant_f32_kernel<<<Nt, 512, 0, s>>>(v, M, V, rowscale);
+  if constexpr (sizeof(TIn) == 4) ntt_quant_f32_kernel<52><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
   else ntt_quant_kernel<TIn><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ntt_conv_kernel<<<dim3(Nt, NP), 512, smem, s>>>(V, M, Nt, logL, t, res);
+  ntt_conv_kernel<NPR><<<dim3(Nt, NPR), 512, smem, s>>>(V, M, Nt, logL, t, res);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ntt_epilogue_kernel<TIn><<<Nt, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t);
+  ntt_epilogue_kernel<TIn, NPR><<<dim3(Nt, epi_chunks(M)), 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale,
+                                                                        t);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+int ntt_partials(int M, int Nt) { return Nt * epi_chunks(M); }
 
 cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                               int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s) {

@@ -1020,8 +1020,11 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->ntt_tab.twi = (const uint2*)q32;
     TRYP(upload(p, &q32, p->ht.ntt_ghat));
     p->ntt_tab.ghat = (const uint2*)q32;
+    TRYP(upload(p, &q32, p->ht.ntt_ghat4));
+    p->ntt_tab.ghat4 = (const uint2*)q32;
     for (int i = 0; i < 10; ++i) p->ntt_tab.crt[i] = make_uint2(p->ht.ntt_crt[2 * i], p->ht.ntt_crt[2 * i + 1]);
     p->ntt_tab.c_gscale = p->ht.ntt_c_gscale;
+    p->ntt_tab.c_gscale4 = p->ht.ntt_c_gscale4;
     TRYP(dalloc(p, &p->ntt_res, (size_t)(aao::kNttPrimes + 2) * n));  // residues + int64 quantised rows
     TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));
     p->ntt = true;
@@ -1042,7 +1045,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     TRYP(dalloc(p, &q, (size_t)p->nsys * p->Msp * csz));
     p->pws = q;
   }
-  p->nsq = (size_t)p->Nt;
+  p->nsq = p->ntt ? (size_t)aao::ntt_partials(p->M, p->Nt) : (size_t)p->Nt;
   if (p->dim == 2) {
     const aao::HostTables& ty = p->hty;
     TRYP(upload_c(p, &p->twy64, ty.tw_L));

@@ -48,6 +48,8 @@ struct HostTables {
   std::vector<uint32_t> ntt_ghat;   // [5][L][2]: NTT of the quantised stencil embedding, bit-reversed, times L^-1
   uint32_t ntt_crt[20] = {0};       // Garner constants and their Shoup companions (see ntt.cu)
   double ntt_c_gscale = 0;          // c 2^(e_g - 58): G_j = round(g_j 2^(58 - e_g))
+  std::vector<uint32_t> ntt_ghat4;  // [4][L][2]: the same for the 52-bit stencil and the first four primes
+  double ntt_c_gscale4 = 0;         // c 2^(e_g - 52)
 };
 
 // Builds the NTT matvec tables of t (after build_tables); primes and generators are
