@@ -263,12 +263,12 @@ NTT_PEAK_GBFLY = 6.27 * 152 * 2.07
 
 
 def ntt_butterflies(M, Nt):
-    """Radix-2-equivalent modular butterflies of one NTT matvec: 5 primes x (forward + inverse)
+    """Radix-2-equivalent modular butterflies of one NTT matvec: 4 primes x (forward + inverse)
     NTT of length L per time row (L/2 log2 L each)."""
     L = 4
     while L < 2 * M:
         L *= 2
-    return 5 * 2 * (L // 2) * np.log2(L) * Nt
+    return 4 * 2 * (L // 2) * np.log2(L) * Nt
 FP32_PEAK_TFLOPS = 2 * 114.0 * 152 * 2.07e9 / 1e12
 
 

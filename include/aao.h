@@ -71,7 +71,7 @@ typedef enum {
 typedef enum {
   AAO_MATVEC_FFT64 = 0, /* FP64 FFT convolution (circulant embedding) */
   AAO_MATVEC_NTT = 1    /* exact integer convolution of the rows quantised to 58-bit fixed point
-                           (2^-59 relative to the row's largest entry) by NTTs modulo five primes
+                           (2^-59 relative to the row's largest entry) by NTTs modulo four primes
                            and CRT */
 } aao_matvec_kind;
 
@@ -164,7 +164,7 @@ aao_status aao_setup_coeffs(double alpha, int64_t n, double* g_host);
  * embedding spectrum of T, the eigenvalues lambda_n of C_eps (Eq. 1.6a) for
  * n = 0..Nt/2, the inner preconditioner's spectrum, FFT twiddle tables, and
  * all device workspace: about (2m+6) * 8 * M * Nt bytes for restart m, plus
- * 28 * M * Nt bytes of NTT scratch (AAO_MATVEC_NTT) and, for the mixed Strang
+ * 24 * M * Nt bytes of NTT scratch (AAO_MATVEC_NTT) and, for the mixed Strang
  * path, the per-system spectra of the Strang inverse ((Nt/2+1) * L * 8 bytes,
  * L the embedding length, a power of two >= 2M).  Mixed 1D plans with
  * M <= 8192 launch kernels during creation (those spectra, and the CTA-size
@@ -194,7 +194,7 @@ aao_status aao_build_rhs(aao_plan* plan, const double* u0_dev, const double* f_d
  * w = calA v (Sec. 3.2): row k of w is sum_{j<=2} C[k,k-j] v_{k-j} - tau K v_k,
  * with the Toeplitz product by circulant embedding.  opts.matvec selects the
  * arithmetic: AAO_MATVEC_NTT (the default in 1D) quantises each row of v to
- * 58-bit fixed point and convolves it exactly by NTTs modulo five primes;
+ * 58-bit fixed point and convolves it exactly by NTTs modulo four primes;
  * AAO_MATVEC_FFT64 (and every 2D plan) uses FP64 FFTs.  Either way the
  * result carries FP64 accuracy.  v_dev, w_dev: double[Nt][M], must not alias.
  */

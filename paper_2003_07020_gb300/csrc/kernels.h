@@ -98,10 +98,10 @@ int cocg_reg_min_threads(int M);
 cudaError_t launch_fill_test_rhs(float2* x, size_t n, cudaStream_t s);
 
 // ---- exact-integer matvec (NTT), ntt.cu ---------------------------------------------
-// Five primes p < 2^30 with 2^22 | p - 1 (product ~2^149) and a primitive root of each.
-constexpr int kNttPrimes = 5;
-constexpr uint32_t kNttPrime[kNttPrimes] = {1004535809u, 998244353u, 985661441u, 943718401u, 880803841u};
-constexpr uint32_t kNttGen[kNttPrimes] = {3u, 3u, 3u, 7u, 26u};
+// Four primes p < 2^30 with 2^22 | p - 1 (product ~2^119.5) and a primitive root of each.
+constexpr int kNttPrimes = 4;
+constexpr uint32_t kNttPrime[kNttPrimes] = {1004535809u, 998244353u, 985661441u, 943718401u};
+constexpr uint32_t kNttGen[kNttPrimes] = {3u, 3u, 3u, 7u};
 // Twiddle tables of the transforms, per prime and direction, in the order the passes read
 // them: 8 constant roots w^(e L / Rmax) (Rmax = min(16, L)), then for every pass but the last
 // (stages s0 .. s0 + r - 1, r = min(4, logL - s0), S = L >> (s0 + r)) its (2^r - 1) S external
@@ -125,21 +125,23 @@ AAO_HD inline int ntt_tw_offset(int logL, int s0) {
 AAO_HD inline int ntt_tw_size(int logL) { return ntt_tw_offset(logL, ntt_last_pass(logL)); }
 #undef AAO_HD
 struct NttTables {
-  const uint2* twf;     // [5][ntt_tw_size(logL)] forward roots w (a primitive L-th root mod p), layout above
-  const uint2* twi;     // [5][ntt_tw_size(logL)] the same for w^-1
-  const uint2* ghat;    // [5][L] stencil spectrum, bit-reversed, times L^-1
-  uint2 crt[10];        // Garner constants (c, floor(c 2^32 / p_b)): p0^-1 mod p1..p4, p1^-1 mod p2..p4,
-                        // p2^-1 mod p3, p4, p3^-1 mod p4
+  const uint2* twf;     // [4][ntt_tw_size(logL)] forward roots w (a primitive L-th root mod p), layout above
+  const uint2* twi;     // [4][ntt_tw_size(logL)] the same for w^-1
+  const uint2* ghat;    // [4][L] stencil spectrum, bit-reversed, times L^-1
+  uint2 crt[6];         // Garner constants (c, floor(c 2^32 / p_b)): p0^-1 mod p1, p2, p3, p1^-1 mod p2, p3,
+                        // p2^-1 mod p3
   double c_gscale;      // c 2^(e_g - 58)
-  const uint2* ghat4;   // [4][L] spectrum of the 52-bit stencil for the four-prime convolution of FP32 rows
-  double c_gscale4;     // c 2^(e_g - 52)
 };
-// w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the quantised row
-// (same contract as launch_matvec_f64; sq_partial gets ntt_partials(M, Nt) per-CTA sums).  FP64 rows
-// are quantised to 58 bits and convolved modulo five primes; FP32 rows (the Arnoldi step's z) to 52 bits
-// and four primes (|Y| < 2^117 below half their product).  res: 7 n uint32 scratch (residues, then n
-// int64 quantised entries, 8-byte aligned when res is); rowscale: Nt doubles.
+// w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the row quantised to 58 bits
+// (same contract as launch_matvec_f64; sq_partial gets ntt_partials(M, Nt) per-CTA sums).  res: 6 n uint32
+// scratch (4 n residues, then n int64 quantised entries, 8-byte aligned when res is); rowscale: Nt doubles.
 int ntt_partials(int M, int Nt);
+// The FP32-row matvec w = calA v of the mixed Arnoldi step with the first Gram-Schmidt pass fused into its
+// epilogue: dots_partial[b nv + i] (b < ntt_partials(M, Nt)) = partial sums of hi(w) hi(V_i), i < nv <= 65,
+// for V a float-float basis (vectors vstride elements apart) -- launch_dots_ff's sums, one read of w less.
+cudaError_t launch_matvec_ntt_fin_dots(const float* v, double* w, int M, int Nt, int logL, const NttTables& t,
+                                       uint32_t* res, double* rowscale, const float2* V, size_t vstride, int nv,
+                                       double* dots_partial, cudaStream_t s);
 cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                               int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
 cudaError_t launch_matvec_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,

@@ -6,9 +6,12 @@
 // Row k of v is scaled by a power of two so that its largest magnitude lies in
 // [2^57, 2^58) and rounded to integers V (quantisation error 2^-59 of the row's
 // largest entry); the FCD stencil g is quantised the same way once at plan
-// creation (G).  The linear convolution Y = G * V has |Y| < M 2^116 <= 2^129
-// and is computed modulo five NTT primes p_q < 2^30 (product ~2^149) by
-// cyclic convolution of length L >= 2M - 1 (circulant embedding), then
+// creation (G, G_0 <= 2^58).  The linear convolution Y = G * V is bounded by
+// max|V| sum_d |G_d|, and the FCD weights have g_0 > 0 >= g_d (d >= 1) with
+// sum over all d of g_d = 0 (Lemma 2.1), so sum_d |G_d| <= 2 G_0 + M (the
+// rounding) and |Y| < 2^117 (1 + 2^-45).  Four NTT primes p_q < 2^30 (product
+// ~2^119.5) therefore determine Y exactly: it is computed by cyclic
+// convolution of length L >= 2M - 1 (circulant embedding) modulo each prime,
 // reconstructed by Garner's mixed-radix CRT and converted to FP64:
 // c T v_k = c 2^(e_v + e_g - 116) Y.
 //
@@ -31,19 +34,14 @@
 // residues straight to global memory, so shared memory sees 2 (log2 L / 4) - 1
 // read-write sweeps per row.  Shared memory is padded by one word per 32.
 // Kernel 2 (ntt_epilogue_kernel): a few CTAs per row: Garner CRT of the
-// residues, scaling, the BDF band of C (Eq. 1.7), optional residual rhs - w and
-// per-CTA sums of squares.
-//
-// FP64 rows (the true residual and aao_matvec) use 58-bit quantisation and five
-// primes; FP32 rows (the Arnoldi step's z_j, whose 24-bit significands lose
-// nothing at 52 bits unless the row spans more than 2^28 in magnitude) use 52
-// bits and four primes: |Y| < M 2^104 <= 2^117, below half the four primes'
-// product (~2^119.5), one transform in five fewer.
+// residues, scaling, the BDF band of C (Eq. 1.7), optional residual rhs - w,
+// per-CTA sums of squares and (Arnoldi step) the first Gram-Schmidt pass.
 //
 // Modular arithmetic: Shoup multiplication by a constant w with precomputed
 // w' = floor(w 2^32 / p), lazy values in [0, 2p) (p < 2^30 keeps all sums
 // below 2^32).
 #include "common.cuh"
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace aao {
@@ -384,27 +382,23 @@ __device__ __forceinline__ void conv_row(const long long* __restrict__ Vk, int M
   dit_last<P>(buf, logL, M, twi + 8, w, out);
 }
 
-// grid (Nt, NPR): blockIdx.y selects the prime.  V: the quantised rows; res: [NPR][Nt][M] residues.  NPR = 5:
-// the 58-bit stencil spectrum; NPR = 4: the 52-bit one.
-template <int NPR>
+// grid (Nt, NP): blockIdx.y selects the prime.  V: the quantised rows; res: [NP][Nt][M] residues.
 __global__ void __launch_bounds__(512, 2) ntt_conv_kernel(const long long* __restrict__ V, int M, int Nt, int logL,
                                                        NttTables t, uint32_t* __restrict__ res) {
   extern __shared__ uint32_t nbuf[];
   const int k = blockIdx.x, q = blockIdx.y;
   const long long* Vk = V + (size_t)k * M;
   uint32_t* out = res + ((size_t)q * Nt + k) * M;
-  const uint2* gh = NPR == 5 ? t.ghat : t.ghat4;
   switch (q) {
-    case 0: conv_row<0>(Vk, M, logL, t, gh, nbuf, out); break;
-    case 1: conv_row<1>(Vk, M, logL, t, gh, nbuf, out); break;
-    case 2: conv_row<2>(Vk, M, logL, t, gh, nbuf, out); break;
-    case 3: conv_row<3>(Vk, M, logL, t, gh, nbuf, out); break;
-    default: if (NPR == 5) conv_row<4>(Vk, M, logL, t, gh, nbuf, out); break;
+    case 0: conv_row<0>(Vk, M, logL, t, t.ghat, nbuf, out); break;
+    case 1: conv_row<1>(Vk, M, logL, t, t.ghat, nbuf, out); break;
+    case 2: conv_row<2>(Vk, M, logL, t, t.ghat, nbuf, out); break;
+    default: conv_row<3>(Vk, M, logL, t, t.ghat, nbuf, out); break;
   }
 }
 
 // One Garner step in 32-bit arithmetic: (r - x) c mod p_B for a residue r < p_B, a digit x < p_A (one
-// subtraction brings it below p_B: the five primes lie within a factor 1.15 of each other) and the constant
+// subtraction brings it below p_B: the four primes lie within a factor 1.07 of each other) and the constant
 // c = (c, floor(c 2^32 / p_B)) by Shoup multiplication.
 template <int B> __device__ __forceinline__ uint32_t gstep(uint32_t r, uint32_t x, uint2 c) {
   constexpr uint32_t P = Prime<B>::p;
@@ -413,30 +407,27 @@ template <int B> __device__ __forceinline__ uint32_t gstep(uint32_t r, uint32_t 
   return red1<P>(mulsh<P>(a, c));
 }
 
-// Garner's mixed-radix digits d_q of the NPR residues r_q, then
-// Y = d0 + p0 (d1 + p1 (d2 + ...)) in integer arithmetic, converted to FP64 once (correctly rounded);
-// negative when the last digit exceeds half its prime (|Y| < 2^129 for five primes, 2^117 for four: far
+// Garner's mixed-radix digits d_q of the four residues r_q, then Y = d0 + p0 (d1 + p1 (d2 + p2 d3)) in
+// integer arithmetic, converted to FP64 once (correctly rounded); negative when d3 > p3 / 2 (|Y| < 2^117.01,
 // below half the product).
-template <int NPR>
-__device__ __forceinline__ double crt(const uint32_t (&rq)[NP], const uint2* c) {
-  constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p, p4 = Prime<4>::p;
-  // c: p0^-1 mod p1..p4 (c[0..3]), p1^-1 mod p2..p4 (c[4..6]), p2^-1 mod p3, p4 (c[7..8]), p3^-1 mod p4 (c[9])
+__device__ __forceinline__ double crt4(const uint32_t (&rq)[NP], const uint2* c) {
+  constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p;
+  // c: p0^-1 mod p1, p2, p3 (c[0..2]), p1^-1 mod p2, p3 (c[3..4]), p2^-1 mod p3 (c[5])
   uint32_t d[NP];
   d[0] = rq[0];
   d[1] = gstep<1>(rq[1], d[0], c[0]);
-  d[2] = gstep<2>(gstep<2>(rq[2], d[0], c[1]), d[1], c[4]);
-  d[3] = gstep<3>(gstep<3>(gstep<3>(rq[3], d[0], c[2]), d[1], c[5]), d[2], c[7]);
-  if (NPR == 5) d[4] = gstep<4>(gstep<4>(gstep<4>(gstep<4>(rq[4], d[0], c[3]), d[1], c[6]), d[2], c[8]), d[3], c[9]);
+  d[2] = gstep<2>(gstep<2>(rq[2], d[0], c[1]), d[1], c[3]);
+  d[3] = gstep<3>(gstep<3>(gstep<3>(rq[3], d[0], c[2]), d[1], c[4]), d[2], c[5]);
   // Y as a 3-limb integer from the mixed-radix digits; when negative, |Y| = (P - 1 - Y) + 1 with the
   // complemented digits p_q - 1 - d_q, converted once.
-  const uint64_t pm[NP] = {p0, p1, p2, p3, p4};
-  const bool neg = d[NPR - 1] > pm[NPR - 1] / 2;
+  const uint64_t pm[NP] = {p0, p1, p2, p3};
+  const bool neg = d[NP - 1] > pm[NP - 1] / 2;
   uint64_t e[NP];
 #pragma unroll
-  for (int q = 0; q < NPR; ++q) e[q] = neg ? pm[q] - 1 - d[q] : d[q];
-  uint64_t l0 = e[NPR - 1], l1 = 0, l2 = 0;
+  for (int q = 0; q < NP; ++q) e[q] = neg ? pm[q] - 1 - d[q] : d[q];
+  uint64_t l0 = e[NP - 1], l1 = 0, l2 = 0;
 #pragma unroll
-  for (int q = NPR - 2; q >= 0; --q) {  // (l2, l1, l0) = (l2, l1, l0) * p_q + e_q
+  for (int q = NP - 2; q >= 0; --q) {  // (l2, l1, l0) = (l2, l1, l0) * p_q + e_q
     const uint64_t m = pm[q];
     const uint64_t lo0 = l0 * m, hi0 = __umul64hi(l0, m);
     const uint64_t lo1 = l1 * m, hi1 = __umul64hi(l1, m);
@@ -482,18 +473,28 @@ __device__ __forceinline__ double crt(const uint32_t (&rq)[NP], const uint2* c) 
 // epilogue launches several waves of CTAs instead of one CTA per row.
 inline int epi_chunks(int M) { return (M + 256 * 8 - 1) / (256 * 8); }
 
+// Pass-1 Gram-Schmidt dots fused into the epilogue (the Arnoldi step of the mixed path): with NVMAX > 0 each
+// CTA also writes the partial sums of hi(w) hi(V_i) for i < nv (V: float-float basis vectors of vstride
+// elements) to dots_partial[(k chunks + c) nv + i], the FP32 first pass of CGS2.
+struct FusedDots {
+  const float2* V;
+  size_t vstride;
+  int nv;
+  double* partial;
+};
+
 // grid (Nt, chunks): CTA (k, c) finishes elements [c chunk, (c + 1) chunk) of row k.
-template <typename TIn, int NPR>
+template <typename TIn, int NVMAX>
 __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict__ v, const double* __restrict__ rhs,
                                                            double* __restrict__ w, double* __restrict__ sq_partial,
                                                            int M, int Nt, const uint32_t* __restrict__ res,
-                                                           const double* __restrict__ rowscale, NttTables t) {
+                                                           const double* __restrict__ rowscale, NttTables t,
+                                                           FusedDots fd) {
   __shared__ double redb[32];
   const int k = blockIdx.x;
   const int chunk = (M + gridDim.y - 1) / gridDim.y;
   const int i0 = blockIdx.y * chunk, i1 = min(M, i0 + chunk);
-  // c 2^(e_g - QB) 2^(e_v - QB)
-  const double f = (NPR == 5 ? t.c_gscale : t.c_gscale4) * rowscale[k];
+  const double f = t.c_gscale * rowscale[k];  // c 2^(e_g - 58) 2^(e_v - 58)
   const TIn* vk = v + (size_t)k * M;
   const TIn* vk1 = vk - M;
   const TIn* vk2 = vk - 2 * M;
@@ -501,11 +502,18 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
   const double* rk = rhs ? rhs + (size_t)k * M : nullptr;
   const size_t n = (size_t)Nt * M, base = (size_t)k * M;
   double sq = 0.0;
+  float acc[NVMAX > 0 ? NVMAX : 1];
+#pragma unroll
+  for (int q = 0; q < (NVMAX > 0 ? NVMAX : 1); ++q) acc[q] = 0.0f;
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     uint32_t rq[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) rq[q] = q < NPR ? res[q * n + base + i] : 0u;
-    const double y = f * crt<NPR>(rq, t.crt);
+    for (int q = 0; q < NP; ++q) rq[q] = res[q * n + base + i];
+    float vh[NVMAX > 0 ? NVMAX : 1];
+#pragma unroll
+    for (int q = 0; q < NVMAX; ++q)
+      if (q < fd.nv) vh[q] = __ldg(&fd.V[q * fd.vstride + base + i]).x;
+    const double y = f * crt4(rq, t.crt);
     double band;
     if (k == 0) band = ldd(vk + i);
     else if (k == 1) band = 1.5 * ldd(vk + i) - 2.0 * ldd(vk1 + i);
@@ -514,39 +522,68 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
     if (rk) out = rk[i] - out;
     wk[i] = out;
     sq += out * out;
+    if (NVMAX > 0) {
+      const float wh = ff_split(out).x;
+#pragma unroll
+      for (int q = 0; q < NVMAX; ++q)
+        if (q < fd.nv) acc[q] = fmaf(wh, vh[q], acc[q]);
+    }
   }
   if (sq_partial) {
     double a[1] = {sq};
     block_sum<double, 1>(a, redb);
     if (threadIdx.x == 0) sq_partial[(size_t)k * gridDim.y + blockIdx.y] = a[0];
   }
+  if constexpr (NVMAX > 0) {
+    double accd[NVMAX];
+#pragma unroll
+    for (int q = 0; q < NVMAX; ++q) accd[q] = (double)acc[q];
+    block_partials_to<NVMAX, 256>(accd, fd.nv, fd.partial + ((size_t)k * gridDim.y + blockIdx.y) * fd.nv);
+  }
 }
 
-// FP64 rows: 58-bit quantisation, five primes; FP32 rows: 52-bit, four primes.
 template <typename TIn>
 cudaError_t launch_ntt(const TIn* v, const double* rhs, double* w, double* sq_partial, int M, int Nt, int logL,
-                       const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s) {
-  constexpr int NPR = sizeof(TIn) == 4 ? 4 : 5;
+                       const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s,
+                       FusedDots fd = FusedDots{nullptr, 0, 0, nullptr}) {
   const int L = 1 << logL;
   const size_t smem = (size_t)(L + L / 32 + 1) * sizeof(uint32_t);
-  cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel<NPR>);
+  cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel);
   if (e != cudaSuccess) return e;
   long long* V = reinterpret_cast<long long*>(res + (size_t)NP * Nt * M);  // after the residues
-  if constexpr (sizeof(TIn) == 4) ntt_quant_f32_kernel<52><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
+  if constexpr (sizeof(TIn) == 4) ntt_quant_f32_kernel<QBITS><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
   else ntt_quant_kernel<TIn><<<Nt, 512, 0, s>>>(v, M, V, rowscale);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ntt_conv_kernel<NPR><<<dim3(Nt, NPR), 512, smem, s>>>(V, M, Nt, logL, t, res);
+  ntt_conv_kernel<<<dim3(Nt, NP), 512, smem, s>>>(V, M, Nt, logL, t, res);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ntt_epilogue_kernel<TIn, NPR><<<dim3(Nt, epi_chunks(M)), 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale,
-                                                                        t);
+  const dim3 ge(Nt, epi_chunks(M));
+  if (!fd.partial) {
+    ntt_epilogue_kernel<TIn, 0><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+  } else {
+    const int nv = fd.nv;
+    if (nv <= 4) ntt_epilogue_kernel<TIn, 4><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+    else if (nv <= 8) ntt_epilogue_kernel<TIn, 8><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+    else if (nv <= 16) ntt_epilogue_kernel<TIn, 16><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+    else if (nv <= 24) ntt_epilogue_kernel<TIn, 24><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+    else if (nv <= 32) ntt_epilogue_kernel<TIn, 32><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+    else ntt_epilogue_kernel<TIn, 65><<<ge, 256, 0, s>>>(v, rhs, w, sq_partial, M, Nt, res, rowscale, t, fd);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
 int ntt_partials(int M, int Nt) { return Nt * epi_chunks(M); }
+
+cudaError_t launch_matvec_ntt_fin_dots(const float* v, double* w, int M, int Nt, int logL, const NttTables& t,
+                                       uint32_t* res, double* rowscale, const float2* V, size_t vstride, int nv,
+                                       double* dots_partial, cudaStream_t s) {
+  if (nv < 1 || nv > 65 || !V || !dots_partial) return cudaErrorInvalidValue;
+  return launch_ntt<float>(v, nullptr, w, nullptr, M, Nt, logL, t, res, rowscale, s,
+                           FusedDots{V, vstride, nv, dots_partial});
+}
 
 cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                               int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s) {

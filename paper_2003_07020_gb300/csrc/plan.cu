@@ -594,9 +594,16 @@ aao_status arnoldi_step(aao_plan* p, int j, GmresDevState* acc) {
   if (p->mixed) {  // float-float basis: w = A z_j into W (FP64), CGS2 writes v_{j+1} as float-float
     const float2* Vf = (const float2*)(const void*)p->V;
     float2* wf = (float2*)(void*)w;
-    TRY(matvec_any(p, zj, true, nullptr, p->W, nullptr));
-    LAUNCH(ST_VEC, 1, aao::launch_dots_ff(p->W, Vf, n, nv, n, p->partial, p->stream));
-    LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
+    if (p->ntt) {  // 1D: pass-1 dots fused into the matvec epilogue (one read of w less)
+      LAUNCH(ST_MATVEC, 3, aao::launch_matvec_ntt_fin_dots((const float*)zj, p->W, p->M, p->Nt, p->logL, p->ntt_tab,
+                                                           p->ntt_res, p->ntt_rowscale, Vf, n, nv, p->partial,
+                                                           p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, (int)p->nsq, nv, p->hdev, p->stream));
+    } else {
+      TRY(matvec_any(p, zj, true, nullptr, p->W, nullptr));
+      LAUNCH(ST_VEC, 1, aao::launch_dots_ff(p->W, Vf, n, nv, n, p->partial, p->stream));
+      LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev, p->stream));
+    }
     LAUNCH(ST_VEC, 1, aao::launch_update_dots_ff(p->W, wf, Vf, n, nv, n, p->hdev, p->partial, p->stream));
     LAUNCH(ST_VEC, 1, aao::launch_reduce_partials(p->partial, nb, nv, p->hdev + 65, p->stream));
     LAUNCH(ST_VEC, 1, aao::launch_update_norm_ff(wf, Vf, n, nv, n, p->hdev + 65, p->partial, p->stream));
@@ -1020,11 +1027,8 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->ntt_tab.twi = (const uint2*)q32;
     TRYP(upload(p, &q32, p->ht.ntt_ghat));
     p->ntt_tab.ghat = (const uint2*)q32;
-    TRYP(upload(p, &q32, p->ht.ntt_ghat4));
-    p->ntt_tab.ghat4 = (const uint2*)q32;
-    for (int i = 0; i < 10; ++i) p->ntt_tab.crt[i] = make_uint2(p->ht.ntt_crt[2 * i], p->ht.ntt_crt[2 * i + 1]);
+    for (int i = 0; i < 6; ++i) p->ntt_tab.crt[i] = make_uint2(p->ht.ntt_crt[2 * i], p->ht.ntt_crt[2 * i + 1]);
     p->ntt_tab.c_gscale = p->ht.ntt_c_gscale;
-    p->ntt_tab.c_gscale4 = p->ht.ntt_c_gscale4;
     TRYP(dalloc(p, &p->ntt_res, (size_t)(aao::kNttPrimes + 2) * n));  // residues + int64 quantised rows
     TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));
     p->ntt = true;
@@ -1130,7 +1134,8 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->err = "cudaMemset failed";
     return bail(AAO_ECUDA);
   }
-  TRYP(dalloc(p, &p->partial, (size_t)std::max(aao::blas_partial_blocks() * 65, p->Nt)));
+  TRYP(dalloc(p, &p->partial, std::max<size_t>((size_t)aao::blas_partial_blocks() * 65,
+                                               std::max<size_t>(p->nsq * 65, (size_t)p->Nt))));
   TRYP(dalloc(p, &p->hdev, 4 * 65));
   TRYP(dalloc(p, &p->sq, p->nsq));
   if (cudaMallocHost(&p->pinned, 4 * 65 * sizeof(double)) != cudaSuccess) {

@@ -280,12 +280,6 @@ void build_ntt_tables(HostTables& t) {
   t.ntt_twf.assign((size_t)NP * tsz * 2, 0);
   t.ntt_twi.assign((size_t)NP * tsz * 2, 0);
   t.ntt_ghat.assign((size_t)NP * L * 2, 0);
-  // the same stencil at 52 bits for the four-prime convolution of FP32 rows (|Y| < 2^117)
-  constexpr int QB4 = 52;
-  std::vector<int64_t> G4((size_t)M);
-  for (int64_t j = 0; j < M; ++j) G4[j] = std::llround(std::ldexp(t.g[j], QB4 - eg));
-  t.ntt_c_gscale4 = t.c * std::ldexp(1.0, eg - QB4);
-  t.ntt_ghat4.assign((size_t)(NP - 1) * L * 2, 0);
   for (int q = 0; q < NP; ++q) {
     const uint64_t p = kNttPrime[q];
     const uint64_t w = powmod(kNttGen[q], (p - 1) / (uint64_t)L, p), wi = powmod(w, p - 2, p);
@@ -312,7 +306,7 @@ void build_ntt_tables(HostTables& t) {
       }
     }
     // circulant embedding of the stencil: c_0 = G_0, c_j = c_{L-j} = G_j (1 <= j < M); its spectrum in
-    // bit-reversed order times L^-1, for the 58-bit stencil and (first four primes) the 52-bit one
+    // bit-reversed order times L^-1
     auto res = [&](int64_t x) { int64_t m = x % (int64_t)p; return (uint64_t)(m < 0 ? m + (int64_t)p : m); };
     const uint64_t Linv = powmod((uint64_t)L % p, p - 2, p);
     auto spectrum = [&](const std::vector<int64_t>& Gq, std::vector<uint32_t>& out) {
@@ -330,10 +324,9 @@ void build_ntt_tables(HostTables& t) {
       }
     };
     spectrum(G, t.ntt_ghat);
-    if (q < NP - 1) spectrum(G4, t.ntt_ghat4);
   }
-  // Garner constants p_a^-1 mod p_b (a < b) in the order (0,1) (0,2) (0,3) (0,4) (1,2) (1,3) (1,4) (2,3) (2,4) (3,4),
-  // each with its Shoup companion floor(c 2^32 / p_b)
+  // Garner constants p_a^-1 mod p_b (a < b) in the order (0,1) (0,2) (0,3) (1,2) (1,3) (2,3), each with its
+  // Shoup companion floor(c 2^32 / p_b)
   int o = 0;
   for (int a = 0; a < NP - 1; ++a)
     for (int bq = a + 1; bq < NP; ++bq) {

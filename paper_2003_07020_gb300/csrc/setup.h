@@ -43,13 +43,11 @@ struct HostTables {
   std::vector<double> tau_eig_nat;  // c * sigma_j, j = 1..M, stored at j - 1
   bool tau_ok = false;
   // exact integer Toeplitz product (NTT matvec): per prime q, interleaved (value, Shoup companion)
-  std::vector<uint32_t> ntt_twf;    // [5][ntt_tw_size][2]: pass-ordered powers of w_q (kernels.h)
-  std::vector<uint32_t> ntt_twi;    // [5][ntt_tw_size][2]: the same for w_q^-1
-  std::vector<uint32_t> ntt_ghat;   // [5][L][2]: NTT of the quantised stencil embedding, bit-reversed, times L^-1
-  uint32_t ntt_crt[20] = {0};       // Garner constants and their Shoup companions (see ntt.cu)
+  std::vector<uint32_t> ntt_twf;    // [4][ntt_tw_size][2]: pass-ordered powers of w_q (kernels.h)
+  std::vector<uint32_t> ntt_twi;    // [4][ntt_tw_size][2]: the same for w_q^-1
+  std::vector<uint32_t> ntt_ghat;   // [4][L][2]: NTT of the quantised stencil embedding, bit-reversed, times L^-1
+  uint32_t ntt_crt[12] = {0};       // Garner constants and their Shoup companions (see ntt.cu)
   double ntt_c_gscale = 0;          // c 2^(e_g - 58): G_j = round(g_j 2^(58 - e_g))
-  std::vector<uint32_t> ntt_ghat4;  // [4][L][2]: the same for the 52-bit stencil and the first four primes
-  double ntt_c_gscale4 = 0;         // c 2^(e_g - 52)
 };
 
 // Builds the NTT matvec tables of t (after build_tables); primes and generators are

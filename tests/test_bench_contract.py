@@ -19,12 +19,12 @@ import bench  # noqa: E402
 
 
 def test_ntt_butterflies_per_row():
-    # 5 primes x (forward + inverse) radix-2 NTT of the embedding length L (the smallest power of
+    # 4 primes x (forward + inverse) radix-2 NTT of the embedding length L (the smallest power of
     # two >= 2M, at least 4): L/2 butterflies per stage, log2 L stages
-    assert bench.ntt_butterflies(8191, 1) == 5 * 2 * 8192 * 14
-    assert bench.ntt_butterflies(8191, 1024) == 1024 * 5 * 2 * 8192 * 14
-    assert bench.ntt_butterflies(1, 1) == 5 * 2 * 2 * 2
-    assert bench.ntt_butterflies(4097, 1) == 5 * 2 * 8192 * 14  # 2M = 8194 -> L = 16384
+    assert bench.ntt_butterflies(8191, 1) == 4 * 2 * 8192 * 14
+    assert bench.ntt_butterflies(8191, 1024) == 1024 * 4 * 2 * 8192 * 14
+    assert bench.ntt_butterflies(1, 1) == 4 * 2 * 2 * 2
+    assert bench.ntt_butterflies(4097, 1) == 4 * 2 * 8192 * 14  # 2M = 8194 -> L = 16384
 
 
 def test_fft64_matvec_flops_per_row():
