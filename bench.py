@@ -251,13 +251,13 @@ FP64_PEAK_TFLOPS = 2 * 1.60 * 152 * 2.07e9 / 1e12
 # Nt rows moves Nt times this.
 MATVEC_DRAM_BYTES_PER_ROW_M8191 = 17.018e6 / 128
 # The same for the exact-integer (NTT) matvec of the Arnoldi steps (FP32 input, 10 of the 11 matvecs of a
-# solve): ntt_quant_f32_kernel + ntt_conv_kernel (5 primes) + ntt_epilogue_kernel<float> read
-# 4.20 + 10.61 + 25.18 MB and write 0 per 128-row launch triple (one ncu capture at M = 8191, Nt = 128; the
-# FP64-input residual matvec reads 8.40 + 10.61 + 37.76 MB).
-NTT_DRAM_BYTES_PER_ROW_M8191 = (4.200e6 + 10.613e6 + 25.181e6) / 128
-# DRAM bytes of cocg_reg_kernel<Strang spectra> per shifted system at M = 8191 (13.21 MB read + 5 KB
+# solve): ntt_quant_f32_kernel<58> + ntt_conv_kernel (4 primes) + ntt_epilogue_kernel<float, 4> (with the fused
+# first CGS2 pass against 4 basis vectors) read 4.20 + 10.17 + 46.68 MB and write 0 per 128-row launch triple
+# (one ncu capture at M = 8191, Nt = 128).
+NTT_DRAM_BYTES_PER_ROW_M8191 = (4.200e6 + 10.171e6 + 46.684e6) / 128
+# DRAM bytes of cocg_reg_kernel<Strang spectra> per shifted system at M = 8191 (13.21 MB read + 21 KB
 # written for 65 systems, one ncu capture at M = 8191, Nt = 128): the per-system spectrum and tables.
-COCG_DRAM_BYTES_PER_SYSTEM_M8191 = (13.215e6 + 0.005e6) / 65
+COCG_DRAM_BYTES_PER_SYSTEM_M8191 = (13.211e6 + 0.021e6) / 65
 # Lazy Shoup butterfly issue rate measured on GB300 (dependent-chain probe): 6.27 per clock per SM.
 NTT_PEAK_GBFLY = 6.27 * 152 * 2.07
 
@@ -931,8 +931,23 @@ def run_batched(args):
         barrier()
         dt = time.perf_counter() - t0
     dt = max_over_ranks(dt, world, dev)
-    launches = sum(n for p in plans for _, n in p.get_profile(reset=True).values())
-    # for comparison: the same instances solved one after another on one stream (one pass)
+    prof_timed = {}
+    for p in plans:
+        for k, (_, nl) in p.get_profile(reset=True).items():
+            prof_timed[k] = prof_timed.get(k, 0) + nl
+    launches = sum(prof_timed.values())
+    # for comparison: the concurrent-streams schedule (one host thread per instance, up to 32) ...
+    for U in Us:
+        U.zero_()
+    aao.solve_batched(plans, Fs, Us, max_workers=32)
+    barrier()
+    t2 = time.perf_counter()
+    for U in Us:
+        U.zero_()
+    aao.solve_batched(plans, Fs, Us, max_workers=32)
+    barrier()
+    t_streams = time.perf_counter() - t2
+    # ... and the same instances solved one after another on one stream (one pass)
     for U in Us:
         U.zero_()
     barrier()
@@ -959,12 +974,17 @@ def run_batched(args):
             "dtype": "f64+f32" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": "batched: 64 independent 1D instances, M in {511,1023,2047,4095}, Nt in "
                                    "{128,256,512,1024}, alpha~U(1.1,1.9), kappa~U(0.5,2), TRR<=1e-10 each; one step "
-                                   "= one aao_solve_batched call (concurrent streams); wall-clock timing",
+                                   "= one aao_solve_batched call (lockstep cycles, one Step (b) launch per Arnoldi "
+                                   "step for all instances); wall-clock timing",
                        "instances": 64, "unknowns_per_step": unknowns, "precision": args.prec,
+                       "step_b_launches_per_step": prof_timed.get("cocg", 0) // max(args.steps, 1),
+                       "stage_launches_per_step": {k: v // max(args.steps, 1) for k, v in prof_timed.items()},
+                       "concurrent_streams_ms": round(1e3 * t_streams, 2),
                        "one_by_one_ms": round(1e3 * t_seq, 2),
                        "outer_iters_max": max(i["outer_iters"] for i in infos),
                        "true_rel_res_max": max(i["true_rel_res"] for i in infos),
-                       "fgmres_cycles": "CUDA graph per restart cycle",
+                       "fgmres_cycles": "lockstep host-driven steps, device Givens (the concurrent-streams and "
+                                        "one-by-one comparisons replay CUDA graphs per cycle)",
                        "cocg_threads_by_M": {str(m): t for m, t in sorted({(p.M, p.cocg_threads) for p in plans})},
                        "stage_ms_sum_over_streams_profiled_step": {k: round(v[0], 3) for k, v in prof.items()}},
             "gpu_launches": launches, "clocks": clk.summary()}

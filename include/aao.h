@@ -270,14 +270,24 @@ aao_status aao_solve_windows(aao_plan* plan, int n_windows, const double* u0_dev
 
 /*
  * Solves n independent problems (different M, Nt, alpha, kappa, precision)
- * concurrently on the current device: each plan runs aao_gmres_solve on its
- * own non-blocking stream (created for the call; the plan's stream is
- * restored afterwards) from a pool of max_workers host threads (<= 0: 32),
- * largest problems first, so that the kernels of small problems overlap and
- * fill the GPU (the batched workload of many instances).  F[i], U[i]: device
- * vectors of plans[i]'s shape; U[i] is the initial guess on entry.  infos
- * (may be NULL) receives n results.  Returns AAO_OK if every solve did, else
- * the first failing status (the other solves still complete).
+ * at once on the current device.  F[i], U[i]: device vectors of plans[i]'s
+ * shape; U[i] is the initial guess on entry.  infos (may be NULL) receives
+ * n results.  Returns AAO_OK if every solve did, else the first failing
+ * status (the other solves still complete).  Two schedules:
+ *   - max_workers <= 0 and plans that are all 1D AAO_PREC_MIXED with the
+ *     register-resident Step (b) (M <= 8192, AAO_INNER_STRANG or
+ *     AAO_INNER_TAU of one kind, the same restart length, no warm start,
+ *     recording, profiling or poly_m): the restart cycles of all instances
+ *     run in lockstep, each instance's Steps (a), (c), matvec and CGS2 on its
+ *     own stream and the shifted solves of ALL instances as ONE kernel launch
+ *     per Arnoldi step (a work list of (instance, system) pairs, the CTA size
+ *     the largest of the plans' cocg_threads; results equal single solves
+ *     when every plan has that CTA size); Givens rotations on the device, one
+ *     host synchronisation per step;
+ *   - otherwise (or max_workers > 0): each plan runs aao_gmres_solve on its
+ *     own non-blocking stream from a pool of max_workers host threads (<= 0:
+ *     32), largest problems first.
+ * Each plan's stream is synchronised first and restored afterwards.
  */
 aao_status aao_solve_batched(int n, aao_plan* const* plans, const double* const* F, double* const* U,
                              aao_info* infos, int max_workers);

@@ -399,7 +399,9 @@ class Fno:
 
 
 def solve_batched(plans, Fs, Us, max_workers=0, raise_on_error=True):
-    """aao_solve_batched: all problems concurrently; returns the list of info dicts."""
+    """aao_solve_batched: all problems at once; returns the list of info dicts.  max_workers <= 0: lockstep
+    restart cycles with one Step (b) launch per Arnoldi step for all instances (when the plans allow it);
+    max_workers > 0: one stream per instance driven by that many host threads."""
     n = len(plans)
     P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
     Fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])

@@ -184,6 +184,161 @@ __device__ __forceinline__ float2 zval(const float2* buf, const CocgTables32& tb
   else return buf[pad16(i)];
 }
 
+// One shifted system n: right-hand side in xb[n] on entry, COCG solution there on exit (x0b: learned
+// initial guesses when WARM).  buf, q, pt: the CTA's FFT buffer and twiddle tables for logL; red: the block
+// reduction scratch.  Starts and ends synchronised.
+template <int KIND, bool WARM, int NT>
+__device__ __forceinline__ void cocg_reg_solve(int n, float2* __restrict__ xb, const float2* __restrict__ x0b, int M,
+                                               int logL, const CocgTables32& tb, float tol, int maxit,
+                                               int* __restrict__ iters, int* __restrict__ flags, float2* buf,
+                                               const float2* q, const float2* pt, float* red) {
+  const int t = threadIdx.x;
+  const double2 lamd = tb.lambda[n];
+  const float2 lam{(float)lamd.x, (float)lamd.y};
+  float2* x = xb + (size_t)n * M;
+  const float2* sc = KIND == 2 ? tb.sconv + ((size_t)n << logL) : nullptr;
+  float2 r[kRegElems], p[kRegElems];
+  float nb2[1] = {0};
+#pragma unroll
+  for (int j = 0; j < kRegElems; ++j) {
+    const int i = t + NT * j;
+    r[j] = (i < M) ? x[i] : float2{0, 0};
+    nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+  }
+  block_sum<float, 1>(nb2, red);
+#pragma unroll
+  for (int j = 0; j < kRegElems; ++j) {
+    const int i = t + NT * j;
+    if (i < M) x[i] = float2{0, 0};
+  }
+  if (nb2[0] == 0.0f) {
+    if (t == 0) { iters[n] = 0; flags[n] = 0; }
+    return;
+  }
+  const float thr = tol * tol * nb2[0];
+  int accepted = 0;
+  if constexpr (WARM) {
+    // warm start: r0 = b - (lambda I + c T) x0, kept only if ||r0|| < ||b||
+    const float2* x0 = x0b + (size_t)n * M;
+    float2 w[kRegElems];
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      w[j] = (i < M) ? x0[i] : float2{0, 0};
+    }
+    toeplitz_reg<NT>(buf, w, M, logL, tb, q, pt);
+    float r02[1] = {0};
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) {
+        const float2 rj = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
+        r02[0] += rj.x * rj.x + rj.y * rj.y;
+      }
+    }
+    block_sum<float, 1>(r02, red);
+    if (r02[0] < nb2[0]) {  // uniform across the block
+      accepted = 1;
+#pragma unroll
+      for (int j = 0; j < kRegElems; ++j) {
+        const int i = t + NT * j;
+        if (i < M) {
+          r[j] = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
+          x[i] = w[j];
+        }
+      }
+      if (r02[0] <= thr) {
+        if (t == 0) { iters[n] = 0; flags[n] = 4; }
+        __syncthreads();
+        return;
+      }
+    }
+    __syncthreads();
+  }
+  // z = P^{-1} r, p = z, rho = r^T z
+  precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
+  float rho2[4] = {0, 0, 0, 0};  // r^T z, |z|^2, |r|^2
+#pragma unroll
+  for (int j = 0; j < kRegElems; ++j) {
+    const int i = t + NT * j;
+    float2 z{0, 0};
+    if (i < M) z = zval<KIND>(buf, tb, i);
+    p[j] = z;
+    rho2[0] += r[j].x * z.x - r[j].y * z.y;
+    rho2[1] += r[j].x * z.y + r[j].y * z.x;
+    rho2[2] += z.x * z.x + z.y * z.y;
+    rho2[3] += r[j].x * r[j].x + r[j].y * r[j].y;
+  }
+  block_sum<float, 4>(rho2, red);
+  float2 rho{rho2[0], rho2[1]};
+  int it = 0, flag = 1;
+  const bool bd0 = near_breakdown(rho2[0], rho2[1], rho2[2], rho2[3]);  // z^T r of the first step
+  if (bd0) flag = 2;
+  while (!bd0 && it < maxit) {
+    // q = (lambda I + c T) p
+    toeplitz_reg<NT>(buf, p, M, logL, tb, q, pt);
+    float pq2[4] = {0, 0, 0, 0};  // p^T q, |p|^2, |q|^2
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) {
+        const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
+        pq2[0] += p[j].x * qq.x - p[j].y * qq.y;
+        pq2[1] += p[j].x * qq.y + p[j].y * qq.x;
+        pq2[2] += p[j].x * p[j].x + p[j].y * p[j].y;
+        pq2[3] += qq.x * qq.x + qq.y * qq.y;
+      }
+    }
+    block_sum<float, 4>(pq2, red);
+    const float2 pq{pq2[0], pq2[1]};
+    if (near_breakdown(pq2[0], pq2[1], pq2[2], pq2[3])) { flag = 2; break; }
+    const float2 a = cdiv(rho, pq);
+    float rr[1] = {0};
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) {
+        const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
+        x[i] = cadd(x[i], cmul(a, p[j]));
+        r[j] = csub(r[j], cmul(a, qq));
+        rr[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+      }
+    }
+    block_sum<float, 1>(rr, red);
+    ++it;
+    if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
+    if (rr[0] <= thr) { flag = 0; break; }
+    precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
+    float rn2[3] = {0, 0, 0};  // r^T z, |z|^2
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      if (i < M) {
+        const float2 z = zval<KIND>(buf, tb, i);
+        rn2[0] += r[j].x * z.x - r[j].y * z.y;
+        rn2[1] += r[j].x * z.y + r[j].y * z.x;
+        rn2[2] += z.x * z.x + z.y * z.y;
+      }
+    }
+    block_sum<float, 3>(rn2, red);
+    const float2 rho_new{rn2[0], rn2[1]};
+    // rho_new divides the next beta: |r^T z| at rounding level of ||r|| ||z|| is a breakdown
+    if (near_breakdown(rn2[0], rn2[1], rn2[2], rr[0])) { flag = 2; break; }
+    const float2 beta = cdiv(rho_new, rho);
+    rho = rho_new;
+#pragma unroll
+    for (int j = 0; j < kRegElems; ++j) {
+      const int i = t + NT * j;
+      float2 z{0, 0};
+      if (i < M) z = zval<KIND>(buf, tb, i);
+      p[j] = cadd(z, cmul(beta, p[j]));
+    }
+    __syncthreads();
+  }
+  if (t == 0) { iters[n] = it; flags[n] = flag | (accepted << 2); }
+  __syncthreads();
+}
+
 template <int KIND, bool WARM, int NT>
 __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
     cocg_reg_kernel(float2* __restrict__ xb, const float2* __restrict__ x0b, int M, int logL, int nsys,
@@ -194,156 +349,31 @@ __global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
   float2* q = buf + padded_size(1 << logL);
   float2* pt = q + (1 << logL) / 4;  // per-pass twiddle tables
   const int L = 1 << logL;
-  const int t = threadIdx.x;
   load_quarter(q, tb.twL, L / 4);
   __syncthreads();
   build_pass_tables(pt, q, logL, logL);
-  for (int n = blockIdx.x; n < nsys; n += gridDim.x) {
-    const double2 lamd = tb.lambda[n];
-    const float2 lam{(float)lamd.x, (float)lamd.y};
-    float2* x = xb + (size_t)n * M;
-    const float2* sc = KIND == 2 ? tb.sconv + ((size_t)n << logL) : nullptr;
-    float2 r[kRegElems], p[kRegElems];
-    float nb2[1] = {0};
-#pragma unroll
-    for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + NT * j;
-      r[j] = (i < M) ? x[i] : float2{0, 0};
-      nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
-    }
-    block_sum<float, 1>(nb2, red);
-#pragma unroll
-    for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + NT * j;
-      if (i < M) x[i] = float2{0, 0};
-    }
-    if (nb2[0] == 0.0f) {
-      if (t == 0) { iters[n] = 0; flags[n] = 0; }
-      continue;
-    }
-    const float thr = tol * tol * nb2[0];
-    int accepted = 0;
-    if constexpr (WARM) {
-      // warm start: r0 = b - (lambda I + c T) x0, kept only if ||r0|| < ||b||
-      const float2* x0 = x0b + (size_t)n * M;
-      float2 w[kRegElems];
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        w[j] = (i < M) ? x0[i] : float2{0, 0};
-      }
-      toeplitz_reg<NT>(buf, w, M, logL, tb, q, pt);
-      float r02[1] = {0};
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        if (i < M) {
-          const float2 rj = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
-          r02[0] += rj.x * rj.x + rj.y * rj.y;
-        }
-      }
-      block_sum<float, 1>(r02, red);
-      if (r02[0] < nb2[0]) {  // uniform across the block
-        accepted = 1;
-#pragma unroll
-        for (int j = 0; j < kRegElems; ++j) {
-          const int i = t + NT * j;
-          if (i < M) {
-            r[j] = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
-            x[i] = w[j];
-          }
-        }
-        if (r02[0] <= thr) {
-          if (t == 0) { iters[n] = 0; flags[n] = 4; }
-          __syncthreads();
-          continue;
-        }
-      }
-      __syncthreads();
-    }
-    // z = P^{-1} r, p = z, rho = r^T z
-    precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
-    float rho2[4] = {0, 0, 0, 0};  // r^T z, |z|^2, |r|^2
-#pragma unroll
-    for (int j = 0; j < kRegElems; ++j) {
-      const int i = t + NT * j;
-      float2 z{0, 0};
-      if (i < M) z = zval<KIND>(buf, tb, i);
-      p[j] = z;
-      rho2[0] += r[j].x * z.x - r[j].y * z.y;
-      rho2[1] += r[j].x * z.y + r[j].y * z.x;
-      rho2[2] += z.x * z.x + z.y * z.y;
-      rho2[3] += r[j].x * r[j].x + r[j].y * r[j].y;
-    }
-    block_sum<float, 4>(rho2, red);
-    float2 rho{rho2[0], rho2[1]};
-    int it = 0, flag = 1;
-    const bool bd0 = near_breakdown(rho2[0], rho2[1], rho2[2], rho2[3]);  // z^T r of the first step
-    if (bd0) flag = 2;
-    while (!bd0 && it < maxit) {
-      // q = (lambda I + c T) p
-      toeplitz_reg<NT>(buf, p, M, logL, tb, q, pt);
-      float pq2[4] = {0, 0, 0, 0};  // p^T q, |p|^2, |q|^2
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        if (i < M) {
-          const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
-          pq2[0] += p[j].x * qq.x - p[j].y * qq.y;
-          pq2[1] += p[j].x * qq.y + p[j].y * qq.x;
-          pq2[2] += p[j].x * p[j].x + p[j].y * p[j].y;
-          pq2[3] += qq.x * qq.x + qq.y * qq.y;
-        }
-      }
-      block_sum<float, 4>(pq2, red);
-      const float2 pq{pq2[0], pq2[1]};
-      if (near_breakdown(pq2[0], pq2[1], pq2[2], pq2[3])) { flag = 2; break; }
-      const float2 a = cdiv(rho, pq);
-      float rr[1] = {0};
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        if (i < M) {
-          const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
-          x[i] = cadd(x[i], cmul(a, p[j]));
-          r[j] = csub(r[j], cmul(a, qq));
-          rr[0] += r[j].x * r[j].x + r[j].y * r[j].y;
-        }
-      }
-      block_sum<float, 1>(rr, red);
-      ++it;
-      if (!(rr[0] == rr[0]) || rr[0] > 1e30f * nb2[0]) { flag = 3; break; }
-      if (rr[0] <= thr) { flag = 0; break; }
-      precond_reg<KIND, NT>(buf, r, M, logL, lam, tb, q, pt, sc);
-      float rn2[3] = {0, 0, 0};  // r^T z, |z|^2
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        if (i < M) {
-          const float2 z = zval<KIND>(buf, tb, i);
-          rn2[0] += r[j].x * z.x - r[j].y * z.y;
-          rn2[1] += r[j].x * z.y + r[j].y * z.x;
-          rn2[2] += z.x * z.x + z.y * z.y;
-        }
-      }
-      block_sum<float, 3>(rn2, red);
-      const float2 rho_new{rn2[0], rn2[1]};
-      // rho_new divides the next beta: |r^T z| at rounding level of ||r|| ||z|| is a breakdown
-      if (near_breakdown(rn2[0], rn2[1], rn2[2], rr[0])) { flag = 2; break; }
-      const float2 beta = cdiv(rho_new, rho);
-      rho = rho_new;
-#pragma unroll
-      for (int j = 0; j < kRegElems; ++j) {
-        const int i = t + NT * j;
-        float2 z{0, 0};
-        if (i < M) z = zval<KIND>(buf, tb, i);
-        p[j] = cadd(z, cmul(beta, p[j]));
-      }
-      __syncthreads();
-    }
-    if (t == 0) { iters[n] = it; flags[n] = flag | (accepted << 2); }
-    __syncthreads();
-  }
+  for (int n = blockIdx.x; n < nsys; n += gridDim.x)
+    cocg_reg_solve<KIND, WARM, NT>(n, xb, x0b, M, logL, tb, tol, maxit, iters, flags, buf, q, pt, red);
+}
+
+// Step (b) of many independent problems in one launch: CTA b solves system work[b].y of instance work[b].x
+// (its sizes, tables, tolerance and buffers in insts[work[b].x]), with the same per-system code as
+// cocg_reg_kernel.  Shared memory for the largest instance.
+template <int KIND, int NT>
+__global__ void __launch_bounds__(NT, kRegMaxThreads / NT)
+    cocg_reg_batched_kernel(const CocgBatchInst* __restrict__ insts, const int2* __restrict__ work) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ float red[4 * 32];
+  const int2 w = work[blockIdx.x];
+  const CocgBatchInst I = insts[w.x];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* q = buf + padded_size(1 << I.logL);
+  float2* pt = q + (1 << I.logL) / 4;
+  load_quarter(q, I.tb.twL, (1 << I.logL) / 4);
+  __syncthreads();
+  build_pass_tables(pt, q, I.logL, I.logL);
+  cocg_reg_solve<KIND, false, NT>(w.y, I.xb, nullptr, I.M, I.logL, I.tb, I.tol, I.maxit, I.iters, I.flags, buf, q,
+                                  pt, red);
 }
 
 template <typename R>

@@ -64,6 +64,22 @@ struct CocgTables64 {
   const double* seig;
   const double* taueig_br;
 };
+// One instance of a batched Step (b) launch (launch_cocg_batched): its right-hand sides / solutions
+// xb ([nsys][M] complex), sizes, tables (Strang spectra or tau eigenvalues), tolerance and statistics.
+struct CocgBatchInst {
+  float2* xb;
+  int M, logL, nsys;
+  CocgTables32 tb;
+  float tol;
+  int maxit;
+  int* iters;
+  int* flags;
+};
+// Step (b) of several instances in ONE launch: CTA b solves system work[b].y of instance work[b].x with
+// the register-resident COCG of CTA size nt (>= every instance's minimum; kind 1 = tau, 2 = Strang spectra).
+// insts, work: device arrays; nwork CTAs; smem_logL: the largest instance's logL.
+cudaError_t launch_cocg_batched(const CocgBatchInst* insts, const int2* work, int nwork, int kind, int nt,
+                                int smem_logL, cudaStream_t s);
 // xb: [nsys][M] complex, right-hand sides on entry, solutions on exit.
 // rws, pws: [nsys][M] complex workspace.  gbuf: global FFT scratch used when
 // the transform does not fit in shared memory (may be null otherwise).

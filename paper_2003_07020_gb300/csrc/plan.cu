@@ -69,7 +69,8 @@ struct GmresDevState {
 };
 
 // Start of a cycle: g = (beta, 0, ...), beta^2 = *beta2 from the residual reduction; enables step 0.
-__global__ void cycle_init_kernel(GmresDevState* d, const double* beta2, int m, cudaGraphConditionalHandle h) {
+__global__ void cycle_init_kernel(GmresDevState* d, const double* beta2, int m, cudaGraphConditionalHandle h,
+                                  int set_cond) {
   if (threadIdx.x != 0) return;
   const double beta = sqrt(*beta2);
   for (int i = 0; i <= m; ++i) d->g[i] = 0.0;
@@ -78,7 +79,7 @@ __global__ void cycle_init_kernel(GmresDevState* d, const double* beta2, int m, 
   d->jdone = 0;
   d->active = 1;
   d->status = 0;
-  cudaGraphSetConditional(h, 1u);
+  if (set_cond) cudaGraphSetConditional(h, 1u);
 }
 
 // Column j of H from the two Gram-Schmidt passes (hd[i] + hd[65 + i], norm^2 in hd[130]),
@@ -448,21 +449,23 @@ aao_status cocg2d_any(aao_plan* p, void* spec) {
   a.G2 = (const C*)p->G2d;
   if (p->direct) {
     prof_begin(p);
-    cudaError_t e = sizeof(R) == 4 ? aao::launch_tau2d_direct_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream)
-                                   : aao::launch_tau2d_direct_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, p->stream);
+    cudaError_t e;
+    if constexpr (sizeof(R) == 4) e = aao::launch_tau2d_direct_f32(a, p->stream);
+    else e = aao::launch_tau2d_direct_f64(a, p->stream);
     if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("tau2d direct: ") + cudaGetErrorString(e));
     prof_end(p, ST_COCG, 4);
     return AAO_OK;
   }
   auto capture = [&](cudaStream_t cs) {
-    return sizeof(R) == 4 ? aao::capture_cocg2d_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, cs, p->cap3)
-                          : aao::capture_cocg2d_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, cs, p->cap3);
+    if constexpr (sizeof(R) == 4) return aao::capture_cocg2d_f32(a, cs, p->cap3);
+    else return aao::capture_cocg2d_f64(a, cs, p->cap3);
   };
   if (p->prof_on) {  // host-driven iterations, so that every launch can be counted and timed
     int its = 0;
     prof_begin(p);
-    cudaError_t e = sizeof(R) == 4 ? aao::launch_cocg2d_f32(*(const aao::Cocg2dArgs<float>*)(const void*)&a, p->stream, &its)
-                                   : aao::launch_cocg2d_f64(*(const aao::Cocg2dArgs<double>*)(const void*)&a, p->stream, &its);
+    cudaError_t e;
+    if constexpr (sizeof(R) == 4) e = aao::launch_cocg2d_f32(a, p->stream, &its);
+    else e = aao::launch_cocg2d_f64(a, p->stream, &its);
     if (e != cudaSuccess) return fail(p, AAO_ECUDA, std::string("cocg2d: ") + cudaGetErrorString(e));
     prof_end(p, ST_COCG, 7 + its * 9);
     return AAO_OK;
@@ -574,14 +577,14 @@ aao_status precond_any(aao_plan* p, const double* v, void* out, int out_kind, bo
   return AAO_OK;
 }
 
+aao_status arnoldi_orthogonalise(aao_plan* p, int j);
+
 // One Arnoldi step j of FGMRES (Sec. 4): z_j = P^{-1} v_j (Steps (a)-(c)), COCG statistics
 // (into p->stats, or accumulated into acc), w = calA z_j, and CGS2 against v_0..v_j:
 // h1 = V^T w (p->hdev), w -= V h1, h2 = V^T w (p->hdev + 65), w -= V h2, ||w||^2 (p->hdev[130]).
 aao_status arnoldi_step(aao_plan* p, int j, GmresDevState* acc) {
   const size_t n = p->n;
-  const int nb = aao::blas_partial_blocks();
   double* vj = p->V + (size_t)j * n;
-  double* w = p->V + (size_t)(j + 1) * n;
   void* zj = p->mixed ? (void*)((float*)p->Z + (size_t)j * n) : (void*)((double*)p->Z + (size_t)j * n);
   TRY(precond_any(p, vj, zj, p->mixed ? 0 : 1, p->mixed));
   if (acc)
@@ -590,6 +593,16 @@ aao_status arnoldi_step(aao_plan* p, int j, GmresDevState* acc) {
   else
     LAUNCH(ST_VEC, 1, (iter_stats_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->stats),
                        cudaGetLastError()));
+  return arnoldi_orthogonalise(p, j);
+}
+
+// The rest of Arnoldi step j after z_j = P^{-1} v_j: w = calA z_j and CGS2 against v_0..v_j,
+// h1 = V^T w (p->hdev), w -= V h1, h2 = V^T w (p->hdev + 65), w -= V h2, ||w||^2 (p->hdev[130]).
+aao_status arnoldi_orthogonalise(aao_plan* p, int j) {
+  const size_t n = p->n;
+  const int nb = aao::blas_partial_blocks();
+  double* w = p->V + (size_t)(j + 1) * n;
+  void* zj = p->mixed ? (void*)((float*)p->Z + (size_t)j * n) : (void*)((double*)p->Z + (size_t)j * n);
   const int nv = j + 1;
   if (p->mixed) {  // float-float basis: w = A z_j into W (FP64), CGS2 writes v_{j+1} as float-float
     const float2* Vf = (const float2*)(const void*)p->V;
@@ -631,8 +644,8 @@ void release_cycle_graph(aao_plan* p) {
 // then the least-squares solve.  Each IF node has its own handle, reset to 0 at every launch;
 // the init kernel enables step 0 and step j's Givens kernel enables step j + 1.  Kernels are
 // recorded on plan-owned capture streams.
-aao_status build_cycle_graph(aao_plan* p) {
-  release_cycle_graph(p);
+// The device FGMRES state (and its pinned host mirror) of the graph-driven and batched cycles.
+aao_status ensure_dev_state(aao_plan* p) {
   if (!p->gd) {
     TRY(dalloc(p, &p->gd, 1));
     if (cudaMallocHost(&p->gd_host, sizeof(GmresDevState)) != cudaSuccess) {
@@ -640,6 +653,12 @@ aao_status build_cycle_graph(aao_plan* p) {
       return fail(p, AAO_ENOMEM, "cudaMallocHost failed");
     }
   }
+  return AAO_OK;
+}
+
+aao_status build_cycle_graph(aao_plan* p) {
+  release_cycle_graph(p);
+  TRY(ensure_dev_state(p));
   if (!p->cap1) {
     CK(cudaStreamCreateWithFlags(&p->cap1, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking));
@@ -665,7 +684,7 @@ aao_status build_cycle_graph(aao_plan* p) {
     for (int j = 0; ok && j < m; ++j)
       ok = check(cudaGraphConditionalHandleCreate(&hs[j], g, 0, cudaGraphCondAssignDefault), "conditional handle");
     if (ok) {
-      cycle_init_kernel<<<1, 1, 0, p->cap1>>>(p->gd, p->hdev, m, hs[0]);
+      cycle_init_kernel<<<1, 1, 0, p->cap1>>>(p->gd, p->hdev, m, hs[0], 1);
       ok = check(cudaGetLastError(), "cycle init") &&
            check(p->mixed ? aao::launch_scale_to_ff((float2*)(void*)p->V, p->W, &p->gd->inv_beta, 0.0, n, p->cap1)
                           : aao::launch_scale_dev(p->V, p->V, &p->gd->inv_beta, n, p->cap1),
@@ -1559,12 +1578,321 @@ aao_status aao_solve_windows(aao_plan* p, int n_windows, const double* u0, const
 #include <atomic>
 #include <thread>
 
+namespace {
+
+// The lockstep batched solver needs plans whose Step (b) is the register-resident COCG with the same kind
+// (Strang spectra or tau), the same restart length and no per-plan extras (warm start, recording, P(m)).
+int lockstep_kind(int n, aao_plan* const* plans) {
+  int kind = 0;
+  for (int i = 0; i < n; ++i) {
+    const aao_plan* p = plans[i];
+    const int k = (p->opts.inner == AAO_INNER_TAU) ? 1 : (p->opts.inner == AAO_INNER_STRANG && p->sconv ? 2 : 0);
+    if (p->dim != 1 || !p->mixed || p->cocg_threads == 0 || p->direct || p->fno || p->rec_cap > p->rec_count ||
+        p->prof_on || p->opts.poly_m != 0 || p->m != plans[0]->m || k == 0 || (kind && k != kind))
+      return 0;
+    kind = k;
+  }
+  return kind;
+}
+
+struct LockstepInst {
+  aao_plan* p;
+  const double* F;
+  double* U;
+  cudaStream_t own, saved;
+  cudaEvent_t ev;
+  double nF = 0;
+  bool zero_guess = false, done = false, in_cycle = false;
+  aao_status st = AAO_ENOCONV;
+  aao_info inf{};
+};
+
+// Restarted FGMRES of all instances in lockstep: every Arnoldi step runs Steps (a) and (c), the matvec and
+// CGS2 of each active instance on its own stream, and Step (b) of all of them as ONE launch
+// (launch_cocg_batched) on the first instance's stream, joined by events.  Givens rotations stay on the
+// device (one FGMRES state per plan); the host reads every active instance's state once per step.
+aao_status solve_lockstep(int n, aao_plan* const* plans, const double* const* F, double* const* U, aao_info* infos,
+                          int kind) {
+  std::vector<LockstepInst> L(n);
+  aao_status result = AAO_OK;
+  std::string err;
+  auto cleanup = [&]() {
+    for (auto& x : L) {
+      if (x.own) {
+        cudaStreamSynchronize(x.own);
+        cudaStreamDestroy(x.own);
+      }
+      if (x.ev) cudaEventDestroy(x.ev);
+      if (x.p) x.p->stream = x.saved;
+    }
+  };
+  int nt = 64, max_logL = 0, total_sys = 0;
+  for (int i = 0; i < n; ++i) {
+    L[i].p = plans[i];
+    L[i].F = F[i];
+    L[i].U = U[i];
+    L[i].saved = plans[i]->stream;
+    cudaStreamSynchronize(L[i].saved);  // the caller's pending work on the plan's stream comes first
+    if (cudaStreamCreateWithFlags(&L[i].own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L[i].ev, cudaEventDisableTiming) != cudaSuccess) {
+      cleanup();
+      return fail(nullptr, AAO_ECUDA, "stream or event creation failed");
+    }
+    plans[i]->stream = L[i].own;
+    if (ensure_dev_state(plans[i]) != AAO_OK) {
+      err = plans[i]->err;
+      cleanup();
+      return fail(nullptr, AAO_ENOMEM, err);
+    }
+    nt = std::max(nt, plans[i]->cocg_threads);
+    max_logL = std::max(max_logL, plans[i]->logL);
+    total_sys += plans[i]->nsys;
+  }
+  aao_plan* p0 = plans[0];
+  cudaStream_t master = L[0].own;
+  cudaEvent_t ev_cocg = nullptr;
+  aao::CocgBatchInst* insts_d = nullptr;
+  int2* work_d = nullptr;
+  int2* work_h = nullptr;
+  auto release = [&]() {
+    if (ev_cocg) cudaEventDestroy(ev_cocg);
+    if (insts_d) cudaFree(insts_d);
+    if (work_d) cudaFree(work_d);
+    if (work_h) cudaFreeHost(work_h);
+    cleanup();
+  };
+#define LS_CK(call, what)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      release();                                                                               \
+      return fail(nullptr, AAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_));     \
+    }                                                                                          \
+  } while (0)
+#define LS_TRY(i, call)                                                                        \
+  do {                                                                                         \
+    aao_status s_ = (call);                                                                    \
+    if (s_ != AAO_OK) {                                                                        \
+      err = "instance " + std::to_string(i) + ": " + L[i].p->err;                             \
+      release();                                                                               \
+      return fail(nullptr, s_, err);                                                           \
+    }                                                                                          \
+  } while (0)
+  LS_CK(cudaEventCreateWithFlags(&ev_cocg, cudaEventDisableTiming), "event");
+  LS_CK(cudaMalloc(&insts_d, (size_t)n * sizeof(aao::CocgBatchInst)), "cudaMalloc");
+  LS_CK(cudaMalloc(&work_d, (size_t)std::max(total_sys, 1) * sizeof(int2)), "cudaMalloc");
+  LS_CK(cudaMallocHost(&work_h, (size_t)std::max(total_sys, 1) * sizeof(int2)), "cudaMallocHost");
+  {
+    std::vector<aao::CocgBatchInst> h(n);
+    for (int i = 0; i < n; ++i) {
+      aao_plan* p = plans[i];
+      h[i].xb = (float2*)p->spec;
+      h[i].M = p->M;
+      h[i].logL = p->logL;
+      h[i].nsys = p->nsys;
+      h[i].tb = aao::CocgTables32{p->twL32, p->Ebr32, p->lambda, p->chirp32, p->chat32, p->seig32, p->tau32, p->sconv};
+      h[i].tol = (float)p->opts.inner_tol;
+      h[i].maxit = p->opts.inner_maxit;
+      h[i].iters = p->iters;
+      h[i].flags = p->flags;
+    }
+    LS_CK(cudaMemcpyAsync(insts_d, h.data(), (size_t)n * sizeof(aao::CocgBatchInst), cudaMemcpyHostToDevice, master),
+          "descriptor upload");
+    LS_CK(cudaStreamSynchronize(master), "descriptor upload");
+  }
+  // ||F||^2 and ||U||^2 of every instance (as aao_gmres_solve)
+  const int nb = aao::blas_partial_blocks();
+  for (int i = 0; i < n; ++i) {
+    aao_plan* p = L[i].p;
+    LS_CK(aao::launch_dots(F[i], F[i], 0, 1, p->n, p->partial, p->stream), "norms");
+    LS_CK(aao::launch_dots(U[i], U[i], 0, 1, p->n, p->partial + nb, p->stream), "norms");
+    LS_CK(aao::launch_reduce_partials(p->partial, nb, 1, p->hdev, p->stream), "norms");
+    LS_CK(aao::launch_reduce_partials(p->partial + nb, nb, 1, p->hdev + 1, p->stream), "norms");
+    LS_CK(cudaMemcpyAsync(p->pinned, p->hdev, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream), "norms");
+    p->prof_launches[ST_VEC] += 4;
+  }
+  for (int i = 0; i < n; ++i) {
+    aao_plan* p = L[i].p;
+    LS_CK(cudaStreamSynchronize(p->stream), "norms");
+    L[i].nF = std::sqrt(p->pinned[0]);
+    L[i].zero_guess = p->pinned[1] == 0.0;
+    if (!std::isfinite(L[i].nF)) {
+      L[i].done = true;
+      L[i].st = AAO_ENONFINITE;
+      p->err = "non-finite right-hand side";
+    } else if (L[i].nF == 0.0) {
+      LS_CK(cudaMemsetAsync(U[i], 0, p->n * sizeof(double), p->stream), "memset");
+      L[i].done = true;
+      L[i].st = AAO_OK;
+    } else {
+      GmresDevState& hs = *p->gd_host;
+      const size_t tail = sizeof(GmresDevState) - offsetof(GmresDevState, thr);
+      std::memset(&hs.thr, 0, tail);
+      hs.thr = 0.5 * p->opts.tol * L[i].nF;
+      LS_CK(cudaMemcpyAsync(&p->gd->thr, &hs.thr, tail, cudaMemcpyHostToDevice, p->stream), "state upload");
+    }
+  }
+  const size_t tail = sizeof(GmresDevState) - offsetof(GmresDevState, thr);
+  const int m = p0->m;
+  for (int cycle = 0; cycle <= p0->opts.max_cycles; ++cycle) {
+    // residuals r0 = F - calA U (or F) and beta of every unfinished instance
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      if (L[i].done) continue;
+      aao_plan* p = L[i].p;
+      if (cycle == 0 && L[i].zero_guess) {
+        LS_CK(cudaMemcpyAsync(p->W, F[i], p->n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream), "copy");
+        p->pinned[0] = L[i].nF * L[i].nF;
+      } else {
+        LS_TRY(i, matvec_any(p, U[i], false, F[i], p->W, p->sq));
+        L[i].inf.matvecs++;
+        p->prof_launches[ST_VEC] += 1;
+        LS_CK(aao::launch_reduce_partials(p->sq, (int)p->nsq, 1, p->hdev, p->stream), "reduce");
+        LS_CK(cudaMemcpyAsync(p->pinned, p->hdev, sizeof(double), cudaMemcpyDeviceToHost, p->stream), "readback");
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      if (L[i].done) continue;
+      aao_plan* p = L[i].p;
+      LS_CK(cudaStreamSynchronize(p->stream), "residual");
+      const double beta = std::sqrt(p->pinned[0]);
+      L[i].in_cycle = false;
+      if (!std::isfinite(beta)) {
+        L[i].done = true;
+        L[i].st = AAO_ENONFINITE;
+        p->err = "non-finite residual";
+        continue;
+      }
+      L[i].inf.true_rel_res = beta / L[i].nF;
+      L[i].inf.cycles = cycle;
+      if (L[i].inf.true_rel_res <= p->opts.tol) {
+        L[i].done = true;
+        L[i].st = AAO_OK;
+        continue;
+      }
+      if (cycle == p0->opts.max_cycles) {
+        L[i].done = true;
+        L[i].st = AAO_ENOCONV;
+        p->err = "FGMRES did not reach the tolerance within max_cycles";
+        continue;
+      }
+      L[i].in_cycle = true;
+      any = true;
+      cycle_init_kernel<<<1, 1, 0, p->stream>>>(p->gd, p->hdev, m, 0, 0);
+      LS_CK(cudaGetLastError(), "cycle init");
+      LS_CK(aao::launch_scale_to_ff((float2*)(void*)p->V, p->W, &p->gd->inv_beta, 0.0, p->n, p->stream), "scale");
+      p->prof_launches[ST_VEC] += 2;
+    }
+    if (!any) break;
+    for (int j = 0; j < m; ++j) {
+      // Step (a) of every instance still in its cycle, then Step (b) of all of them in one launch
+      int nwork = 0;
+      for (int i = 0; i < n; ++i) {
+        if (!L[i].in_cycle) continue;
+        aao_plan* p = L[i].p;
+        const float2* vj = (const float2*)(const void*)(p->V + (size_t)j * p->n);
+        LS_CK(aao::launch_tdft_fwd_f32_ff(vj, (float2*)p->spec, p->M, p->Nt, p->sfwd32, p->twNt32, p->stream),
+              "Step (a)");
+        p->prof_launches[ST_TDFT_FWD] += 1;
+        LS_CK(cudaEventRecord(L[i].ev, p->stream), "event");
+        LS_CK(cudaStreamWaitEvent(master, L[i].ev, 0), "event wait");
+        for (int q = 0; q < p->nsys; ++q) work_h[nwork++] = make_int2(i, q);
+      }
+      if (nwork == 0) break;
+      LS_CK(cudaMemcpyAsync(work_d, work_h, (size_t)nwork * sizeof(int2), cudaMemcpyHostToDevice, master),
+            "work upload");
+      LS_CK(aao::launch_cocg_batched(insts_d, work_d, nwork, kind, nt, max_logL, master), "Step (b)");
+      p0->prof_launches[ST_COCG] += 1;
+      LS_CK(cudaEventRecord(ev_cocg, master), "event");
+      // Step (c), the matvec and CGS2 of each, the Givens update on the device
+      for (int i = 0; i < n; ++i) {
+        if (!L[i].in_cycle) continue;
+        aao_plan* p = L[i].p;
+        LS_CK(cudaStreamWaitEvent(p->stream, ev_cocg, 0), "event wait");
+        iter_stats_accum_kernel<<<1, 256, 0, p->stream>>>(p->iters, p->flags, p->nsys, p->gd);
+        LS_CK(cudaGetLastError(), "stats");
+        float* zj = (float*)p->Z + (size_t)j * p->n;
+        LS_CK(aao::launch_tdft_inv_f32((const float2*)p->spec, zj, p->M, p->Nt, p->sinv32, p->twNt32, p->stream),
+              "Step (c)");
+        p->prof_launches[ST_TDFT_INV] += 1;
+        p->prof_launches[ST_VEC] += 1;
+        LS_TRY(i, arnoldi_orthogonalise(p, j));
+        L[i].inf.matvecs++;
+        givens_kernel<<<1, 1, 0, p->stream>>>(p->gd, p->hdev, j, m, 0, 0);
+        LS_CK(cudaGetLastError(), "Givens");
+        float2* w = (float2*)(void*)(p->V + (size_t)(j + 1) * p->n);
+        LS_CK(aao::launch_scale_ff(w, &p->gd->inv_hn, 0.0, p->n, p->stream), "scale");
+        p->prof_launches[ST_VEC] += 2;
+        LS_CK(cudaMemcpyAsync(&p->gd_host->thr, &p->gd->thr, tail, cudaMemcpyDeviceToHost, p->stream), "readback");
+      }
+      if (j + 1 == m) break;
+      for (int i = 0; i < n; ++i) {
+        if (!L[i].in_cycle) continue;
+        LS_CK(cudaStreamSynchronize(L[i].p->stream), "step");
+        if (!L[i].p->gd_host->active) L[i].in_cycle = false;
+      }
+    }
+    // end of the cycle: least squares and U += Z y for every instance that ran steps
+    for (int i = 0; i < n; ++i) {
+      if (L[i].done) continue;
+      aao_plan* p = L[i].p;
+      lsq_kernel<<<1, 1, 0, p->stream>>>(p->gd);
+      LS_CK(cudaGetLastError(), "least squares");
+      LS_CK(cudaMemcpyAsync(&p->gd_host->thr, &p->gd->thr, tail, cudaMemcpyDeviceToHost, p->stream), "readback");
+      LS_CK(cudaStreamSynchronize(p->stream), "cycle");
+      p->prof_launches[ST_VEC] += 1;
+      GmresDevState& hs = *p->gd_host;
+      if (hs.status != 0) {
+        L[i].done = true;
+        L[i].st = (aao_status)hs.status;
+        p->err = L[i].st == AAO_EBREAKDOWN ? "GMRES breakdown" : "non-finite Arnoldi vector";
+        continue;
+      }
+      if (hs.jdone > 0) {
+        LS_CK(aao::launch_zy_update_f32(U[i], (const float*)p->Z, p->n, hs.jdone, p->n, p->gd->y, p->stream),
+              "update");
+        p->prof_launches[ST_VEC] += 1;
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    aao_plan* p = L[i].p;
+    LS_CK(cudaStreamSynchronize(p->stream), "final");
+    GmresDevState& hs = *p->gd_host;
+    aao_info& inf = L[i].inf;
+    if (p->gd && L[i].nF > 0 && std::isfinite(L[i].nF)) {
+      inf.outer_iters = hs.outer_total;
+      inf.inner_iters_max = hs.inner_max;
+      inf.inner_iters_sum = hs.inner_sum;
+      inf.warm_accepted = hs.accepted;
+      if (hs.flag_max != 0)
+        inf.status_detail = hs.flag_max == 1 ? AAO_ENOCONV : (hs.flag_max == 2 ? AAO_EBREAKDOWN : AAO_ENONFINITE);
+    }
+    if (infos) infos[i] = inf;
+    if (L[i].st != AAO_OK && result == AAO_OK) {
+      result = L[i].st;
+      err = "instance " + std::to_string(i) + ": " + p->err;
+    }
+  }
+  release();
+#undef LS_CK
+#undef LS_TRY
+  if (result != AAO_OK) return fail(nullptr, result, err);
+  return AAO_OK;
+}
+
+}  // namespace
+
 extern "C" aao_status aao_solve_batched(int n, aao_plan* const* plans, const double* const* F, double* const* U,
                                         aao_info* infos, int max_workers) {
   if (n < 0 || (n > 0 && (!plans || !F || !U))) return fail(nullptr, AAO_EINVAL, "bad batched arguments");
   if (n == 0) return AAO_OK;
   for (int i = 0; i < n; ++i)
     if (!plans[i] || !F[i] || !U[i]) return fail(nullptr, AAO_EINVAL, "null plan or vector in the batch");
+  if (max_workers <= 0) {
+    const int kind = lockstep_kind(n, plans);
+    if (kind) return solve_lockstep(n, plans, F, U, infos, kind);
+  }
   // one non-blocking stream per instance so that the instances' kernels overlap on the GPU
   std::vector<cudaStream_t> saved(n), own(n, nullptr);
   for (int i = 0; i < n; ++i) {
