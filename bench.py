@@ -182,10 +182,25 @@ def cpu_baseline(M, Nt):
     n_steps = 64
     t_lu, t_step = time_oracle_sample(M, Nt, 1.8, n_steps)
     total = t_lu + Nt * t_step
-    return {"value": M * Nt / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": ("sequential BDF2 (numpy/scipy FP64, dense LU) at M=%d, alpha=1.8: LU of both step "
-                       "matrices %.2f s + %d of %d time steps at %.4f s each; value = M*Nt / (LU + Nt*step)"
-                       % (M, t_lu, n_steps, Nt, t_step))}
+    out = {"value": M * Nt / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": ("sequential BDF2 (numpy/scipy FP64, dense LU) at M=%d, alpha=1.8: LU of both step "
+                      "matrices %.2f s + %d of %d time steps at %.4f s each; value = M*Nt / (LU + Nt*step)"
+                      % (M, t_lu, n_steps, Nt, t_step))}
+    # the same sample on one core: a fresh interpreter with the BLAS thread pools limited to one thread
+    import subprocess
+    import sys
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; print(json.dumps(bench.time_oracle_sample(%d, %d, 1.8, %d)))" % (M, Nt, n_steps))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600,
+                           cwd=os.path.dirname(os.path.abspath(__file__)))
+        t1_lu, t1_step = json.loads(r.stdout.strip().splitlines()[-1])
+        out["single_core"] = {"value": M * Nt / (t1_lu + Nt * t1_step), "unit": UNIT, "cores": 1,
+                              "sample": "the same sample with OMP/OpenBLAS threads = 1: LU %.2f s, step %.4f s"
+                                        % (t1_lu, t1_step)}
+    except Exception as e:  # the all-core figure stands on its own
+        out["single_core"] = {"unavailable": "%s" % type(e).__name__}
+    return out
 
 
 def run_reference(args):

@@ -263,9 +263,10 @@ def test_training_lowers_loss_and_warm_start_solves_exactly():
         plan.close()
     print("inner iterations per application: cold %.1f warm %.1f, accepted %d" % (cold_it, warm_it, accepted))
     assert accepted > 0
-    # what the trained model gains (measured: about 2% fewer COCG iterations at this size); it must not cost
-    # iterations beyond run-to-run noise of the training (float atomics in the weight-gradient sums)
-    assert warm_it <= 1.05 * cold_it, (warm_it, cold_it)
+    # what the trained model gains: strictly fewer COCG iterations than the same solves from x0 = 0 (measured:
+    # about 2 % fewer at this size, 0.4 % at M = 1023, Nt = 256; the FNO kernels are deterministic, so this
+    # fails exactly when the trained model stops helping).  Its wall-time cost is larger than that gain.
+    assert warm_it < cold_it, (warm_it, cold_it)
     net.close()
 
 
