@@ -381,8 +381,9 @@ def comparison_arms(args, plans, Fs, rank, dev, barrier):
     out = {}
 
     def summary(ms, infos, m, nt):
+        its = [i["outer_iters"] for i in infos]
         return {"value": m * nt / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                "outer_iters": [i["outer_iters"] for i in infos],
+                "outer_iters": its if len(its) <= 6 else [min(its), max(its)],
                 "true_rel_res_max": max(i["true_rel_res"] for i in infos)}
 
     arms = [("plain_fp64", dict(prec=aao.AAO_PREC_FP64)),
