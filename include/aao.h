@@ -306,6 +306,19 @@ aao_status aao_plan_set_profiling(aao_plan* plan, int on);
 aao_status aao_plan_get_profile(aao_plan* plan, double* ms, int64_t* launches, int reset);
 
 /*
+ * Per-system record of the most recent Step (b) (Sec. 3.1: the Nt/2 + 1
+ * shifted solves (lambda_n I - tau K) x_n = y_n of one preconditioner
+ * application, n = 0 .. Nt/2).  n_sys must equal Nt/2 + 1.  iters_host[n]
+ * receives the inner iterations of system n (0 for the direct tau solve),
+ * flags_host[n] its outcome: 0 converged, 1 iteration cap reached,
+ * 2 breakdown (|u^T w| at rounding level of ||u|| ||w|| for a COCG divisor),
+ * 3 non-finite values, plus 4 when the learned warm start was accepted.
+ * Either pointer may be null.  Synchronises the plan's stream; AAO_EINVAL
+ * for a bad n_sys.
+ */
+aao_status aao_plan_get_inner_record(aao_plan* plan, int n_sys, int* iters_host, int* flags_host);
+
+/*
  * The preconditioner apply of aao_bc_precond_apply (mixed precision only)
  * without a plan and without any device allocation.  The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc, e.g. code

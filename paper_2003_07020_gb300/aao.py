@@ -29,7 +29,8 @@ EXPORTED = ("aao_default_opts", "aao_setup_coeffs", "aao_plan_create", "aao_plan
             "aao_fno_num_params", "aao_fno_create", "aao_fno_destroy", "aao_fno_set_params",
             "aao_fno_get_params", "aao_fno_save", "aao_fno_load", "aao_fno_predict", "aao_fno_loss_grad",
             "aao_fno_train_step", "aao_fno_train", "aao_plan_set_warm_start", "aao_plan_record_pairs",
-            "aao_plan_recorded_pairs", "aao_plan_get_tuning", "aao_bicgstab_solve", "aao_solve_windows")
+            "aao_plan_recorded_pairs", "aao_plan_get_tuning", "aao_bicgstab_solve", "aao_solve_windows",
+            "aao_plan_get_inner_record")
 STAGES = ("matvec", "tdft_fwd", "cocg", "tdft_inv", "vector", "fno")
 
 
@@ -111,6 +112,7 @@ def load():
     lib.aao_plan_record_pairs.argtypes = [vp, i64, vp, vp, vp]
     lib.aao_plan_recorded_pairs.argtypes = [vp, ctypes.POINTER(i64)]
     lib.aao_plan_get_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.aao_plan_get_inner_record.argtypes = [vp, ctypes.c_int, vp, vp]
     for name in EXPORTED:
         if name not in ("aao_default_opts", "aao_plan_workspace_bytes", "aao_last_error", "aao_fno_num_params"):
             getattr(lib, name).restype = ctypes.c_int
@@ -194,6 +196,16 @@ class Plan:
         v = ctypes.c_int()
         _check(load().aao_plan_get_tuning(self.handle, ctypes.byref(v)), self.handle)
         return v.value
+
+    def inner_record(self):
+        """(iterations, flags) of each shifted system in the most recent Step (b), as int32 arrays of
+        Nt/2 + 1 entries (flags: 0 converged, 1 cap, 2 breakdown, 3 non-finite, + 4 warm start accepted)."""
+        n = self.Nt // 2 + 1
+        it = np.zeros(n, dtype=np.int32)
+        fl = np.zeros(n, dtype=np.int32)
+        _check(load().aao_plan_get_inner_record(self.handle, n, it.ctypes.data_as(ctypes.c_void_p),
+                                                fl.ctypes.data_as(ctypes.c_void_p)), self.handle)
+        return it, fl
 
     def _vec(self, t, name):
         if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):

@@ -198,23 +198,34 @@ __device__ __forceinline__ void cocg_reg_solve(int n, float2* __restrict__ xb, c
   float2* x = xb + (size_t)n * M;
   const float2* sc = KIND == 2 ? tb.sconv + ((size_t)n << logL) : nullptr;
   float2 r[kRegElems], p[kRegElems];
-  float nb2[1] = {0};
+  // The iteration runs on b / ||b||_1 (x stays in the units of b): COCG is scale invariant, and the
+  // normalised vectors keep the squared norms and the breakdown products far from FP32 underflow even
+  // when b is at rounding level (a frequency that Step (a) cancels).
+  float b1[1] = {0};
 #pragma unroll
   for (int j = 0; j < kRegElems; ++j) {
     const int i = t + NT * j;
     r[j] = (i < M) ? x[i] : float2{0, 0};
-    nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+    b1[0] += fabsf(r[j].x) + fabsf(r[j].y);
   }
-  block_sum<float, 1>(nb2, red);
+  block_sum<float, 1>(b1, red);
 #pragma unroll
   for (int j = 0; j < kRegElems; ++j) {
     const int i = t + NT * j;
     if (i < M) x[i] = float2{0, 0};
   }
-  if (nb2[0] == 0.0f) {
-    if (t == 0) { iters[n] = 0; flags[n] = 0; }
+  if (!(b1[0] > 0.0f) || b1[0] > 3.0e38f) {  // zero right-hand side, or NaN / infinity in it
+    if (t == 0) { iters[n] = 0; flags[n] = b1[0] == 0.0f ? 0 : 3; }
     return;
   }
+  const float bs = b1[0], ibs = 1.0f / bs;
+  float nb2[1] = {0};
+#pragma unroll
+  for (int j = 0; j < kRegElems; ++j) {
+    r[j] = float2{r[j].x * ibs, r[j].y * ibs};
+    nb2[0] += r[j].x * r[j].x + r[j].y * r[j].y;
+  }
+  block_sum<float, 1>(nb2, red);
   const float thr = tol * tol * nb2[0];
   int accepted = 0;
   if constexpr (WARM) {
@@ -224,7 +235,7 @@ __device__ __forceinline__ void cocg_reg_solve(int n, float2* __restrict__ xb, c
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
-      w[j] = (i < M) ? x0[i] : float2{0, 0};
+      w[j] = (i < M) ? float2{x0[i].x * ibs, x0[i].y * ibs} : float2{0, 0};
     }
     toeplitz_reg<NT>(buf, w, M, logL, tb, q, pt);
     float r02[1] = {0};
@@ -244,7 +255,7 @@ __device__ __forceinline__ void cocg_reg_solve(int n, float2* __restrict__ xb, c
         const int i = t + NT * j;
         if (i < M) {
           r[j] = csub(r[j], cadd(buf[pad16(i)], cmul(lam, w[j])));
-          x[i] = w[j];
+          x[i] = x0[i];
         }
       }
       if (r02[0] <= thr) {
@@ -293,13 +304,14 @@ __device__ __forceinline__ void cocg_reg_solve(int n, float2* __restrict__ xb, c
     const float2 pq{pq2[0], pq2[1]};
     if (near_breakdown(pq2[0], pq2[1], pq2[2], pq2[3])) { flag = 2; break; }
     const float2 a = cdiv(rho, pq);
+    const float2 ax{a.x * bs, a.y * bs};  // the step in the units of b
     float rr[1] = {0};
 #pragma unroll
     for (int j = 0; j < kRegElems; ++j) {
       const int i = t + NT * j;
       if (i < M) {
         const float2 qq = cadd(buf[pad16(i)], cmul(lam, p[j]));
-        x[i] = cadd(x[i], cmul(a, p[j]));
+        x[i] = cadd(x[i], cmul(ax, p[j]));
         r[j] = csub(r[j], cmul(a, qq));
         rr[0] += r[j].x * r[j].x + r[j].y * r[j].y;
       }

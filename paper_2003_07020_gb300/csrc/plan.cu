@@ -1149,7 +1149,9 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
   TRYP(dalloc(p, &p->iters, (size_t)p->nsys));
   TRYP(dalloc(p, &p->flags, (size_t)p->nsys));
   TRYP(dalloc(p, &p->stats, 4));
-  if (cudaMemset(p->stats, 0, 4 * sizeof(int)) != cudaSuccess) {
+  if (cudaMemset(p->stats, 0, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(p->iters, 0, (size_t)p->nsys * sizeof(int)) != cudaSuccess ||
+      cudaMemset(p->flags, 0, (size_t)p->nsys * sizeof(int)) != cudaSuccess) {
     p->err = "cudaMemset failed";
     return bail(AAO_ECUDA);
   }
@@ -1194,6 +1196,15 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
 aao_status aao_plan_get_tuning(const aao_plan* p, int* cocg_threads) {
   if (!p || !cocg_threads) return fail(nullptr, AAO_EINVAL, "null argument");
   *cocg_threads = p->cocg_threads;
+  return AAO_OK;
+}
+
+aao_status aao_plan_get_inner_record(aao_plan* p, int n_sys, int* iters_host, int* flags_host) {
+  if (!p) return fail(nullptr, AAO_EINVAL, "null plan");
+  if (n_sys != p->nsys) return fail(p, AAO_EINVAL, "n_sys must be Nt/2 + 1");
+  CK(cudaStreamSynchronize(p->stream));
+  if (iters_host) CK(cudaMemcpy(iters_host, p->iters, sizeof(int) * n_sys, cudaMemcpyDeviceToHost));
+  if (flags_host) CK(cudaMemcpy(flags_host, p->flags, sizeof(int) * n_sys, cudaMemcpyDeviceToHost));
   return AAO_OK;
 }
 

@@ -11,7 +11,9 @@ Tolerances (stated per check below):
     Step (c) multiplies time row k by eps^{-k/Nt}, so any relative error of
     the FP32 spectrum (inner tolerance plus FP32 rounding, u32 = 2^-24) is
     amplified up to cond(V_eps) = 1/eps (the conditioning of V_eps noted
-    after Eq. 1.6b);
+    after Eq. 1.6b); and, system by system, the residual of every shifted
+    system (lambda_n I - tau K) x_n = y_n recovered through exact FP64
+    Steps (a)/(c) is at most t + 16 u32 ||A_n|| ||x_n|| / ||y_n||;
   * solve: true relative residual <= 1e-10 (computed by the oracle) and
     ||U - U_seq|| / ||U_seq|| <= 1e-10 (FP64 path) or 1e-9 (mixed path).
 """
@@ -121,6 +123,45 @@ def test_precond_mixed_residual(M, Nt, alpha, inner):
     err = rel(host(z), zr)
     bound = 4 * (1e-6 + 64 * 2.0 ** -24) / eps
     assert err <= bound, (err, bound, rel(oprec.P_eps_matvec(K, tau, eps, host(z)), v))
+
+
+@pytest.mark.parametrize("M,Nt,alpha", PREC_CASES + [(255, 128, 1.8), (511, 256, 1.5)])
+@pytest.mark.parametrize("inner", [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU])
+def test_precond_mixed_residual_of_every_shifted_system(M, Nt, alpha, inner):
+    # Step (b) seen system by system.  Inverting the GPU's Step (c) exactly (in FP64: Step (a) of z is
+    # the spectrum x_n that Step (c) received) and applying Step (a) exactly to v gives, for every
+    # frequency n, the residual of the shifted system (lambda_n I - tau K) x_n = y_n (Sec. 3.1).  FP32
+    # COCG stops at ||r|| <= t ||y_n|| on its recurrence residual, t = 1e-6; the true residual differs by
+    # the FP32 rounding of the recurrence, modelled as gamma u32 kappa_n with kappa_n =
+    # ||A_n|| ||x_n|| / ||y_n|| (A_n is normal: ||A_n|| = max_j |lambda_n - tau mu_j(K)|) and
+    # gamma = 16, which covers a root-sum-square accumulation sqrt(k log2 L) of up to k = 18
+    # iterations at L = 2^14.  A Step (b) defect of 1e-4 fails this on the well-conditioned systems.
+    if inner == aao.AAO_INNER_TAU and (M + 1) & M:
+        pytest.skip("tau preconditioner needs M+1 a power of two")
+    v = workloads.random_vector(Nt, M, seed=4)
+    tau = 1.0 / Nt
+    eps = mixed_eps(tau)
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED, inner=inner) as plan:
+        z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z)
+        its, flags = plan.inner_record()
+    assert (flags == 0).all(), flags
+    K = jac(M, alpha)
+    mu = np.linalg.eigvalsh(K)
+    lam = oprec.eigenvalues_C_eps(Nt, eps)
+    Y = oprec.time_dft_half(v, eps)
+    X = oprec.time_dft_half(host(z), eps)
+    u32, t, gamma = 2.0 ** -24, 1e-6, 16.0
+    worst = 0.0
+    for n in range(Nt // 2 + 1):
+        A = lam[n] * np.eye(M) - tau * K
+        ny = np.linalg.norm(Y[n])
+        res = np.linalg.norm(Y[n] - A @ X[n]) / ny
+        kappa = np.abs(lam[n] - tau * mu).max() * np.linalg.norm(X[n]) / ny
+        bound = t + gamma * u32 * kappa
+        worst = max(worst, res / bound)
+        assert res <= bound, (n, res, bound, its[n])
+    assert worst > 0.01, worst  # the check is not vacuous
 
 
 def test_precond_aliasing_allowed():
@@ -308,13 +349,10 @@ def test_largest_accepted_nt_solves_and_the_next_is_rejected(prec, nt_max):
     assert e.value.status == aao.AAO_EINVAL and "at most %d" % nt_max in str(e.value)
 
 
-@pytest.mark.parametrize("prec", [aao.AAO_PREC_MIXED, aao.AAO_PREC_FP64])
-def test_cocg_breakdown_is_detected_and_fgmres_still_converges(prec):
-    # A crafted right-hand side whose frequency-1 shifted system has b^T A^{-1} b = 0 (complex b): at
-    # M = 2 the Strang circulant equals T, so COCG's first rho = r^T z = b^T A^{-1} b vanishes up to
-    # rounding.  The relative breakdown test (|u^T w| <= 64 u ||u|| ||w||) must report it
-    # (status_detail = AAO_EBREAKDOWN), and flexible GMRES absorbs the failed inner solve.
-    Nt, M, alpha = 8, 2, 1.5
+def breakdown_rhs(prec, Nt=8, M=2, alpha=1.5):
+    """A crafted right-hand side whose frequency-1 shifted system has b^T A^{-1} b = 0 (complex b): at
+    M = 2 the Strang circulant equals T, so COCG's first rho = r^T z = b^T A^{-1} b vanishes up to
+    rounding.  Returns (F, eps)."""
     tau = 1.0 / Nt
     c = tau / (1.0 / (M + 1)) ** alpha
     eps = mixed_eps(tau) if prec == aao.AAO_PREC_MIXED else oprec.default_eps(tau)
@@ -327,6 +365,16 @@ def test_cocg_breakdown_is_detected_and_fgmres_still_converges(prec):
     zh = oprec.time_dft_half(F, eps)  # Step (a) gives b at n = 1 and zero elsewhere
     np.testing.assert_allclose(zh[1], b, atol=1e-12)
     assert np.abs(np.delete(zh, 1, axis=0)).max() < 1e-12
+    return F, eps
+
+
+@pytest.mark.parametrize("prec", [aao.AAO_PREC_MIXED, aao.AAO_PREC_FP64])
+def test_cocg_breakdown_is_detected_and_fgmres_still_converges(prec):
+    # The relative breakdown test (|u^T w| <= 64 u ||u|| ||w||) must report the crafted breakdown
+    # (status_detail = AAO_EBREAKDOWN), and flexible GMRES absorbs the failed inner solve.
+    Nt, M, alpha = 8, 2, 1.5
+    tau = 1.0 / Nt
+    F, eps = breakdown_rhs(prec, Nt, M, alpha)
     with aao.Plan(M, Nt, alpha, prec=prec, inner=aao.AAO_INNER_STRANG, matvec=aao.AAO_MATVEC_FFT64) as plan:
         U = torch.zeros((Nt, M), dtype=torch.float64, device=DEV)
         info = plan.gmres_solve(cu(F), U)
@@ -335,3 +383,59 @@ def test_cocg_breakdown_is_detected_and_fgmres_still_converges(prec):
     assert oaao.true_relative_residual(K, tau, F, host(U)) <= 1e-10, info
     np.testing.assert_allclose(host(U), np.linalg.solve(oaao.assemble_all_at_once(K, Nt, tau), F.ravel()).reshape(Nt, M),
                                rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [aao.AAO_PREC_MIXED, aao.AAO_PREC_FP64])
+def test_inner_record_names_the_system_that_broke_down(prec):
+    # Step (a) of the crafted right-hand side is nonzero at frequency 1 only (elsewhere it is zero or at
+    # rounding level): the record of one preconditioner application shows a breakdown there and
+    # convergence everywhere else (at most M = 2 iterations; none for an exactly zero right-hand side).
+    Nt, M, alpha = 8, 2, 1.5
+    F, _ = breakdown_rhs(prec, Nt, M, alpha)
+    with aao.Plan(M, Nt, alpha, prec=prec, inner=aao.AAO_INNER_STRANG, matvec=aao.AAO_MATVEC_FFT64) as plan:
+        z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(F), z)
+        it, fl = plan.inner_record()
+    assert it.shape == (Nt // 2 + 1,) and fl[1] == 2, (it, fl)
+    assert (np.delete(fl, 1) == 0).all() and (np.delete(it, 1) <= M).all(), (it, fl)
+
+
+def test_tiny_right_hand_side_is_no_breakdown():
+    # COCG is scale invariant: a right-hand side of 1e-17 N(0, 1) entries (squares near the FP32 underflow
+    # threshold) converges like any other and gives z = 1e-17 P_eps^{-1} v' (the mixed path normalises
+    # each shifted system's right-hand side by its 1-norm before the iteration).
+    Nt, M, alpha = 8, 2, 1.5
+    v = workloads.random_vector(Nt, M, seed=7)
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED, matvec=aao.AAO_MATVEC_FFT64) as plan:
+        z1 = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z1)
+        z2 = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(1e-17 * v), z2)
+        it, fl = plan.inner_record()
+    assert (fl == 0).all() and (it >= 1).all(), (it, fl)
+    assert rel(1e17 * host(z2), host(z1)) <= 1e-5, rel(1e17 * host(z2), host(z1))
+
+
+@pytest.mark.parametrize("inner", [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU, aao.AAO_INNER_TAU_DIRECT])
+def test_inner_record_of_a_generic_apply(inner):
+    M, Nt, alpha = 255, 32, 1.8
+    v = workloads.random_vector(Nt, M, seed=6)
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED, inner=inner) as plan:
+        z = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.bc_precond_apply(cu(v), z)
+        it, fl = plan.inner_record()
+        with pytest.raises(aao.AaoError):
+            record_with_wrong_count(plan)
+    assert (fl == 0).all(), fl
+    if inner == aao.AAO_INNER_TAU_DIRECT:
+        assert (it == 0).all(), it
+    else:
+        assert it.min() >= 1 and it.max() <= 200, it
+
+
+def record_with_wrong_count(plan):
+    import ctypes
+    n = plan.Nt // 2
+    buf = np.zeros(n + 1, dtype=np.int32)
+    aao._check(aao.load().aao_plan_get_inner_record(plan.handle, n, buf.ctypes.data_as(ctypes.c_void_p), None),
+               plan.handle)
