@@ -623,11 +623,13 @@ def run_ours(args):
               else cocg2d_flops(M, My, inner_sum, n_apply, nsys, args.inner)) / max(n_apply, 1)
         pkv = FP32_PEAK_TFLOPS if args.prec == "mixed" else FP64_PEAK_TFLOPS
         achieved = fl / (t_launch * 1e-3) / 1e12
+        tm = reg and plans[0].cocg_threads == aao.AAO_COCG_TMEM  # the tensor-memory kernel
         traffic = (COCG_DRAM_BYTES_PER_SYSTEM_M8191 * nsys
-                   if (reg and args.inner == "strang" and M == 8191) else None)
+                   if (reg and not tm and args.inner == "strang" and M == 8191) else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": pkv, "unit": "TFLOP/s", "frac": achieved / pkv,
                 "traffic": traffic,
-                "kernel": ("cocg_reg_kernel" if reg else ("c2d line kernels" if args.dim == 2 else "cocg_kernel")),
+                "kernel": ("cocg_tm_kernel" if tm else "cocg_reg_kernel") if reg else
+                          ("c2d line kernels" if args.dim == 2 else "cocg_kernel"),
                 "peak_source": "FMA issue rate x 152 SMs x 2.07 GHz (derived)",
                 "traffic_source": "ncu dram bytes of a 65-system launch scaled to the systems" if traffic else None}
     else:

@@ -103,6 +103,8 @@ typedef struct {
   double kappa_y;       /* 2D: diffusion coefficient in y */
 } aao_problem;
 
+#define AAO_COCG_TMEM (-1) /* aao_opts.cocg_threads: the Step (b) kernel with its vectors in tensor memory */
+
 /* Solver options.  aao_default_opts fills the defaults given in brackets. */
 typedef struct {
   int restart;          /* FGMRES restart length m [20], 1..64 */
@@ -120,9 +122,12 @@ typedef struct {
                            runs as one graph launch with its WHILE loop, except while profiling) */
   aao_matvec_kind matvec; /* [AAO_MATVEC_NTT] 1D matvec arithmetic; 2D always uses FP64 FFTs */
   int cocg_threads;     /* [0] mixed 1D, M <= 8192: CTA size of the register-resident COCG kernel
-                           (64, 128, 256 or 512, at least M / 16); 0 lets plan creation time the
-                           admissible sizes on the plan's own systems and keep the fastest (cached
-                           per problem shape for the process) */
+                           (64, 128, 256 or 512, at least M / 16), or AAO_COCG_TMEM: the kernel that
+                           keeps the COCG vectors in tensor memory (Strang preconditioner,
+                           4096 < M <= 8191; the learned warm start still runs on the 512-thread
+                           register kernel).  0 picks the tensor-memory kernel where it applies and
+                           otherwise times the admissible sizes on the plan's own systems and keeps
+                           the fastest (cached per problem shape for the process) */
   int poly_m;           /* [0] 0..16: apply the m-step polynomial preconditioner of Sec. 3.1 (the
                            remark after Thm 3.1) instead of P_eps:
                            P(m) v = sum_{k=0}^{m} (P_eps^{-1} S_eps)^k P_eps^{-1} v,
@@ -181,7 +186,7 @@ size_t aao_plan_workspace_bytes(const aao_plan* plan);
 
 /* Launch shapes the plan uses: *cocg_threads = CTA size of the Step (b) kernel
  * (0 where the shared-memory kernel serves: FP64, M > 8192 or 2D). */
-aao_status aao_plan_get_tuning(const aao_plan* plan, int* cocg_threads);
+aao_status aao_plan_get_tuning(const aao_plan* plan, int* cocg_threads);  /* AAO_COCG_TMEM: tensor-memory kernel */
 
 /*
  * Right-hand side of Eq. 12: F_1 = tau f^1 + u^0, F_2 = tau f^2 - u^0/2,

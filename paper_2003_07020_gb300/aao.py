@@ -18,6 +18,7 @@ AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOCONV, AAO_EBREAKDOWN, AAO_ENON
 AAO_PREC_FP64, AAO_PREC_MIXED = 0, 1
 AAO_INNER_STRANG, AAO_INNER_TAU, AAO_INNER_TAU_DIRECT = 0, 1, 2
 AAO_MATVEC_FFT64, AAO_MATVEC_NTT = 0, 1
+AAO_COCG_TMEM = -1  # aao_opts.cocg_threads: the Step (b) kernel with its vectors in tensor memory
 STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA", 4: "AAO_ENOCONV",
                 5: "AAO_EBREAKDOWN", 6: "AAO_ENONFINITE"}
 

@@ -243,6 +243,10 @@ struct aao_plan {
   bool direct = false;     // Step (b) by the direct tau-matrix solve (AAO_INNER_TAU_DIRECT)
   double* polyw = nullptr; // n doubles: right-hand side of a Horner step of P_eps(m) (opts.poly_m > 0)
   float2* sconv = nullptr;  // mixed Strang: per-system spectra of (lambda_n I + c S)^{-1} as L-point circulants
+  // Step (b) by the tensor-memory kernel (cocg_tm.cu): the spectra in the order of its fused pass
+  bool tm = false;
+  float2* sconv_tm = nullptr;
+  float2* Ebr_tm = nullptr;
   // exact-integer matvec (opts.matvec == AAO_MATVEC_NTT, 1D)
   bool ntt = false;
   aao::NttTables ntt_tab{};
@@ -526,6 +530,11 @@ aao_status precond_once(aao_plan* p, const double* v, void* out, int out_kind, b
       if (p->direct)
         LAUNCH(ST_COCG, 1, aao::launch_tau_direct_f32(spec, p->M, p->logL, p->nsys, tb, p->iters, p->flags,
                                                       p->stream));
+      else if (p->tm && !p->fno)
+        LAUNCH(ST_COCG, 1, aao::launch_cocg_tm(spec, p->M, p->logL, p->nsys,
+                                               aao::CocgTmTables{p->twL32, p->Ebr_tm, p->sconv_tm, p->lambda},
+                                               (float)p->opts.inner_tol, p->opts.inner_maxit, p->iters, p->flags,
+                                               p->stream));
       else
         LAUNCH(ST_COCG, 1, aao::launch_cocg_f32(spec, (float2*)p->rws, (float2*)p->pws, p->M, p->logL, p->nsys,
                                                 (int)p->opts.inner, tb, (float)p->opts.inner_tol,
@@ -849,11 +858,14 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   if (o->use_graphs != 0 && o->use_graphs != 1) return fail(nullptr, AAO_EINVAL, "use_graphs must be 0 or 1");
   if (o->matvec != AAO_MATVEC_FFT64 && o->matvec != AAO_MATVEC_NTT) return fail(nullptr, AAO_EINVAL, "bad matvec");
   if (o->cocg_threads != 0 && o->cocg_threads != 64 && o->cocg_threads != 128 && o->cocg_threads != 256 &&
-      o->cocg_threads != 512)
-    return fail(nullptr, AAO_EINVAL, "cocg_threads must be 0, 64, 128, 256 or 512");
-  if (o->cocg_threads != 0 && o->prec == AAO_PREC_MIXED && prob->dim == 1 &&
+      o->cocg_threads != 512 && o->cocg_threads != AAO_COCG_TMEM)
+    return fail(nullptr, AAO_EINVAL, "cocg_threads must be 0, 64, 128, 256, 512 or AAO_COCG_TMEM");
+  if (o->cocg_threads > 0 && o->prec == AAO_PREC_MIXED && prob->dim == 1 &&
       o->cocg_threads < aao::cocg_reg_min_threads((int)prob->M))
     return fail(nullptr, AAO_EINVAL, "cocg_threads must be at least M / 16");
+  if (o->cocg_threads == AAO_COCG_TMEM &&
+      (o->prec != AAO_PREC_MIXED || prob->dim != 1 || o->inner != AAO_INNER_STRANG || prob->M <= 4096))
+    return fail(nullptr, AAO_EINVAL, "AAO_COCG_TMEM needs mixed precision, 1D, the Strang preconditioner and M > 4096");
   return AAO_OK;
 }
 
@@ -1182,9 +1194,31 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     }
   }
   if (opts->poly_m > 0) TRYP(dalloc(p, &p->polyw, p->n));
+  if (p->sconv && aao::cocg_tm_supported(p->M, p->logL) &&
+      (opts->cocg_threads == AAO_COCG_TMEM || opts->cocg_threads == 0)) {
+    // the spectra in the order of the tensor-memory kernel's fused pass: entry s holds L-frequency
+    // tm_order_freq(s), read from the fused order of the register-resident kernel
+    const int L = 1 << p->logL;
+    std::vector<int> from_freq(L), perm(L);
+    for (int f = 0; f < L; ++f) from_freq[aao::fused_to_freq(f, p->logL)] = f;
+    for (int s2 = 0; s2 < L; ++s2) perm[s2] = from_freq[aao::tm_order_freq(s2)];
+    int* dperm = nullptr;
+    TRYP(upload(p, &dperm, perm));
+    TRYP(dalloc(p, &p->sconv_tm, (size_t)p->nsys << p->logL));
+    TRYP(dalloc(p, &p->Ebr_tm, (size_t)L));
+    cudaError_t e = aao::launch_tm_gather(p->sconv, p->sconv_tm, p->Ebr32, p->Ebr_tm, dperm, p->nsys, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+      p->err = std::string("tensor-memory kernel spectra: ") + cudaGetErrorString(e);
+      return bail(AAO_ECUDA);
+    }
+    p->tm = true;
+  }
   if (p->mixed && p->dim == 1 && !p->direct && aao::cocg_reg_min_threads(p->M) > 0) {
-    if (opts->cocg_threads)
+    if (opts->cocg_threads > 0)
       p->cocg_threads = opts->cocg_threads;
+    else if (p->tm)
+      p->cocg_threads = 512;  // the register-resident kernel serves the learned warm start
     else
       TRYP(autotune_cocg_threads(p));
   }
@@ -1195,7 +1229,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
 
 aao_status aao_plan_get_tuning(const aao_plan* p, int* cocg_threads) {
   if (!p || !cocg_threads) return fail(nullptr, AAO_EINVAL, "null argument");
-  *cocg_threads = p->cocg_threads;
+  *cocg_threads = p->tm ? AAO_COCG_TMEM : p->cocg_threads;
   return AAO_OK;
 }
 
@@ -1598,7 +1632,7 @@ int lockstep_kind(int n, aao_plan* const* plans) {
   for (int i = 0; i < n; ++i) {
     const aao_plan* p = plans[i];
     const int k = (p->opts.inner == AAO_INNER_TAU) ? 1 : (p->opts.inner == AAO_INNER_STRANG && p->sconv ? 2 : 0);
-    if (p->dim != 1 || !p->mixed || p->cocg_threads == 0 || p->direct || p->fno || p->rec_cap > p->rec_count ||
+    if (p->dim != 1 || !p->mixed || p->cocg_threads == 0 || p->tm || p->direct || p->fno || p->rec_cap > p->rec_count ||
         p->prof_on || p->opts.poly_m != 0 || p->m != plans[0]->m || k == 0 || (kind && k != kind))
       return 0;
     kind = k;

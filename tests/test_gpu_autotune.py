@@ -38,12 +38,17 @@ def test_every_cta_size_solves_the_same_problem(inner):
 
 
 def test_autotuned_choice_is_admissible_and_cached():
-    for M, lo in ((63, 64), (1023, 64), (2047, 128), (4095, 256), (8191, 512)):
+    for M, lo in ((63, 64), (1023, 64), (2047, 128), (4095, 256)):
         a = aao.Plan(M, 16, 1.5)
         b = aao.Plan(M, 16, 1.7)  # same shape: the cached choice
         assert lo <= a.cocg_threads <= 512 and a.cocg_threads & (a.cocg_threads - 1) == 0, (M, a.cocg_threads)
         assert b.cocg_threads == a.cocg_threads
         a.close()
         b.close()
+    # above M = 4096 the Strang systems go to the tensor-memory kernel unless a CTA size is given
+    with aao.Plan(8191, 16, 1.5) as a, aao.Plan(8191, 16, 1.5, cocg_threads=512) as b:
+        assert a.cocg_threads == aao.AAO_COCG_TMEM and b.cocg_threads == 512
+    with aao.Plan(8191, 16, 1.5, inner=aao.AAO_INNER_TAU) as c:
+        assert c.cocg_threads == 512
     with aao.Plan(8191, 16, 1.5, prec=aao.AAO_PREC_FP64) as p64:
         assert p64.cocg_threads == 0
