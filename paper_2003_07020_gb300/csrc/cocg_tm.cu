@@ -4,9 +4,11 @@
 //
 // The register-resident kernel (cocg_reg.cuh) keeps r and p in registers, which leaves its FFT passes
 // 64 registers and forces radix-16 passes (five round trips through shared memory per convolution).
-// Here r, p and x live in TMEM (the SM's 256 KB tensor memory, 128 lanes x 512 columns of 32 bits,
-// used as per-thread storage: a warp reaches the 32 lanes of its sub-partition), so the passes get
-// the whole register file:
+// Here r and p live in TMEM (the SM's 256 KB tensor memory, 128 lanes x 512 columns of 32 bits,
+// used as per-thread storage: a warp reaches the 32 lanes of its sub-partition), together with the
+// thread's 31 twiddles W_L^{t m} of its first and last pass (read once per convolution half instead of
+// looked up in the quarter table, whose strided reads conflict in the shared-memory banks), so the
+// passes get the whole register file:
 //   * first forward pass: 32 points at stride 512 (five radix-2 stages), of which the upper 16 are
 //     the zero padding of the embedding, in the thread's registers;
 //   * one 16-point pass at stride 32 through shared memory;
@@ -29,7 +31,7 @@ constexpr int kTmLogL = 14, kTmL = 1 << kTmLogL, kTmNT = 512, kTmE = 16;
 constexpr int kTmPadded = kTmL + kTmL / 32;
 constexpr int kTmPassS = 32;                // stride of the 16-point pass (first stage 5)
 constexpr int kTmTable = 15 * kTmPassS;     // its twiddles W_512^{j0 m}, [m - 1][j0]
-constexpr int kTmCols = 512;                // TMEM columns allocated (r, p, x: 96 per thread, 4 warps per lane group)
+constexpr int kTmCols = 512;                // TMEM columns allocated (r, p and 2 x 16 twiddles: 128 per thread, 4 warps per lane group)
 
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
@@ -106,32 +108,31 @@ __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::
 // ---- the convolution ------------------------------------------------------------------------------
 // v (the thread's 16 elements of a vector supported on [0, L/2)) <- the first L/2 outputs of its L-point
 // cyclic convolution with the kernel whose spectrum F is stored in fused-pass order.  buf: the padded
-// transform buffer; q: quarter twiddle table of L; pt: the 16-point pass's table.  Starts and ends
-// synchronised.
-__device__ __forceinline__ void tm_conv(float2* buf, const float2* q, const float2* pt, float2 (&v)[kTmE],
-                                        const float2* __restrict__ F) {
+// transform buffer; pt: the 16-point pass's table; tE, tO: the TMEM addresses of the thread's twiddles
+// W_L^{2 t m'} and W_L^{t (2 m' + 1)}, m' < 16.  Starts and ends synchronised.
+__device__ __forceinline__ void tm_conv(float2* buf, const float2* pt, float2 (&v)[kTmE],
+                                        const float2* __restrict__ F, uint32_t tE, uint32_t tO) {
   const int t = threadIdx.x;
+  // the thread's 32 spectrum values (two 128-byte lines) into L1 ahead of the fused pass
+  asm volatile("prefetch.global.L1 [%0];" :: "l"(F + (t << 5)));
+  asm volatile("prefetch.global.L1 [%0];" :: "l"(F + (t << 5) + 16));
   // first forward pass (DIF, 32 points at stride 512, inputs 16..31 zero): output 2m' is the 16-point DFT
   // of v, output 2m'+1 that of v_k W_32^k; output m is multiplied by W_L^{t m} and stored at
   // t + bitrev_5(m) 512 (bitrev_5(2m') = bitrev_4(m'), bitrev_5(2m'+1) = 16 + bitrev_4(m'))
   {
-    float2 h[16];
+    float2 h[16], w[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) h[k] = v[k];
     dft<-1, 4>(h);
+    tm_ld(tE, w);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      if (m > 0) h[m] = cmul(h[m], twiddle<-1>(q, t * (2 * m), kTmLogL));
-      buf[pad32(t + brev_c<4>(m) * kTmNT)] = h[m];
-    }
+    for (int m = 0; m < 16; ++m) buf[pad32(t + brev_c<4>(m) * kTmNT)] = cmul(h[m], w[m]);
 #pragma unroll
     for (int k = 0; k < 16; ++k) h[k] = k > 0 ? cmul(v[k], w32<-1>(k)) : v[k];
     dft<-1, 4>(h);
+    tm_ld(tO, w);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      h[m] = cmul(h[m], twiddle<-1>(q, t * (2 * m + 1), kTmLogL));
-      buf[pad32(t + (16 + brev_c<4>(m)) * kTmNT)] = h[m];
-    }
+    for (int m = 0; m < 16; ++m) buf[pad32(t + (16 + brev_c<4>(m)) * kTmNT)] = cmul(h[m], w[m]);
   }
   __syncthreads();
   // 16-point DIF pass, stages 5..8 (stride 32): two groups per thread
@@ -184,18 +185,16 @@ __device__ __forceinline__ void tm_conv(float2* buf, const float2* q, const floa
   // last backward pass: outputs k < 16 only, x_k = A_k + W_32^{-k} B_k with A, B the 16-point inverse DFTs
   // of the even and odd inputs (each multiplied by W_L^{-t m} first)
   {
-    float2 h[16];
+    float2 h[16], w[16];
+    tm_ld(tE, w);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      h[m] = buf[pad32(t + brev_c<4>(m) * kTmNT)];
-      if (m > 0) h[m] = cmul(h[m], twiddle<+1>(q, t * (2 * m), kTmLogL));
-    }
+    for (int m = 0; m < 16; ++m) h[m] = cmulc(buf[pad32(t + brev_c<4>(m) * kTmNT)], w[m]);
     dft<+1, 4>(h);
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = h[k];
+    tm_ld(tO, w);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) h[m] = cmul(buf[pad32(t + (16 + brev_c<4>(m)) * kTmNT)],
-                                             twiddle<+1>(q, t * (2 * m + 1), kTmLogL));
+    for (int m = 0; m < 16; ++m) h[m] = cmulc(buf[pad32(t + (16 + brev_c<4>(m)) * kTmNT)], w[m]);
     dft<+1, 4>(h);
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = cadd(v[k], k > 0 ? cmul(h[k], w32<+1>(k)) : h[k]);
@@ -225,7 +224,8 @@ __global__ void __launch_bounds__(kTmNT, 1)
   const int n = blockIdx.x;
   if (n >= nsys) return;
   // TMEM: 512 columns (one CTA per SM: the shared memory allows no second one, so the allocation
-  // never waits); warp w uses lanes 32 (w mod 4) .. +31 and columns 96 (w div 4) + {0: r, 32: p, 64: x}
+  // never waits); warp w uses lanes 32 (w mod 4) .. +31 and columns 128 (w div 4) + {0: r, 32: p,
+  // 64: W_L^{2 t m'}, 96: W_L^{t (2m'+1)}}
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"((uint32_t)__cvta_generic_to_shared(&sc.tmem)), "r"((uint32_t)kTmCols) : "memory");
@@ -239,10 +239,19 @@ __global__ void __launch_bounds__(kTmNT, 1)
     const int m = idx / kTmPassS + 1, j0 = idx - (m - 1) * kTmPassS;
     pt[idx] = twiddle<-1>(q, (j0 * m) << 5, kTmLogL);
   }
-  const uint32_t tbase = sc.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 96u * (uint32_t)(warp >> 2);
-  const uint32_t tR = tbase, tP = tbase + 32, tX = tbase + 64;
+  const uint32_t tbase = sc.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+  const uint32_t tR = tbase, tP = tbase + 32, tE = tbase + 64, tO = tbase + 96;
   float2* const xt = xb + (size_t)n * M + t;
   const float2* const G = tb.sconv + ((size_t)n << kTmLogL);
+  {
+    float2 w[kTmE];
+#pragma unroll
+    for (int m = 0; m < kTmE; ++m) w[m] = twiddle<-1>(q, t * (2 * m), kTmLogL);
+    tm_st(tE, w);
+#pragma unroll
+    for (int m = 0; m < kTmE; ++m) w[m] = twiddle<-1>(q, t * (2 * m + 1), kTmLogL);
+    tm_st(tO, w);
+  }
 
   // b / ||b||_1 (zero beyond M) into r; x = 0
   float2 v[kTmE];
@@ -270,8 +279,8 @@ __global__ void __launch_bounds__(kTmNT, 1)
       }
       tm_st(tR, v);
 #pragma unroll
-      for (int j = 0; j < kTmE; ++j) v[j] = float2{0, 0};
-      tm_st(tX, v);
+      for (int j = 0; j < kTmE; ++j)
+        if (t + kTmNT * j < M) xt[kTmNT * j] = float2{0, 0};
       block_sum<float, 1>(nb2, red);
       if (t == 0) {
         const double2 lamd = tb.lambda[n];
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(kTmNT, 1)
 #pragma unroll 1
     for (;;) {
       tm_ld(kind ? tP : tR, v);
-      tm_conv(buf, q, pt, v, kind ? tb.Ebr : G);
+      tm_conv(buf, pt, v, kind ? tb.Ebr : G, tE, tO);
       if (kind == 0) {
         // z = v (zero beyond M); rho = r^T z; p = z (first step) or z + beta p
 #pragma unroll
@@ -352,12 +361,13 @@ __global__ void __launch_bounds__(kTmNT, 1)
           tm_st(tR, r);
         }
         {
-          float2 x[kTmE], p[kTmE];
-          tm_ld(tX, x);
+          const float bs = sc.bs;
+          const float2 ax{a.x * bs, a.y * bs};  // the step in the units of b
+          float2 p[kTmE];
           tm_ld(tP, p);
 #pragma unroll
-          for (int j = 0; j < kTmE; ++j) x[j] = cadd(x[j], cmul(a, p[j]));
-          tm_st(tX, x);
+          for (int j = 0; j < kTmE; ++j)
+            if (t + kTmNT * j < M) xt[kTmNT * j] = cadd(xt[kTmNT * j], cmul(ax, p[j]));
         }
         block_sum<float, 1>(rr, red);
         ++it;
@@ -366,12 +376,6 @@ __global__ void __launch_bounds__(kTmNT, 1)
         kind = 0;
       }
     }
-    // x in the units of b
-    const float bs = sc.bs;
-    tm_ld(tX, v);
-#pragma unroll
-    for (int j = 0; j < kTmE; ++j)
-      if (t + kTmNT * j < M) xt[kTmNT * j] = float2{v[j].x * bs, v[j].y * bs};
   }
   if (t == 0) { iters[n] = it; flags[n] = flag; }
   // release TMEM once every warp's accesses are complete
