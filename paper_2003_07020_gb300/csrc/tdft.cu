@@ -22,7 +22,7 @@ template <typename R> __device__ __forceinline__ R ldv(const float2* p) { return
 
 // ---- Step (a) ----
 template <typename R, typename TV>
-__global__ void __launch_bounds__(256) tdft_fwd_kernel(const TV* __restrict__ v,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) tdft_fwd_kernel(const TV* __restrict__ v,
                                                        typename cplx_t<R>::type* __restrict__ out, int M,
                                                        int logNt, const R* __restrict__ scale,
                                                        const typename cplx_t<R>::type* __restrict__ tw) {
@@ -34,7 +34,10 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const TV* __restrict__ v,
   const int bstride = padded_size(Nt) + 1;  // odd stride: the TW/2 transforms start in different banks
   const int c0 = blockIdx.x * TW;
   C* tq = sm + TWH * bstride;
+  C* pt = tq + Nt / 4;  // per-pass twiddle tables (conflict-free reads in the 16-point passes)
   load_quarter(tq, tw, Nt / 4);
+  __syncthreads();
+  build_pass_tables(pt, tq, logNt, logNt);
   // load y_k = scale_k v_k (real) into position bitrev(k); column cc -> transform cc % TWH, part cc / TWH
   for (int base = threadIdx.x; base < Nt * TW; base += LU * blockDim.x) {
     R vals[LU];
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const TV* __restrict__ v,
       smr[2 * (q * bstride + pad16(bitrev(k, logNt))) + part] = vals[u] * __ldg(&scale[k]);
     }
   }
-  fft_backward(sm, logNt, TWH, bstride, tq, logNt);  // sum_k y_k exp(+2 pi i nk/Nt), natural order
+  fft_backward(sm, logNt, TWH, bstride, tq, logNt, pt);  // sum_k y_k exp(+2 pi i nk/Nt), natural order
   const int half = Nt / 2;
   for (int idx = threadIdx.x; idx < (half + 1) * TW; idx += blockDim.x) {
     const int n = idx / TW, cc = idx - n * TW;
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(256) tdft_fwd_kernel(const TV* __restrict__ v,
 
 // ---- Step (c) ----
 template <typename R, typename TOut>
-__global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>::type* __restrict__ in,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) tdft_inv_kernel(const typename cplx_t<R>::type* __restrict__ in,
                                                        TOut* __restrict__ z, int M, int logNt,
                                                        const R* __restrict__ scale_inv,
                                                        const typename cplx_t<R>::type* __restrict__ tw) {
@@ -83,7 +86,10 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
   const int c0 = blockIdx.x * TW;
   const int half = Nt / 2;
   C* tq = sm + TWH * bstride;
+  C* pt = tq + Nt / 4;
   load_quarter(tq, tw, Nt / 4);
+  __syncthreads();
+  build_pass_tables(pt, tq, logNt, logNt);
   const int nin = (half + 1) * TWH;
   for (int base = threadIdx.x; base < nin; base += LU * blockDim.x) {
     C xa[LU], xb[LU];
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
       if (n != 0 && n != half) sm[q * bstride + pad16(Nt - n)] = C{Xa.x + Xb.y, Xb.x - Xa.y};  // conj Xa + i conj Xb
     }
   }
-  fft_forward(sm, logNt, TWH, bstride, tq, logNt);  // sum_n Z_n exp(-2 pi i nk/Nt), bit-reversed
+  fft_forward(sm, logNt, TWH, bstride, tq, logNt, pt);  // sum_n Z_n exp(-2 pi i nk/Nt), bit-reversed
   for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
     const int k = idx / TW, cc = idx - k * TW;
     const int col = c0 + cc;
@@ -118,12 +124,14 @@ __global__ void __launch_bounds__(256) tdft_inv_kernel(const typename cplx_t<R>:
   }
 }
 
+static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
 template <typename R>
 static size_t tdft_smem(int Nt) {
-  return ((size_t)TWH * (padded_size(Nt) + 1) + (size_t)(Nt / 4)) * sizeof(typename cplx_t<R>::type);
+  return ((size_t)TWH * (padded_size(Nt) + 1) + (size_t)(Nt / 4) + (size_t)pass_table_size(ilog2i(Nt))) *
+         sizeof(typename cplx_t<R>::type);
 }
 
-static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 size_t tdft_smem_bytes(int Nt, bool fp32) { return fp32 ? tdft_smem<float>(Nt) : tdft_smem<double>(Nt); }
 
