@@ -273,6 +273,9 @@ NTT_DRAM_BYTES_PER_ROW_M8191 = (4.200e6 + 10.171e6 + 46.684e6) / 128
 # DRAM bytes of cocg_reg_kernel<Strang spectra> per shifted system at M = 8191 (13.21 MB read + 21 KB
 # written for 65 systems, one ncu capture at M = 8191, Nt = 128): the per-system spectrum and tables.
 COCG_DRAM_BYTES_PER_SYSTEM_M8191 = (13.211e6 + 0.021e6) / 65
+# The same for cocg_tm_kernel (13.19 MB read + 9.47 MB written for 65 systems, one ncu capture at M = 8191,
+# Nt = 128, profiles/cocg_tm_small_full.md): the spectrum read once and the write-back of x.
+COCG_TM_DRAM_BYTES_PER_SYSTEM_M8191 = (13.186e6 + 9.472e6) / 65
 # Lazy Shoup butterfly issue rate measured on GB300 (dependent-chain probe): 6.27 per clock per SM.
 NTT_PEAK_GBFLY = 6.27 * 152 * 2.07
 
@@ -624,8 +627,8 @@ def run_ours(args):
         pkv = FP32_PEAK_TFLOPS if args.prec == "mixed" else FP64_PEAK_TFLOPS
         achieved = fl / (t_launch * 1e-3) / 1e12
         tm = reg and plans[0].cocg_threads == aao.AAO_COCG_TMEM  # the tensor-memory kernel
-        traffic = (COCG_DRAM_BYTES_PER_SYSTEM_M8191 * nsys
-                   if (reg and not tm and args.inner == "strang" and M == 8191) else None)
+        traffic = ((COCG_TM_DRAM_BYTES_PER_SYSTEM_M8191 if tm else COCG_DRAM_BYTES_PER_SYSTEM_M8191) * nsys
+                   if (reg and args.inner == "strang" and M == 8191) else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": pkv, "unit": "TFLOP/s", "frac": achieved / pkv,
                 "traffic": traffic,
                 "kernel": ("cocg_tm_kernel" if tm else "cocg_reg_kernel") if reg else
