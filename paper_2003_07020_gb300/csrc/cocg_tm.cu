@@ -159,8 +159,13 @@ __device__ __forceinline__ void tm_conv(float2* buf, const float2* pt, float2 (&
 #pragma unroll
     for (int k = 0; k < 32; ++k) h[k] = buf[pad32(start + k)];
     dft32<-1>(h);
+    const float4* F4 = reinterpret_cast<const float4*>(F + start);  // 16-byte aligned: start is a multiple of 32
 #pragma unroll
-    for (int m = 0; m < 32; ++m) h[m] = cmul(h[m], __ldg(&F[start + m]));
+    for (int m = 0; m < 16; ++m) {
+      const float4 f = __ldg(&F4[m]);
+      h[2 * m] = cmul(h[2 * m], float2{f.x, f.y});
+      h[2 * m + 1] = cmul(h[2 * m + 1], float2{f.z, f.w});
+    }
     dft32<+1>(h);
 #pragma unroll
     for (int k = 0; k < 32; ++k) buf[pad32(start + k)] = h[k];
