@@ -107,15 +107,21 @@ __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::
 
 // ---- the convolution ------------------------------------------------------------------------------
 // v (the thread's 16 elements of a vector supported on [0, L/2)) <- the first L/2 outputs of its L-point
-// cyclic convolution with the kernel whose spectrum F is stored in fused-pass order.  buf: the padded
+// cyclic convolution with the kernel whose spectrum F (or, if Fr is not null, the real spectrum Fr) is
+// stored in fused-pass order.  buf: the padded
 // transform buffer; pt: the 16-point pass's table; tE, tO: the TMEM addresses of the thread's twiddles
 // W_L^{2 t m'} and W_L^{t (2 m' + 1)}, m' < 16.  Starts and ends synchronised.
 __device__ __forceinline__ void tm_conv(float2* buf, const float2* pt, float2 (&v)[kTmE],
-                                        const float2* __restrict__ F, uint32_t tE, uint32_t tO) {
+                                        const float2* __restrict__ F, const float* __restrict__ Fr, uint32_t tE,
+                                        uint32_t tO) {
   const int t = threadIdx.x;
-  // the thread's 32 spectrum values (two 128-byte lines) into L1 ahead of the fused pass
-  asm volatile("prefetch.global.L1 [%0];" :: "l"(F + (t << 5)));
-  asm volatile("prefetch.global.L1 [%0];" :: "l"(F + (t << 5) + 16));
+  // the thread's 32 spectrum values (one or two 128-byte lines) into L1 ahead of the fused pass
+  if (Fr) {
+    asm volatile("prefetch.global.L1 [%0];" :: "l"(Fr + (t << 5)));
+  } else {
+    asm volatile("prefetch.global.L1 [%0];" :: "l"(F + (t << 5)));
+    asm volatile("prefetch.global.L1 [%0];" :: "l"(F + (t << 5) + 16));
+  }
   // first forward pass (DIF, 32 points at stride 512, inputs 16..31 zero): output 2m' is the 16-point DFT
   // of v, output 2m'+1 that of v_k W_32^k; output m is multiplied by W_L^{t m} and stored at
   // t + bitrev_5(m) 512 (bitrev_5(2m') = bitrev_4(m'), bitrev_5(2m'+1) = 16 + bitrev_4(m'))
@@ -159,12 +165,24 @@ __device__ __forceinline__ void tm_conv(float2* buf, const float2* pt, float2 (&
 #pragma unroll
     for (int k = 0; k < 32; ++k) h[k] = buf[pad32(start + k)];
     dft32<-1>(h);
-    const float4* F4 = reinterpret_cast<const float4*>(F + start);  // 16-byte aligned: start is a multiple of 32
+    if (Fr) {  // a real spectrum (the Toeplitz embedding's): four values per 16-byte load
+      const float4* F4 = reinterpret_cast<const float4*>(Fr + start);  // 16-byte aligned: start is a multiple of 32
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const float4 f = __ldg(&F4[m]);
-      h[2 * m] = cmul(h[2 * m], float2{f.x, f.y});
-      h[2 * m + 1] = cmul(h[2 * m + 1], float2{f.z, f.w});
+      for (int m = 0; m < 8; ++m) {
+        const float4 f = __ldg(&F4[m]);
+        h[4 * m] = cscale(h[4 * m], f.x);
+        h[4 * m + 1] = cscale(h[4 * m + 1], f.y);
+        h[4 * m + 2] = cscale(h[4 * m + 2], f.z);
+        h[4 * m + 3] = cscale(h[4 * m + 3], f.w);
+      }
+    } else {  // complex: two values per load
+      const float4* F4 = reinterpret_cast<const float4*>(F + start);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const float4 f = __ldg(&F4[m]);
+        h[2 * m] = cmul(h[2 * m], float2{f.x, f.y});
+        h[2 * m + 1] = cmul(h[2 * m + 1], float2{f.z, f.w});
+      }
     }
     dft32<+1>(h);
 #pragma unroll
@@ -300,7 +318,7 @@ __global__ void __launch_bounds__(kTmNT, 1)
 #pragma unroll 1
     for (;;) {
       tm_ld(kind ? tP : tR, v);
-      tm_conv(buf, pt, v, kind ? tb.Ebr : G, tE, tO);
+      tm_conv(buf, pt, v, G, kind ? tb.Ebr : nullptr, tE, tO);
       if (kind == 0) {
         // z = v (zero beyond M); rho = r^T z; p = z (first step) or z + beta p
 #pragma unroll
@@ -420,13 +438,12 @@ __global__ void tm_gather_kernel(const float2* __restrict__ src, float2* __restr
     dst[e] = src[(e & ~(size_t)(kTmL - 1)) + perm[e & (kTmL - 1)]];
 }
 
-__global__ void tm_gather_real_kernel(const float* __restrict__ src, float2* __restrict__ dst,
+__global__ void tm_gather_real_kernel(const float* __restrict__ src, float* __restrict__ dst,
                                       const int* __restrict__ perm) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kTmL; e += gridDim.x * blockDim.x)
-    dst[e] = float2{src[perm[e]], 0.0f};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kTmL; e += gridDim.x * blockDim.x) dst[e] = src[perm[e]];
 }
 
-cudaError_t launch_tm_gather(const float2* src, float2* dst, const float* srcr, float2* dstr, const int* perm, int nsys,
+cudaError_t launch_tm_gather(const float2* src, float2* dst, const float* srcr, float* dstr, const int* perm, int nsys,
                              cudaStream_t s) {
   tm_gather_kernel<<<4 * 152, 256, 0, s>>>(src, dst, perm, nsys);
   tm_gather_real_kernel<<<kTmL / 256, 256, 0, s>>>(srcr, dstr, perm);

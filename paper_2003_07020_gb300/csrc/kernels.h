@@ -60,15 +60,15 @@ struct CocgTables32 {
 // pass: entry s holds L-frequency tm_order_freq(s).
 struct CocgTmTables {
   const float2* twL;      // exp(-2 pi i m/L), m < L/2
-  const float2* Ebr;      // c DFT_L(e) / L as complex values [L]
+  const float* Ebr;       // c DFT_L(e) / L (real) [L]
   const float2* sconv;    // per system, the spectra of CocgTables32::sconv [nsys][L]
   const double2* lambda;  // lambda_n
 };
 int tm_order_freq(int s);
 bool cocg_tm_supported(int M, int logL);
 size_t cocg_tm_smem_bytes();
-// dst[n][s] = src[n][perm[s]] (n < nsys), dstr[s] = (srcr[perm[s]], 0), s < 2^14
-cudaError_t launch_tm_gather(const float2* src, float2* dst, const float* srcr, float2* dstr, const int* perm, int nsys,
+// dst[n][s] = src[n][perm[s]] (n < nsys), dstr[s] = srcr[perm[s]], s < 2^14
+cudaError_t launch_tm_gather(const float2* src, float2* dst, const float* srcr, float* dstr, const int* perm, int nsys,
                              cudaStream_t s);
 // xb: [nsys][M] right-hand sides in, solutions out; iters / flags as launch_cocg_f32.
 cudaError_t launch_cocg_tm(float2* xb, int M, int logL, int nsys, const CocgTmTables& tb, float tol, int maxit,

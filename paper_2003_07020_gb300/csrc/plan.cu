@@ -246,7 +246,7 @@ struct aao_plan {
   // Step (b) by the tensor-memory kernel (cocg_tm.cu): the spectra in the order of its fused pass
   bool tm = false;
   float2* sconv_tm = nullptr;
-  float2* Ebr_tm = nullptr;
+  float* Ebr_tm = nullptr;
   // exact-integer matvec (opts.matvec == AAO_MATVEC_NTT, 1D)
   bool ntt = false;
   aao::NttTables ntt_tab{};
