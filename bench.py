@@ -273,9 +273,9 @@ NTT_DRAM_BYTES_PER_ROW_M8191 = (4.200e6 + 10.171e6 + 46.684e6) / 128
 # DRAM bytes of cocg_reg_kernel<Strang spectra> per shifted system at M = 8191 (13.21 MB read + 21 KB
 # written for 65 systems, one ncu capture at M = 8191, Nt = 128): the per-system spectrum and tables.
 COCG_DRAM_BYTES_PER_SYSTEM_M8191 = (13.211e6 + 0.021e6) / 65
-# The same for cocg_tm_kernel (13.19 MB read + 9.47 MB written for 65 systems, one ncu capture at M = 8191,
+# The same for cocg_tm_kernel (12.99 MB read + 6.91 MB written for 65 systems, one ncu capture at M = 8191,
 # Nt = 128, profiles/cocg_tm_small_full.md): the spectrum read once and the write-back of x.
-COCG_TM_DRAM_BYTES_PER_SYSTEM_M8191 = (13.186e6 + 9.472e6) / 65
+COCG_TM_DRAM_BYTES_PER_SYSTEM_M8191 = (12.988e6 + 6.912e6) / 65
 # Lazy Shoup butterfly issue rate measured on GB300 (dependent-chain probe): 6.27 per clock per SM.
 NTT_PEAK_GBFLY = 6.27 * 152 * 2.07
 
