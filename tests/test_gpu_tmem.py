@@ -99,3 +99,25 @@ def test_tmem_zero_tiny_and_nonfinite_right_hand_sides():
     w[3, 17] = np.nan
     _, _, fl3 = apply(M, Nt, alpha, w, aao.AAO_COCG_TMEM)
     assert (fl3 & 3 == 3).all(), fl3  # every frequency sees the NaN through Step (a)
+
+
+def test_learned_warm_start_on_a_tensor_memory_plan():
+    # The tensor-memory kernel takes no initial guess: with a model attached the plan's Step (b) runs on the
+    # 512-thread register kernel, and the acceptance rule and FGMRES keep the result exact (random model).
+    M, Nt, alpha = 4500, 16, 1.4
+    u0, f = workloads.make_inputs(M, Nt, seed=15)
+    K = fcd.jacobian_1d(alpha, 1.0, M, 1.0 / (M + 1))
+    Useq = oaao.sequential_bdf2(K, 1.0 / Nt, u0, f)
+    with aao.Plan(M, Nt, alpha, prec=aao.AAO_PREC_MIXED) as plan, aao.Fno(M, max_batch=Nt // 2 + 1, seed=2) as net:
+        assert plan.cocg_threads == aao.AAO_COCG_TMEM
+        F = torch.empty((Nt, M), dtype=torch.float64, device=DEV)
+        plan.build_rhs(cu(u0), cu(f), F)
+        plan.set_warm_start(net)
+        U = torch.zeros_like(F)
+        info = plan.gmres_solve(F, U)
+        plan.set_warm_start(None)
+        U2 = torch.zeros_like(F)
+        info2 = plan.gmres_solve(F, U2)  # back on the tensor-memory kernel
+    for inf, u in ((info, U), (info2, U2)):
+        assert inf["true_rel_res"] <= 1e-10, inf
+        assert rel(u.cpu().numpy(), Useq) <= 1e-9
