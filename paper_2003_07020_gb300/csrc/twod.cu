@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kElemThreads) c2d_init(Cx<R>* __restrict__ X, 
 // out = scale * S_x in (rows, odd extension of length Lx = 2 (Mx+1)); MODE 1 also accumulates
 // the bilinear partial sum_e r_e out_e (rho of COCG).
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kLineThreads) c2d_rows_dst(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_rows_dst(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
                                                              const Cx<R>* __restrict__ rr, int Mx, int My, int logLx,
                                                              const Cx<R>* __restrict__ twx, R scale, int B,
                                                              const SysState* __restrict__ st,
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kLineThreads) c2d_rows_dst(const Cx<R>* __rest
 // out = (2/(My+1)) S_y D S_y in along columns (B complex columns per CTA), D from lambda_n,
 // c_x sigma^x_i (natural order) and c_y sigma^y (fused order, 1e30 where the DST multiplier vanishes)
 template <typename R>
-__global__ void __launch_bounds__(kLineThreads) c2d_cols_dst_div(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_cols_dst_div(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
                                                                  int Mx, int My, int logLy,
                                                                  const Cx<R>* __restrict__ twy,
                                                                  const R* __restrict__ sxn, const R* __restrict__ syf,
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kLineThreads) c2d_cols_dst_div(const Cx<R>* __
 
 // p = z + beta p (written back), then tmp = c_x T_x p along rows
 template <typename R>
-__global__ void __launch_bounds__(kLineThreads) c2d_rows_conv(const Cx<R>* __restrict__ Z, Cx<R>* __restrict__ P,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_rows_conv(const Cx<R>* __restrict__ Z, Cx<R>* __restrict__ P,
                                                               Cx<R>* __restrict__ Tm, int Mx, int My, int logLx,
                                                               const Cx<R>* __restrict__ twx,
                                                               const R* __restrict__ Exf, int B,
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kLineThreads) c2d_rows_conv(const Cx<R>* __res
 
 // q = tmp + lambda p + c_y T_y p along columns; partial p^T q
 template <typename R>
-__global__ void __launch_bounds__(kLineThreads) c2d_cols_conv(const Cx<R>* __restrict__ P, const Cx<R>* __restrict__ Tm,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_cols_conv(const Cx<R>* __restrict__ P, const Cx<R>* __restrict__ Tm,
                                                               Cx<R>* __restrict__ Q, int Mx, int My, int logLy,
                                                               const Cx<R>* __restrict__ twy,
                                                               const R* __restrict__ Eyf,
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kElemThreads) c2d_update(Cx<R>* __restrict__ X
 
 // W[n][j][p] = forward DIF FFT along x of the zero-padded row j of X[n] (position p holds frequency bitrev(p))
 template <typename R>
-__global__ void __launch_bounds__(kLineThreads) c2d_rows_fft_fwd(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ W,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_rows_fft_fwd(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ W,
                                                                  int Mx, int My, int logLx,
                                                                  const Cx<R>* __restrict__ twx, int B,
                                                                  const SysState* __restrict__ st) {
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kLineThreads) c2d_rows_fft_fwd(const Cx<R>* __
 // Along y for every x-position p: W[n][:][p] <- first My outputs of the Ly-periodic convolution of the
 // zero-padded column with the spectrum G[n][p][:] (fused order)
 template <typename R>
-__global__ void __launch_bounds__(kLineThreads) c2d_cols_conv_g(Cx<R>* __restrict__ W, int Lx, int My, int logLy,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_cols_conv_g(Cx<R>* __restrict__ W, int Lx, int My, int logLy,
                                                                 const Cx<R>* __restrict__ twy,
                                                                 const Cx<R>* __restrict__ G, int B,
                                                                 const SysState* __restrict__ st) {
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(kLineThreads) c2d_cols_conv_g(Cx<R>* __restric
 // out[n][j][i] = inverse DIT FFT along x of W[n][j][:] (bit-reversed in), first Mx outputs; MODE 1 also
 // accumulates the bilinear partial sum_e r_e out_e (rho of COCG)
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kLineThreads) c2d_rows_fft_inv(const Cx<R>* __restrict__ W, Cx<R>* __restrict__ out,
+__global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_rows_fft_inv(const Cx<R>* __restrict__ W, Cx<R>* __restrict__ out,
                                                                  const Cx<R>* __restrict__ rr, int Mx, int My,
                                                                  int logLx, const Cx<R>* __restrict__ twx, int B,
                                                                  const SysState* __restrict__ st,
