@@ -26,6 +26,75 @@ __device__ __forceinline__ bool near_breakdown(R re, R im, R uu, R ww) {
   return !(re * re + im * im > k * k * uu * ww);
 }
 
+// ---- spectrum providers for the fused pass: element access and blocks of R values by 16-byte loads ----
+// (a thread's group of R factors is contiguous and starts at a multiple of R, so the loads are aligned)
+struct RealSpec32 {  // (e_k, 0), e real
+  const float* e;
+  __device__ __forceinline__ float2 operator()(int k) const { return float2{__ldg(&e[k]), 0.0f}; }
+  template <int R> __device__ __forceinline__ void block(int s, float2 (&f)[R]) const {
+    if constexpr (R % 4 == 0) {
+      const float4* e4 = reinterpret_cast<const float4*>(e + s);
+#pragma unroll
+      for (int m = 0; m < R / 4; ++m) {
+        const float4 a = __ldg(&e4[m]);
+        f[4 * m] = float2{a.x, 0.0f};
+        f[4 * m + 1] = float2{a.y, 0.0f};
+        f[4 * m + 2] = float2{a.z, 0.0f};
+        f[4 * m + 3] = float2{a.w, 0.0f};
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) f[m] = (*this)(s + m);
+    }
+  }
+};
+struct CplxSpec32 {  // complex values
+  const float2* c;
+  __device__ __forceinline__ float2 operator()(int k) const { return __ldg(&c[k]); }
+  template <int R> __device__ __forceinline__ void block(int s, float2 (&f)[R]) const {
+    if constexpr (R % 2 == 0) {
+      const float4* c4 = reinterpret_cast<const float4*>(c + s);
+#pragma unroll
+      for (int m = 0; m < R / 2; ++m) {
+        const float4 a = __ldg(&c4[m]);
+        f[2 * m] = float2{a.x, a.y};
+        f[2 * m + 1] = float2{a.z, a.w};
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) f[m] = (*this)(s + m);
+    }
+  }
+};
+
+struct TauSpec32 {  // 1 / (L (lambda + sigma_p)), sigma real
+  const float* sig;
+  float2 lam;
+  float invL;
+  __device__ __forceinline__ float2 at(float sg) const {
+    float2 d = lam;
+    d.x += sg;
+    return cdiv(float2{invL, 0}, d);
+  }
+  __device__ __forceinline__ float2 operator()(int p) const { return at(__ldg(&sig[p])); }
+  template <int R> __device__ __forceinline__ void block(int s, float2 (&f)[R]) const {
+    if constexpr (R % 4 == 0) {
+      const float4* s4 = reinterpret_cast<const float4*>(sig + s);
+#pragma unroll
+      for (int m = 0; m < R / 4; ++m) {
+        const float4 a = __ldg(&s4[m]);
+        f[4 * m] = at(a.x);
+        f[4 * m + 1] = at(a.y);
+        f[4 * m + 2] = at(a.z);
+        f[4 * m + 3] = at(a.w);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) f[m] = (*this)(s + m);
+    }
+  }
+};
+
 // ---- FP32 path with register-resident vectors -------------------------------------------
 // NT threads (64 .. 512, chosen per problem by the autotuner of plan creation); thread t owns
 // elements i = t + NT j, j < 16 (M <= 16 NT), so r and p live in registers for the whole solve
@@ -90,7 +159,7 @@ __device__ __forceinline__ void fft_convolve_own(float2* buf, const float2 (&x)[
 template <int NT>
 __device__ __forceinline__ void toeplitz_reg(float2* buf, const float2 (&x)[kRegElems], int M, int logL,
                                              const CocgTables32& tb, const float2* q, const float2* pt) {
-  auto ef = [&](int k) { return float2{__ldg(&tb.Ebr[k]), 0.0f}; };
+  const RealSpec32 ef{tb.Ebr};
   if (logL == own_logL<NT>()) {
     fft_convolve_own<NT>(buf, x, q, ef, pt);
     return;
@@ -116,7 +185,7 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
   const int L = 1 << logL;
   const int t = threadIdx.x;
   if constexpr (KIND == 2) {
-    auto sf = [&](int p) { return __ldg(&sc[p]); };
+    const CplxSpec32 sf{sc};
     if (logL == own_logL<NT>()) {
       fft_convolve_own<NT>(buf, r, q, sf, pt);
       return;
@@ -165,14 +234,8 @@ __device__ __forceinline__ void precond_reg(float2* buf, const float2 (&r)[kRegE
         buf[pad16(L - 1 - i)] = float2{-r[j].x, -r[j].y};
       }
     }
-    const int Mp1 = M + 1;
-    const float invL = 1.0f / (float)L;
-    fft_convolve(buf, logL, q, logL, [&](int p) {
-      float2 d = lam;
-      d.x += __ldg(&tb.taueig_br[p]);
-      return cdiv(float2{invL, 0}, d);
-    }, pt);
-    (void)Mp1;
+    const TauSpec32 tf{tb.taueig_br, lam, 1.0f / (float)L};
+    fft_convolve(buf, logL, q, logL, tf, pt);
   }
 }
 

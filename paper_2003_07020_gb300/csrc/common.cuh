@@ -27,6 +27,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace aao {
 
 template <typename R> struct cplx_t;
@@ -335,6 +338,14 @@ __device__ void fft_backward(T* buf, int logN, int batch, int bstride, const T* 
 // natural DFT output index), i.e. the kernel spectrum for bit-reversed
 // position start + bitrev_r(m); tables are stored in that order so that a
 // thread reads its 2^r factors contiguously.
+// A factor provider may also offer block<R>(start, f), filling f[m] = factor(start + m) for m < R in one
+// go (vector loads of the R contiguous values a thread needs); fused_mid_pass uses it when present.
+template <typename F, typename T, int R, typename = void> struct has_block : std::false_type {};
+template <typename F, typename T, int R>
+struct has_block<F, T, R,
+                 std::void_t<decltype(std::declval<const F&>().template block<R>(0, std::declval<T (&)[R]>()))>>
+    : std::true_type {};
+
 template <typename T, int r, typename F>
 __device__ __forceinline__ void fused_mid_pass(T* buf, int logN, F factor) {
   constexpr int R = 1 << r;
@@ -345,8 +356,15 @@ __device__ __forceinline__ void fused_mid_pass(T* buf, int logN, F factor) {
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = buf[pad16(start + k)];
     dft<-1, r>(v);
+    if constexpr (has_block<F, T, R>::value) {
+      T f[R];
+      factor.template block<R>(start, f);
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = cmul(v[m], factor(start + m));
+      for (int m = 0; m < R; ++m) v[m] = cmul(v[m], f[m]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = cmul(v[m], factor(start + m));
+    }
     dft<+1, r>(v);
 #pragma unroll
     for (int k = 0; k < R; ++k) buf[pad16(start + k)] = v[k];
