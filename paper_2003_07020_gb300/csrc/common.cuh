@@ -371,7 +371,14 @@ __device__ __forceinline__ void fused_mid_pass(T* buf, int logN, F factor) {
   }
 }
 
-// Batched form of fused_mid_pass: factor(b, pf) for transform b.
+// Batched form of fused_mid_pass: factor(b, pf) for transform b (and factor.block<R>(b, start, f) when
+// the provider offers it).
+template <typename F, typename T, int R, typename = void> struct has_block_b : std::false_type {};
+template <typename F, typename T, int R>
+struct has_block_b<
+    F, T, R, std::void_t<decltype(std::declval<const F&>().template block<R>(0, 0, std::declval<T (&)[R]>()))>>
+    : std::true_type {};
+
 template <typename T, int r, typename F>
 __device__ __forceinline__ void fused_mid_pass_b(T* buf, int logN, int batch, int bstride, F factor) {
   constexpr int R = 1 << r;
@@ -384,8 +391,15 @@ __device__ __forceinline__ void fused_mid_pass_b(T* buf, int logN, int batch, in
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = base[pad16(start + k)];
     dft<-1, r>(v);
+    if constexpr (has_block_b<F, T, R>::value) {
+      T f[R];
+      factor.template block<R>(b, start, f);
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = cmul(v[m], factor(b, start + m));
+      for (int m = 0; m < R; ++m) v[m] = cmul(v[m], f[m]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[m] = cmul(v[m], factor(b, start + m));
+    }
     dft<+1, r>(v);
 #pragma unroll
     for (int k = 0; k < R; ++k) base[pad16(start + k)] = v[k];

@@ -40,6 +40,58 @@ __host__ __device__ inline int lines_per_cta(int L, int csize) {
 
 template <typename TIn> __device__ __forceinline__ double ldd(const TIn* p) { return (double)__ldg(p); }
 
+// Spectrum providers for the fused pass of the line convolutions (see fused_mid_pass_b): a real spectrum
+// shared by all lines, and per-line complex spectra G[line][.] (zero beyond the lines); a thread's R
+// contiguous factors come in 16-byte loads (FP32).
+template <typename R> struct LineReal {
+  const R* e;
+  __device__ __forceinline__ Cx<R> operator()(int, int pf) const { return Cx<R>{__ldg(&e[pf]), (R)0}; }
+  template <int RR> __device__ __forceinline__ void block(int, int s, Cx<R> (&f)[RR]) const {
+    if constexpr (sizeof(R) == 4 && RR % 4 == 0) {
+      const float4* e4 = reinterpret_cast<const float4*>(e + s);
+#pragma unroll
+      for (int m = 0; m < RR / 4; ++m) {
+        const float4 a = __ldg(&e4[m]);
+        f[4 * m] = Cx<R>{a.x, 0};
+        f[4 * m + 1] = Cx<R>{a.y, 0};
+        f[4 * m + 2] = Cx<R>{a.z, 0};
+        f[4 * m + 3] = Cx<R>{a.w, 0};
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < RR; ++m) f[m] = (*this)(0, s + m);
+    }
+  }
+};
+template <typename R> struct LineCplx {
+  const Cx<R>* g;  // line b at g + (p0 + b) * stride
+  int p0, nlines, stride;
+  __device__ __forceinline__ Cx<R> operator()(int b, int pf) const {
+    const int p = p0 + b;
+    return p < nlines ? g[(size_t)p * stride + pf] : Cx<R>{0, 0};
+  }
+  template <int RR> __device__ __forceinline__ void block(int b, int s, Cx<R> (&f)[RR]) const {
+    const int p = p0 + b;
+    if constexpr (sizeof(R) == 4 && RR % 2 == 0) {
+      if (p < nlines) {
+        const float4* g4 = reinterpret_cast<const float4*>(g + (size_t)p * stride + s);
+#pragma unroll
+        for (int m = 0; m < RR / 2; ++m) {
+          const float4 a = __ldg(&g4[m]);
+          f[2 * m] = Cx<R>{a.x, a.y};
+          f[2 * m + 1] = Cx<R>{a.z, a.w};
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < RR; ++m) f[m] = Cx<R>{0, 0};
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < RR; ++m) f[m] = (*this)(b, s + m);
+    }
+  }
+};
+
 // ---------------------------------------------------------------- matvec, FP64
 // tmp[k][j][i] = c_x (T_x v[k][j][:])_i, rows j = 2q, 2q+1 packed as one complex line
 template <typename TIn>
@@ -314,7 +366,7 @@ __global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_rows
       buf[b * bs + pad16(i)] = (j < My && i < Mx) ? p : C{0, 0};
     }
   }
-  fft_convolve_batched(buf, logLx, B, bs, q, logLx, [&](int, int pf) { return C{__ldg(&Exf[pf]), (R)0}; });
+  fft_convolve_batched(buf, logLx, B, bs, q, logLx, LineReal<R>{Exf});
   for (int idx = threadIdx.x; idx < B * Mx; idx += blockDim.x) {
     const int b = idx / Mx, i = idx - b * Mx, j = j0 + b;
     if (j < My) Tm[slab + (size_t)j * Mx + i] = buf[b * bs + pad16(i)];
@@ -357,7 +409,7 @@ __global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_cols
       buf[b * bs + pad16(j)] = pv[u];
     }
   }
-  fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int, int pf) { return C{__ldg(&Eyf[pf]), (R)0}; });
+  fft_convolve_batched(buf, logLy, B, bs, q, logLy, LineReal<R>{Eyf});
   const C lam = to_c<R>(lambda[n]);
   R sre = 0, sim = 0;
   for (int idx = threadIdx.x; idx < My * B; idx += blockDim.x) {
@@ -474,10 +526,7 @@ __global__ void __launch_bounds__(kLineThreads, sizeof(R) == 4 ? 3 : 1) c2d_cols
     }
   }
   const C* Gn = G + (size_t)n * Lx * Ly;
-  fft_convolve_batched(buf, logLy, B, bs, q, logLy, [&](int b, int pf) {
-    const int p = p0 + b;
-    return p < Lx ? Gn[(size_t)p * Ly + pf] : C{0, 0};
-  });
+  fft_convolve_batched(buf, logLy, B, bs, q, logLy, LineCplx<R>{Gn, p0, Lx, Ly});
   for (int idx = threadIdx.x; idx < My * B; idx += blockDim.x) {
     const int j = idx / B, b = idx - j * B, p = p0 + b;
     if (p < Lx) W[wslab + (size_t)j * Lx + p] = buf[b * bs + pad16(j)];
