@@ -187,61 +187,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) tdft_inv_kernel(c
   }
 }
 
-// Step (c) for Nt >= 64 with the first four radix-2 stages in registers: the first pass of the forward (DIF)
-// transform takes 16 frequencies n = j0 + m Nt/16 of one column pair straight from the half spectrum
-// (Z_n = Xa_n + i Xb_n for n <= Nt/2, conj Xa + i conj Xb at Nt - n above), every load of the pass issued
-// together; the remaining stages run in shared memory, and the output reads the bit-reversed result.
-template <typename R, typename TOut>
-__global__ void __launch_bounds__(256, 4) tdft_inv_reg_kernel(const typename cplx_t<R>::type* __restrict__ in,
-                                                              TOut* __restrict__ z, int M, int logNt,
-                                                              const R* __restrict__ scale_inv,
-                                                              const typename cplx_t<R>::type* __restrict__ tw) {
-  using C = typename cplx_t<R>::type;
-  extern __shared__ unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
-  const int Nt = 1 << logNt, S = Nt >> 4, half = Nt / 2;
-  const int bstride = padded_size(Nt) + 1;
-  const int c0 = blockIdx.x * TW;
-  C* tq = sm + TWH * bstride;
-  load_quarter(tq, tw, Nt / 4);
-  __syncthreads();
-  for (int gg = threadIdx.x; gg < TWH * S; gg += blockDim.x) {
-    const int q = gg & (TWH - 1), j0 = gg / TWH;
-    const int ca = c0 + q, cb = ca + TWH;
-    C w[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int n = j0 + m * S;
-      const bool up = n > half;
-      const int nr = up ? Nt - n : n;  // the stored frequency
-      C Xa = ca < M ? in[(size_t)nr * M + ca] : C{0, 0};
-      C Xb = cb < M ? in[(size_t)nr * M + cb] : C{0, 0};
-      if (nr == 0 || nr == half) { Xa.y = 0; Xb.y = 0; }
-      w[m] = up ? C{Xa.x + Xb.y, Xb.x - Xa.y} : C{Xa.x - Xb.y, Xa.y + Xb.x};  // conj Xa + i conj Xb, or Xa + i Xb
-    }
-    dft<-1, 4>(w);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      if (j0 != 0 && m != 0) w[m] = cmul(w[m], twiddle<-1>(tq, j0 * m, logNt));
-      sm[q * bstride + pad16(j0 + brev_c<4>(m) * S)] = w[m];
-    }
-  }
-  __syncthreads();
-  for (int s0 = 4; s0 < logNt; s0 += 4) {
-    dif_pass_any<C>(min(4, logNt - s0), sm, logNt, s0, TWH, bstride, tq, logNt);
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
-    const int k = idx / TW, cc = idx - k * TW;
-    const int col = c0 + cc;
-    if (col >= M) continue;
-    const int q = cc & (TWH - 1), part = cc / TWH;
-    const C Zk = sm[q * bstride + pad16(bitrev(k, logNt))];
-    const R val = (part == 0 ? Zk.x : Zk.y) * __ldg(&scale_inv[k]);
-    z[(size_t)k * M + col] = (TOut)val;
-  }
-}
-
 static int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 template <typename R>
@@ -282,14 +227,6 @@ template <typename R, typename TOut>
 static cudaError_t inv(const typename cplx_t<R>::type* in, TOut* z, int M, int Nt, const R* scale_inv,
                        const typename cplx_t<R>::type* tw, cudaStream_t s) {
   const size_t smem = tdft_smem<R>(Nt);
-  if constexpr (sizeof(R) == 4) {
-    if (Nt >= 64) {
-      cudaError_t e = allow_max_dynamic_smem(tdft_inv_reg_kernel<R, TOut>);
-      if (e != cudaSuccess) return e;
-      tdft_inv_reg_kernel<R, TOut><<<(M + TW - 1) / TW, 256, smem, s>>>(in, z, M, ilog2i(Nt), scale_inv, tw);
-      return cudaGetLastError();
-    }
-  }
   cudaError_t e = allow_max_dynamic_smem(tdft_inv_kernel<R, TOut>);
   if (e != cudaSuccess) return e;
   tdft_inv_kernel<R, TOut><<<(M + TW - 1) / TW, 256, smem, s>>>(in, z, M, ilog2i(Nt), scale_inv, tw);
