@@ -120,7 +120,9 @@ typedef struct {
                            are a conditional WHILE node inside each step); ignored while profiling
                            or while recording pairs.  0: host-driven steps (2D Step (b) then still
                            runs as one graph launch with its WHILE loop, except while profiling) */
-  aao_matvec_kind matvec; /* [AAO_MATVEC_NTT] 1D matvec arithmetic; 2D always uses FP64 FFTs */
+  aao_matvec_kind matvec; /* [AAO_MATVEC_NTT] matvec arithmetic: exact-integer convolutions of rows quantised
+                           to 58 bits (1D rows; 2D the rows and columns of each time level, one scale per
+                           level), or FP64 FFTs */
   int cocg_threads;     /* [0] mixed 1D, M <= 8192: CTA size of the register-resident COCG kernel
                            (64, 128, 256 or 512, at least M / 16), or AAO_COCG_TMEM: the kernel that
                            keeps the COCG vectors in tensor memory (Strang preconditioner,

@@ -178,6 +178,18 @@ cudaError_t launch_matvec_ntt_fin_dots(const float* v, double* w, int M, int Nt,
                                        double* dots_partial, cudaStream_t s);
 cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                               int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
+// 2D (Eq. 4.2): w = band + c_x T_x v + c_y T_y v (or rhs - that) by exact line convolutions of every time level
+// quantised to 58 bits (one scale per level), tx / ty the tables of the x and y stencils; sq_partial gets
+// ntt2d_partials(Mx, My, Nt) per-CTA sums.  res: ntt2d_scratch_words(Mx, My, Nt) uint32 (8-byte aligned);
+// levelscale: Nt doubles.
+int ntt2d_partials(int Mx, int My, int Nt);
+size_t ntt2d_scratch_words(int Mx, int My, int Nt);
+cudaError_t launch_matvec2d_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int Mx, int My,
+                                int Nt, int logLx, int logLy, const NttTables& tx, const NttTables& ty, uint32_t* res,
+                                double* levelscale, cudaStream_t s);
+cudaError_t launch_matvec2d_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int Mx, int My,
+                                    int Nt, int logLx, int logLy, const NttTables& tx, const NttTables& ty,
+                                    uint32_t* res, double* levelscale, cudaStream_t s);
 cudaError_t launch_matvec_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                                   int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s);
 

@@ -472,6 +472,7 @@ __device__ __forceinline__ double crt4(const uint32_t (&rq)[NP], const uint2* c)
 // Chunks per row of the epilogue: about 8 elements per thread of a 256-thread CTA, so that a matvec's
 // epilogue launches several waves of CTAs instead of one CTA per row.
 inline int epi_chunks(int M) { return (M + 256 * 8 - 1) / (256 * 8); }
+inline int ntt2d_chunks(int Mx, int My) { return ((Mx * My) + 256 * 8 - 1) / (256 * 8); }
 
 // Pass-1 Gram-Schmidt dots fused into the epilogue (the Arnoldi step of the mixed path): with NVMAX > 0 each
 // CTA also writes the partial sums of hi(w) hi(V_i) for i < nv (V: float-float basis vectors of vstride
@@ -573,6 +574,223 @@ cudaError_t launch_ntt(const TIn* v, const double* rhs, double* w, double* sq_pa
   return cudaGetLastError();
 }
 
+// ---- 2D (Eq. 4.2): c_x T_x along the rows and c_y T_y along the columns of every time level, each an
+// exact-integer line convolution of the level quantised to 58 bits with one scale per level -------------
+// A CTA transforms lb lines of one prime in shared memory (each padded by one word per 32; lb from
+// ntt2d_lines_per_cta, at most 16 and at most 96 KB): the same passes as conv_row (forward 16-point passes,
+// the fused middle pass with the stencil spectrum, inverse passes), looped over the lines.
+inline int ntt2d_lines_per_cta(int logL) {
+  const int L = 1 << logL, bytes = (L + L / 32 + 1) * 4;
+  const int b = (96 * 1024) / bytes;
+  return b < 1 ? 1 : (b > 16 ? 16 : b);
+}
+
+template <uint32_t P>
+__device__ __forceinline__ void bdif_pass(uint32_t* buf, int LS, int nb, int logL, int s0, const uint2* __restrict__ tw,
+                                          const uint2 (&wint)[8]) {
+  constexpr int r = 4, R = 16;
+  const int logS = logL - s0 - r, S = 1 << logS, lper = logL - r;
+  for (int gg = threadIdx.x; gg < (nb << lper); gg += blockDim.x) {
+    const int line = gg >> lper, g = gg & ((1 << lper) - 1);
+    const int b = g >> logS, j = g & (S - 1);
+    const int base = (b << (logL - s0)) + j;
+    uint32_t* bl = buf + line * LS;
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = bl[pad32(base + k * S)];
+    dif_core<P, r>(v, wint);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&tw[(k - 1) * S + j]));
+      bl[pad32(base + k * S)] = v[k];
+    }
+  }
+}
+
+template <uint32_t P>
+__device__ __forceinline__ void bdit_pass(uint32_t* buf, int LS, int nb, int logL, int s0, const uint2* __restrict__ twi,
+                                          const uint2 (&wint)[8]) {
+  constexpr int r = 4, R = 16;
+  const int logS = logL - s0 - r, S = 1 << logS, lper = logL - r;
+  for (int gg = threadIdx.x; gg < (nb << lper); gg += blockDim.x) {
+    const int line = gg >> lper, g = gg & ((1 << lper) - 1);
+    const int b = g >> logS, j = g & (S - 1);
+    const int base = (b << (logL - s0)) + j;
+    uint32_t* bl = buf + line * LS;
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      v[k] = bl[pad32(base + k * S)];
+      if (k) v[k] = mulsh<P>(v[k], __ldg(&twi[(k - 1) * S + j]));
+    }
+    dit_core<P, r>(v, wint);
+#pragma unroll
+    for (int k = 0; k < R; ++k) bl[pad32(base + k * S)] = v[k];
+  }
+}
+
+template <uint32_t P, int r>
+__device__ __forceinline__ void bmid(uint32_t* buf, int LS, int nb, int logL, const uint2* __restrict__ gh,
+                                     const uint2* __restrict__ twf, const uint2* __restrict__ twi) {
+  constexpr int R = 1 << r;
+  uint2 wf[8], wi[8];
+  load_roots<r>(wf, twf, logL);
+  load_roots<r>(wi, twi, logL);
+  const int lper = logL - r;
+  for (int gg = threadIdx.x; gg < (nb << lper); gg += blockDim.x) {
+    const int line = gg >> lper, g = gg & ((1 << lper) - 1);
+    const int base = g << r;
+    uint32_t* bl = buf + line * LS;
+    uint32_t v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = bl[pad32(base + k)];
+    dif_core<P, r>(v, wf);
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = mulsh<P>(v[k], __ldg(&gh[base + k]));
+    dit_core<P, r>(v, wi);
+#pragma unroll
+    for (int k = 0; k < R; ++k) bl[pad32(base + k)] = v[k];
+  }
+}
+
+// COL = false: line l = k My + j is row j of level k (M = Mx points, stride 1); COL = true: line l = k Mx + i
+// is column i of level k (M = My points, stride Mx).  Lines are read and written so that consecutive threads
+// touch consecutive addresses (along the row, or across neighbouring columns).
+template <uint32_t P, bool COL>
+__device__ __forceinline__ void conv_lines(const long long* __restrict__ V, int Mx, int My, int nlines, int logL,
+                                           int lb, const NttTables& t, int q, uint32_t* buf,
+                                           uint32_t* __restrict__ out) {
+  const int L = 1 << logL, LS = L + L / 32 + 1;
+  const int M = COL ? My : Mx, per = COL ? Mx : My;  // points per line, lines per level
+  const size_t Ms = (size_t)Mx * My;
+  const int l0 = blockIdx.x * lb;
+  const int nb = min(lb, nlines - l0);
+  auto addr = [&](int line, int i) -> size_t {  // element i of line l0 + line
+    const int l = l0 + line, k = l / per, c = l - k * per;
+    return (size_t)k * Ms + (COL ? (size_t)i * Mx + c : (size_t)c * Mx + i);
+  };
+  for (int idx = threadIdx.x; idx < lb * L; idx += blockDim.x) {
+    const int line = COL ? idx % lb : idx / L, i = COL ? idx / lb : idx % L;
+    if (line >= nb) continue;
+    buf[line * LS + pad32(i)] = i < M ? residue<P>(__ldg(V + addr(line, i))) : 0u;
+  }
+  __syncthreads();
+  const size_t tsz = (size_t)ntt_tw_size(logL);
+  const uint2* twf = t.twf + (size_t)q * tsz;
+  const uint2* twi = t.twi + (size_t)q * tsz;
+  const uint2* gh = t.ghat + (size_t)q * L;
+  const int sl = ntt_last_pass(logL);
+  for (int s0 = 0; s0 < sl; s0 += 4) {
+    uint2 w[8];
+    load_roots<4>(w, twf, logL);
+    bdif_pass<P>(buf, LS, nb, logL, s0, twf + ntt_tw_offset(logL, s0), w);
+    __syncthreads();
+  }
+  switch (logL - sl) {
+    case 1: bmid<P, 1>(buf, LS, nb, logL, gh, twf, twi); break;
+    case 2: bmid<P, 2>(buf, LS, nb, logL, gh, twf, twi); break;
+    case 3: bmid<P, 3>(buf, LS, nb, logL, gh, twf, twi); break;
+    default: bmid<P, 4>(buf, LS, nb, logL, gh, twf, twi); break;
+  }
+  __syncthreads();
+  for (int s0 = sl - 4; s0 >= 0; s0 -= 4) {
+    uint2 w[8];
+    load_roots<4>(w, twi, logL);
+    bdit_pass<P>(buf, LS, nb, logL, s0, twi + ntt_tw_offset(logL, s0), w);
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < lb * M; idx += blockDim.x) {
+    const int line = COL ? idx % lb : idx / M, i = COL ? idx / lb : idx % M;
+    if (line >= nb) continue;
+    out[addr(line, i)] = red1<P>(buf[line * LS + pad32(i)]);
+  }
+}
+
+// grid (ceil(nlines / lb), NP); res: [NP][Nt Mx My] residues of this direction
+template <bool COL>
+__global__ void __launch_bounds__(256) ntt2d_lines_kernel(const long long* __restrict__ V, int Mx, int My, int Nt,
+                                                          int logL, int lb, NttTables t, uint32_t* __restrict__ res) {
+  extern __shared__ uint32_t nbuf[];
+  const int q = blockIdx.y;
+  const int nlines = Nt * (COL ? Mx : My);
+  uint32_t* out = res + (size_t)q * Nt * Mx * My;
+  switch (q) {
+    case 0: conv_lines<Prime<0>::p, COL>(V, Mx, My, nlines, logL, lb, t, q, nbuf, out); break;
+    case 1: conv_lines<Prime<1>::p, COL>(V, Mx, My, nlines, logL, lb, t, q, nbuf, out); break;
+    case 2: conv_lines<Prime<2>::p, COL>(V, Mx, My, nlines, logL, lb, t, q, nbuf, out); break;
+    default: conv_lines<Prime<3>::p, COL>(V, Mx, My, nlines, logL, lb, t, q, nbuf, out); break;
+  }
+}
+
+// w = band + c_x T_x v + c_y T_y v (or rhs - that), both products reconstructed from their residues; grid
+// (chunks, Nt), per-CTA sums of squares at sq_partial[k chunks + chunk]
+template <typename TIn>
+__global__ void __launch_bounds__(256) ntt2d_epilogue_kernel(const TIn* __restrict__ v, const double* __restrict__ rhs,
+                                                             double* __restrict__ w, double* __restrict__ sq_partial,
+                                                             int Ms, int Nt, const uint32_t* __restrict__ rx,
+                                                             const uint32_t* __restrict__ ry,
+                                                             const double* __restrict__ levelscale, NttTables tx,
+                                                             NttTables ty) {
+  __shared__ double redb[32];
+  const int k = blockIdx.y;
+  const int chunk = (Ms + gridDim.x - 1) / gridDim.x;
+  const int e0 = blockIdx.x * chunk, e1 = min(Ms, e0 + chunk);
+  const double fx = tx.c_gscale * levelscale[k], fy = ty.c_gscale * levelscale[k];
+  const size_t n = (size_t)Nt * Ms, base = (size_t)k * Ms;
+  double sq = 0.0;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    uint32_t ax[NP], ay[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      ax[q] = rx[q * n + base + e];
+      ay[q] = ry[q * n + base + e];
+    }
+    const double y = fx * crt4(ax, tx.crt) + fy * crt4(ay, ty.crt);
+    const TIn* vk = v + base + e;
+    double band;
+    if (k == 0) band = ldd(vk);
+    else if (k == 1) band = 1.5 * ldd(vk) - 2.0 * ldd(vk - Ms);
+    else band = 1.5 * ldd(vk) - 2.0 * ldd(vk - Ms) + 0.5 * ldd(vk - 2 * (size_t)Ms);
+    double out = band + y;
+    if (rhs) out = rhs[base + e] - out;
+    w[base + e] = out;
+    sq += out * out;
+  }
+  if (sq_partial) {
+    double a[1] = {sq};
+    block_sum<double, 1>(a, redb);
+    if (threadIdx.x == 0) sq_partial[(size_t)k * gridDim.x + blockIdx.x] = a[0];
+  }
+}
+
+template <typename TIn>
+cudaError_t launch_ntt2d(const TIn* v, const double* rhs, double* w, double* sq_partial, int Mx, int My, int Nt,
+                         int logLx, int logLy, const NttTables& tx, const NttTables& ty, uint32_t* res,
+                         double* levelscale, cudaStream_t s) {
+  const size_t Ms = (size_t)Mx * My, n = Ms * Nt;
+  uint32_t* rx = res;
+  uint32_t* ry = res + (size_t)NP * n;
+  long long* V = reinterpret_cast<long long*>(res + (size_t)2 * NP * n);  // after both residue sets
+  if constexpr (sizeof(TIn) == 4) ntt_quant_f32_kernel<QBITS><<<Nt, 512, 0, s>>>(v, (int)Ms, V, levelscale);
+  else ntt_quant_kernel<TIn><<<Nt, 512, 0, s>>>(v, (int)Ms, V, levelscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int Lx = 1 << logLx, Ly = 1 << logLy;
+  const int bx = ntt2d_lines_per_cta(logLx), by = ntt2d_lines_per_cta(logLy);
+  const size_t smx = (size_t)bx * (Lx + Lx / 32 + 1) * sizeof(uint32_t);
+  const size_t smy = (size_t)by * (Ly + Ly / 32 + 1) * sizeof(uint32_t);
+  e = allow_max_dynamic_smem(ntt2d_lines_kernel<false>);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem(ntt2d_lines_kernel<true>);
+  if (e != cudaSuccess) return e;
+  ntt2d_lines_kernel<false><<<dim3((Nt * My + bx - 1) / bx, NP), 256, smx, s>>>(V, Mx, My, Nt, logLx, bx, tx, rx);
+  ntt2d_lines_kernel<true><<<dim3((Nt * Mx + by - 1) / by, NP), 256, smy, s>>>(V, Mx, My, Nt, logLy, by, ty, ry);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ntt2d_epilogue_kernel<TIn><<<dim3(ntt2d_chunks(Mx, My), Nt), 256, 0, s>>>(v, rhs, w, sq_partial, (int)Ms, Nt, rx, ry,
+                                                                           levelscale, tx, ty);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int ntt_partials(int M, int Nt) { return Nt * epi_chunks(M); }
@@ -592,6 +810,20 @@ cudaError_t launch_matvec_ntt(const double* v, const double* rhs, double* w, dou
 cudaError_t launch_matvec_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int M, int Nt,
                                   int logL, const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s) {
   return launch_ntt<float>(v, rhs, w, sq_partial, M, Nt, logL, t, res, rowscale, s);
+}
+
+int ntt2d_partials(int Mx, int My, int Nt) { return Nt * ntt2d_chunks(Mx, My); }
+size_t ntt2d_scratch_words(int Mx, int My, int Nt) { return (size_t)(2 * kNttPrimes + 2) * Mx * My * Nt; }
+
+cudaError_t launch_matvec2d_ntt(const double* v, const double* rhs, double* w, double* sq_partial, int Mx, int My,
+                                int Nt, int logLx, int logLy, const NttTables& tx, const NttTables& ty, uint32_t* res,
+                                double* levelscale, cudaStream_t s) {
+  return launch_ntt2d<double>(v, rhs, w, sq_partial, Mx, My, Nt, logLx, logLy, tx, ty, res, levelscale, s);
+}
+cudaError_t launch_matvec2d_ntt_fin(const float* v, const double* rhs, double* w, double* sq_partial, int Mx, int My,
+                                    int Nt, int logLx, int logLy, const NttTables& tx, const NttTables& ty,
+                                    uint32_t* res, double* levelscale, cudaStream_t s) {
+  return launch_ntt2d<float>(v, rhs, w, sq_partial, Mx, My, Nt, logLx, logLy, tx, ty, res, levelscale, s);
 }
 
 }  // namespace aao

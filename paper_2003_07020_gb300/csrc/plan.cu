@@ -250,8 +250,11 @@ struct aao_plan {
   // exact-integer matvec (opts.matvec == AAO_MATVEC_NTT, 1D)
   bool ntt = false;
   aao::NttTables ntt_tab{};
-  uint32_t* ntt_res = nullptr;  // 5 n residues + n int64 quantised entries
-  double* ntt_rowscale = nullptr;
+  uint32_t* ntt_res = nullptr;  // 1D: 4 n residues + n int64 quantised entries; 2D: 2 x 4 n residues + n int64
+  double* ntt_rowscale = nullptr;  // one scale per time row (1D) or per time level (2D)
+  // exact-integer 2D matvec (opts.matvec == AAO_MATVEC_NTT, dim 2): ntt_tab holds the x stencil, this the y one
+  bool ntt2d = false;
+  aao::NttTables ntt_tab_y{};
   int* iters = nullptr;
   int* flags = nullptr;
   int* stats = nullptr;
@@ -387,6 +390,17 @@ aao_status reduce_to_host(aao_plan* p, const double* partials, int nblocks, int 
 }
 
 aao_status matvec_any(aao_plan* p, const void* v, bool v_is_f32, const double* rhs, double* w, double* sq) {
+  if (p->dim == 2 && p->ntt2d) {
+    if (v_is_f32)
+      LAUNCH(ST_MATVEC, 4, aao::launch_matvec2d_ntt_fin((const float*)v, rhs, w, sq, p->M, p->My, p->Nt, p->logL,
+                                                        p->logLy, p->ntt_tab, p->ntt_tab_y, p->ntt_res,
+                                                        p->ntt_rowscale, p->stream));
+    else
+      LAUNCH(ST_MATVEC, 4, aao::launch_matvec2d_ntt((const double*)v, rhs, w, sq, p->M, p->My, p->Nt, p->logL,
+                                                    p->logLy, p->ntt_tab, p->ntt_tab_y, p->ntt_res, p->ntt_rowscale,
+                                                    p->stream));
+    return AAO_OK;
+  }
   if (p->dim == 2) {
     if (v_is_f32)
       LAUNCH(ST_MATVEC, 2, aao::launch_matvec2d_f64_fin((const float*)v, rhs, w, p->tmp2d, sq, p->M, p->My, p->Nt,
@@ -1112,6 +1126,27 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
       return bail(AAO_ECUDA);
     }
     p->nsq = aao::mv2d_partials(p->M, p->Nt, p->logLy);
+    if (opts->matvec == AAO_MATVEC_NTT) {
+      // exact-integer line convolutions along x and y (Eq. 4.2), one quantisation scale per time level
+      for (int d = 0; d < 2; ++d) {
+        aao::HostTables& hd = d ? p->hty : p->ht;
+        aao::NttTables& nt = d ? p->ntt_tab_y : p->ntt_tab;
+        aao::build_ntt_tables(hd);
+        uint32_t* q32;
+        TRYP(upload(p, &q32, hd.ntt_twf));
+        nt.twf = (const uint2*)q32;
+        TRYP(upload(p, &q32, hd.ntt_twi));
+        nt.twi = (const uint2*)q32;
+        TRYP(upload(p, &q32, hd.ntt_ghat));
+        nt.ghat = (const uint2*)q32;
+        for (int i = 0; i < 6; ++i) nt.crt[i] = make_uint2(hd.ntt_crt[2 * i], hd.ntt_crt[2 * i + 1]);
+        nt.c_gscale = hd.ntt_c_gscale;
+      }
+      TRYP(dalloc(p, &p->ntt_res, aao::ntt2d_scratch_words(p->M, p->My, p->Nt)));
+      TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));
+      p->nsq = (size_t)aao::ntt2d_partials(p->M, p->My, p->Nt);
+      p->ntt2d = true;
+    }
     if (opts->inner == AAO_INNER_STRANG) {
       // 2D Strang (BCCB): per-direction spectral maps on the host, the per-system spectra on the device
       std::vector<aao::cd> qx, qy;

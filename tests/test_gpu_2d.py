@@ -41,15 +41,35 @@ def jacs(Mx, My, ax, ay, kx=1.0, ky=1.0):
 CASES = [(15, 7, 8, 1.3, 1.7), (31, 63, 16, 1.5, 1.2), (7, 3, 4, 1.9, 1.1), (255, 255, 4, 1.3, 1.7)]
 
 
+@pytest.mark.parametrize("kind", [aao.AAO_MATVEC_NTT, aao.AAO_MATVEC_FFT64])
 @pytest.mark.parametrize("Mx,My,Nt,ax,ay", CASES)
-def test_matvec_2d(Mx, My, Nt, ax, ay):
+def test_matvec_2d(Mx, My, Nt, ax, ay, kind):
+    # exact-integer line convolutions (default) and FP64 FFTs: 1e-13 in norm, and for the exact form every
+    # element within 1e-13 of the largest (the 58-bit level quantisation is the only rounding before FP64)
     v = np.random.default_rng(Mx + My).standard_normal((Nt, My, Mx))
-    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay) as plan:
+    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, matvec=kind) as plan:
         w = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
         plan.matvec(cu(v), w)
         torch.cuda.synchronize()
     Kx, Ky = jacs(Mx, My, ax, ay)
-    assert rel(host(w), oaao.matvec_2d(Kx, Ky, 1.0 / Nt, v)) <= 1e-13
+    want = oaao.matvec_2d(Kx, Ky, 1.0 / Nt, v)
+    assert rel(host(w), want) <= 1e-13
+    if kind == aao.AAO_MATVEC_NTT:
+        assert np.abs(host(w) - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_gmres_2d_with_the_fp64_fft_matvec():
+    Mx, My, Nt, ax, ay = 31, 15, 16, 1.4, 1.6
+    u0, f = workloads.make_inputs_2d(Mx, My, Nt, seed=3)
+    Kx, Ky = jacs(Mx, My, ax, ay)
+    Useq = oaao.sequential_bdf2_2d(Kx, Ky, 1.0 / Nt, u0, f)
+    with aao.Plan(Mx, Nt, ax, My=My, alpha_y=ay, matvec=aao.AAO_MATVEC_FFT64) as plan:
+        F = torch.empty((Nt, My, Mx), dtype=torch.float64, device=DEV)
+        plan.build_rhs(cu(u0), cu(f), F)
+        U = torch.zeros_like(F)
+        info = plan.gmres_solve(F, U)
+    assert info["true_rel_res"] <= 1e-10, info
+    assert rel(host(U), Useq) <= 1e-9
 
 
 INNERS = [aao.AAO_INNER_STRANG, aao.AAO_INNER_TAU]
