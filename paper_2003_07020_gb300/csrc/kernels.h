@@ -164,7 +164,8 @@ struct NttTables {
   const uint2* ghat;    // [4][L] stencil spectrum, bit-reversed, times L^-1
   uint2 crt[6];         // Garner constants (c, floor(c 2^32 / p_b)): p0^-1 mod p1, p2, p3, p1^-1 mod p2, p3,
                         // p2^-1 mod p3
-  double c_gscale;      // c 2^(e_g - 58)
+  double c_gscale;      // 2^(e_g - 58): the stencil is c g quantised, G_j = round(c g_j 2^(58 - e_g))
+  int gexp;             // e_g - 58
 };
 // w = calA v (or rhs - calA v) with c T v_k by exact NTT convolution of the row quantised to 58 bits
 // (same contract as launch_matvec_f64; sq_partial gets ntt_partials(M, Nt) per-CTA sums).  res: 6 n uint32

@@ -5,15 +5,15 @@
 //
 // Row k of v is scaled by a power of two so that its largest magnitude lies in
 // [2^57, 2^58) and rounded to integers V (quantisation error 2^-59 of the row's
-// largest entry); the FCD stencil g is quantised the same way once at plan
-// creation (G, G_0 <= 2^58).  The linear convolution Y = G * V is bounded by
+// largest entry); the FCD stencil times c (c > 0) is quantised the same way
+// once at plan creation (G, G_0 <= 2^58).  The linear convolution Y = G * V is bounded by
 // max|V| sum_d |G_d|, and the FCD weights have g_0 > 0 >= g_d (d >= 1) with
 // sum over all d of g_d = 0 (Lemma 2.1), so sum_d |G_d| <= 2 G_0 + M (the
 // rounding) and |Y| < 2^117 (1 + 2^-45).  Four NTT primes p_q < 2^30 (product
 // ~2^119.5) therefore determine Y exactly: it is computed by cyclic
 // convolution of length L >= 2M - 1 (circulant embedding) modulo each prime,
-// reconstructed by Garner's mixed-radix CRT and converted to FP64:
-// c T v_k = c 2^(e_v + e_g - 116) Y.
+// reconstructed by Garner's mixed-radix CRT and rounded to FP64 once:
+// c T v_k = 2^(e_v + e_g - 116) Y, the power of two applied to the exponent.
 //
 // Kernel 0 (ntt_quant_kernel): one CTA per time row: the row's scale and its
 // int64 quantisation (the only FP64 work before the epilogue).
@@ -408,9 +408,14 @@ template <int B> __device__ __forceinline__ uint32_t gstep(uint32_t r, uint32_t 
 }
 
 // Garner's mixed-radix digits d_q of the four residues r_q, then Y = d0 + p0 (d1 + p1 (d2 + p2 d3)) in
-// integer arithmetic, converted to FP64 once (correctly rounded); negative when d3 > p3 / 2 (|Y| < 2^117.01,
-// below half the product).
-__device__ __forceinline__ double crt4(const uint32_t (&rq)[NP], const uint2* c) {
+// integer arithmetic; negative when d3 > p3 / 2 (|Y| < 2^117.01, below half the product).  Returns the 64
+// leading bits of |Y| with a sticky bit in bit 0 (top) and the weight of its lowest bit (|Y| ~ top 2^sh).
+struct CrtTop {
+  uint64_t top;
+  int sh;
+  bool neg;
+};
+__device__ __forceinline__ CrtTop crt4_top(const uint32_t (&rq)[NP], const uint2* c) {
   constexpr uint64_t p0 = Prime<0>::p, p1 = Prime<1>::p, p2 = Prime<2>::p, p3 = Prime<3>::p;
   // c: p0^-1 mod p1, p2, p3 (c[0..2]), p1^-1 mod p2, p3 (c[3..4]), p2^-1 mod p3 (c[5])
   uint32_t d[NP];
@@ -419,7 +424,7 @@ __device__ __forceinline__ double crt4(const uint32_t (&rq)[NP], const uint2* c)
   d[2] = gstep<2>(gstep<2>(rq[2], d[0], c[1]), d[1], c[3]);
   d[3] = gstep<3>(gstep<3>(gstep<3>(rq[3], d[0], c[2]), d[1], c[4]), d[2], c[5]);
   // Y as a 3-limb integer from the mixed-radix digits; when negative, |Y| = (P - 1 - Y) + 1 with the
-  // complemented digits p_q - 1 - d_q, converted once.
+  // complemented digits p_q - 1 - d_q
   const uint64_t pm[NP] = {p0, p1, p2, p3};
   const bool neg = d[NP - 1] > pm[NP - 1] / 2;
   uint64_t e[NP];
@@ -447,26 +452,80 @@ __device__ __forceinline__ double crt4(const uint32_t (&rq)[NP], const uint2* c)
     l1 += cc;
     l2 += (cc && l1 == 0);
   }
-  // top 64 significant bits with a sticky bit (correct rounding), times 2^shift
-  uint64_t top;
-  int sh;
+  CrtTop r;
+  r.neg = neg;
   if (l2) {
     const int z = __clzll(l2);
-    top = z ? (l2 << z) | (l1 >> (64 - z)) : l2;
+    r.top = z ? (l2 << z) | (l1 >> (64 - z)) : l2;
     const uint64_t rest = z ? (l1 << z) | l0 : (l1 | l0);
-    top |= (rest != 0);
-    sh = 128 - z;
+    r.top |= (rest != 0);
+    r.sh = 128 - z;
   } else if (l1) {
     const int z = __clzll(l1);
-    top = z ? (l1 << z) | (l0 >> (64 - z)) : l1;
-    top |= (z ? (l0 << z) : l0) != 0;
-    sh = 64 - z;
+    r.top = z ? (l1 << z) | (l0 >> (64 - z)) : l1;
+    r.top |= (z ? (l0 << z) : l0) != 0;
+    r.sh = 64 - z;
   } else {
-    top = l0;
-    sh = 0;
+    r.top = l0;
+    r.sh = 0;
   }
-  const double mag = __ull2double_rn(top) * __longlong_as_double((long long)(1023 + sh) << 52);
-  return neg ? -mag : mag;
+  return r;
+}
+
+// (+-) top 2^(sh + E) correctly rounded to FP64.  A normal result is assembled from the bits by integer
+// operations (round half to even on the 53 leading bits; a carry out of the significand moves into the
+// exponent field by the addition); zero stays zero; results outside the normal range take the conversion and
+// ldexp on the FP64 pipe.
+__device__ __forceinline__ double crt_to_double(CrtTop t, int E) {
+  if (t.top == 0) return 0.0;
+  const int z = __clzll(t.top);
+  const uint64_t top = t.top << z;
+  const int be = t.sh - z + E + 63 + 1023;  // biased exponent of the leading bit
+  if (be < 1 || be > 2045) {
+    const double m = ldexp(__ull2double_rn(top), t.sh - z + E);
+    return t.neg ? -m : m;
+  }
+  uint64_t m = top >> 11;
+  m += ((top >> 10) & 1ull) & ((uint64_t)((top & 0x3ffull) != 0) | (m & 1ull));
+  const uint64_t bits = ((uint64_t)(be - 1) << 52) + m;
+  return __longlong_as_double((long long)(bits | ((uint64_t)t.neg << 63)));
+}
+
+// The row scale 2^(e_v - 58) as its exponent when it is a normal power of two (fast: the epilogue adds it to
+// the exponent); a zero row (scale 0) or a row with a non-finite entry (scale NaN) gives fast = false and the
+// epilogue multiplies by the scale instead, which keeps 0 and NaN.
+__device__ __forceinline__ int pow2_exponent(double s, bool& fast) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  fast = (b >> 63) == 0 && (b & 0xfffffffffffffull) == 0 && ex != 0 && ex != 0x7ff;
+  return ex - 1023;
+}
+
+// Widened FP32 value times 2^d (|d| <= 1) from the bits for zero and normal f; other f take the FP64 pipe.
+__device__ __forceinline__ double f2d_bits_pow2(float f, int d) {
+  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ex == 0 || ex == 255) return (double)f * (d > 0 ? 2.0 : 0.5);
+  return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u + (unsigned)d) << 20) | ((u & 0x7fffffu) >> 3)),
+                          (int)((u & 0x7u) << 29));
+}
+
+// The BDF2 band of time row k at element i (Eq. 2.5: row 0 the BDF1 start): v_k, 1.5 v_k - 2 v_{k-1}, or
+// 1.5 v_k - 2 v_{k-1} + 0.5 v_{k-2}; vk points at v_k[i], rows are `stride` apart.  FP32 rows are widened with
+// the factors 2 and 1/2 folded into the exponent (two FP64 operations for a full band instead of three).
+__device__ __forceinline__ double bdf_band(const double* vk, size_t stride, int k) {
+  const double a = __ldg(vk);
+  if (k == 0) return a;
+  const double b = __ldg(vk - stride);
+  if (k == 1) return fma(1.5, a, -2.0 * b);
+  return fma(1.5, a, fma(-2.0, b, 0.5 * __ldg(vk - 2 * stride)));
+}
+__device__ __forceinline__ double bdf_band(const float* vk, size_t stride, int k) {
+  const double a = f2d_bits(__ldg(vk));
+  if (k == 0) return a;
+  const double b2 = -f2d_bits_pow2(__ldg(vk - stride), 1);
+  if (k == 1) return fma(1.5, a, b2);
+  return fma(1.5, a, b2 + f2d_bits_pow2(__ldg(vk - 2 * stride), -1));
 }
 
 // Chunks per row of the epilogue: about 8 elements per thread of a 256-thread CTA, so that a matvec's
@@ -495,10 +554,11 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
   const int k = blockIdx.x;
   const int chunk = (M + gridDim.y - 1) / gridDim.y;
   const int i0 = blockIdx.y * chunk, i1 = min(M, i0 + chunk);
-  const double f = t.c_gscale * rowscale[k];  // c 2^(e_g - 58) 2^(e_v - 58)
+  const double rs = rowscale[k];  // 2^(e_v - 58)
+  bool fast;
+  const int E = t.gexp + pow2_exponent(rs, fast);
+  const double f = t.c_gscale * rs;  // 2^(e_g - 58) 2^(e_v - 58), for rows whose scale is 0 or NaN
   const TIn* vk = v + (size_t)k * M;
-  const TIn* vk1 = vk - M;
-  const TIn* vk2 = vk - 2 * M;
   double* wk = w + (size_t)k * M;
   const double* rk = rhs ? rhs + (size_t)k * M : nullptr;
   const size_t n = (size_t)Nt * M, base = (size_t)k * M;
@@ -514,12 +574,8 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
 #pragma unroll
     for (int q = 0; q < NVMAX; ++q)
       if (q < fd.nv) vh[q] = __ldg(&fd.V[q * fd.vstride + base + i]).x;
-    const double y = f * crt4(rq, t.crt);
-    double band;
-    if (k == 0) band = ldd(vk + i);
-    else if (k == 1) band = 1.5 * ldd(vk + i) - 2.0 * ldd(vk1 + i);
-    else band = 1.5 * ldd(vk + i) - 2.0 * ldd(vk1 + i) + 0.5 * ldd(vk2 + i);
-    double out = band + y;
+    const double y = fast ? crt_to_double(crt4_top(rq, t.crt), E) : f * crt_to_double(crt4_top(rq, t.crt), 0);
+    double out = bdf_band(vk + i, (size_t)M, k) + y;
     if (rk) out = rk[i] - out;
     wk[i] = out;
     sq += out * out;
@@ -735,7 +791,10 @@ __global__ void __launch_bounds__(256) ntt2d_epilogue_kernel(const TIn* __restri
   const int k = blockIdx.y;
   const int chunk = (Ms + gridDim.x - 1) / gridDim.x;
   const int e0 = blockIdx.x * chunk, e1 = min(Ms, e0 + chunk);
-  const double fx = tx.c_gscale * levelscale[k], fy = ty.c_gscale * levelscale[k];
+  const double ls = levelscale[k];  // 2^(e_v - 58)
+  bool fast;
+  const int ev = pow2_exponent(ls, fast);
+  const double fx = tx.c_gscale * ls, fy = ty.c_gscale * ls;  // for levels whose scale is 0 or NaN
   const size_t n = (size_t)Nt * Ms, base = (size_t)k * Ms;
   double sq = 0.0;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -745,13 +804,10 @@ __global__ void __launch_bounds__(256) ntt2d_epilogue_kernel(const TIn* __restri
       ax[q] = rx[q * n + base + e];
       ay[q] = ry[q * n + base + e];
     }
-    const double y = fx * crt4(ax, tx.crt) + fy * crt4(ay, ty.crt);
-    const TIn* vk = v + base + e;
-    double band;
-    if (k == 0) band = ldd(vk);
-    else if (k == 1) band = 1.5 * ldd(vk) - 2.0 * ldd(vk - Ms);
-    else band = 1.5 * ldd(vk) - 2.0 * ldd(vk - Ms) + 0.5 * ldd(vk - 2 * (size_t)Ms);
-    double out = band + y;
+    const double y = fast ? crt_to_double(crt4_top(ax, tx.crt), tx.gexp + ev) +
+                                crt_to_double(crt4_top(ay, ty.crt), ty.gexp + ev)
+                          : fx * crt_to_double(crt4_top(ax, tx.crt), 0) + fy * crt_to_double(crt4_top(ay, ty.crt), 0);
+    double out = bdf_band(v + base + e, (size_t)Ms, k) + y;
     if (rhs) out = rhs[base + e] - out;
     w[base + e] = out;
     sq += out * out;

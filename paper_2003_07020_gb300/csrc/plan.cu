@@ -1074,6 +1074,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
     p->ntt_tab.ghat = (const uint2*)q32;
     for (int i = 0; i < 6; ++i) p->ntt_tab.crt[i] = make_uint2(p->ht.ntt_crt[2 * i], p->ht.ntt_crt[2 * i + 1]);
     p->ntt_tab.c_gscale = p->ht.ntt_c_gscale;
+    p->ntt_tab.gexp = p->ht.ntt_gexp;
     TRYP(dalloc(p, &p->ntt_res, (size_t)(aao::kNttPrimes + 2) * n));  // residues + int64 quantised rows
     TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));
     p->ntt = true;
@@ -1141,6 +1142,7 @@ aao_status aao_plan_create(const aao_problem* prob, const aao_opts* opts, void* 
         nt.ghat = (const uint2*)q32;
         for (int i = 0; i < 6; ++i) nt.crt[i] = make_uint2(hd.ntt_crt[2 * i], hd.ntt_crt[2 * i + 1]);
         nt.c_gscale = hd.ntt_c_gscale;
+        nt.gexp = hd.ntt_gexp;
       }
       TRYP(dalloc(p, &p->ntt_res, aao::ntt2d_scratch_words(p->M, p->My, p->Nt)));
       TRYP(dalloc(p, &p->ntt_rowscale, (size_t)p->Nt));

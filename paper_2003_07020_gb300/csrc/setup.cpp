@@ -270,12 +270,15 @@ void build_ntt_tables(HostTables& t) {
   const int64_t L = t.L, M = t.M;
   const int logL = t.logL;
   constexpr int NP = kNttPrimes, QB = 58;
-  // quantised stencil: G_j = round(g_j 2^(58 - e_g)), g_0 = max |g_j| < 2^e_g
+  // quantised stencil of c T: G_j = round(c g_j 2^(58 - e_g)), c g_0 = max |c g_j| < 2^e_g (c > 0).  The scale of
+  // the product, 2^(e_g - 58) 2^(e_v - 58), is then a power of two, which the epilogue applies to the exponent
+  // of the reconstructed integer instead of multiplying in FP64.
   int eg = 0;
-  std::frexp(t.g[0], &eg);
+  std::frexp(t.c * t.g[0], &eg);
   std::vector<int64_t> G((size_t)M);
-  for (int64_t j = 0; j < M; ++j) G[j] = std::llround(std::ldexp(t.g[j], QB - eg));
-  t.ntt_c_gscale = t.c * std::ldexp(1.0, eg - QB);
+  for (int64_t j = 0; j < M; ++j) G[j] = std::llround(std::ldexp(t.c * t.g[j], QB - eg));
+  t.ntt_c_gscale = std::ldexp(1.0, eg - QB);
+  t.ntt_gexp = eg - QB;
   const size_t tsz = (size_t)ntt_tw_size(logL);
   t.ntt_twf.assign((size_t)NP * tsz * 2, 0);
   t.ntt_twi.assign((size_t)NP * tsz * 2, 0);

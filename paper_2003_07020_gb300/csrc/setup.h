@@ -47,7 +47,8 @@ struct HostTables {
   std::vector<uint32_t> ntt_twi;    // [4][ntt_tw_size][2]: the same for w_q^-1
   std::vector<uint32_t> ntt_ghat;   // [4][L][2]: NTT of the quantised stencil embedding, bit-reversed, times L^-1
   uint32_t ntt_crt[12] = {0};       // Garner constants and their Shoup companions (see ntt.cu)
-  double ntt_c_gscale = 0;          // c 2^(e_g - 58): G_j = round(g_j 2^(58 - e_g))
+  double ntt_c_gscale = 0;          // 2^(e_g - 58): G_j = round(c g_j 2^(58 - e_g))
+  int ntt_gexp = 0;                 // e_g - 58
 };
 
 // Builds the NTT matvec tables of t (after build_tables); primes and generators are
