@@ -334,9 +334,8 @@ aao_status aao_plan_get_inner_record(aao_plan* plan, int n_sys, int* iters_host,
  * live in one fixed 16 MiB device array of the library, held by every GPU
  * that loads it until the process exits; problems whose scratch
  * (nsys * M * 8 bytes plus tables, nsys = Nt/2 + 1) exceeds it are rejected
- * with AAO_EINVAL.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Each
- * call writes its tables into the array with small kernels that carry them
+ * with AAO_EINVAL.  Every call looks up the array's address on the current
+ * device (cudaGetSymbolAddress).  Each call writes its tables into the array with small kernels that carry them
  * as launch parameters, so it copies nothing from pageable host memory and
  * does not wait for work already queued on cuda_stream.  Calls share the
  * array, so calls that overlap on the GPU race.  The shifted solves are not

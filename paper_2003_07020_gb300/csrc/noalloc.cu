@@ -13,9 +13,9 @@
 // array.
 //
 // The array is kNoAllocScratchBytes (16 MiB) and is held by every GPU that
-// loads the library until the process exits.  Its address is taken with
-// cudaGetSymbolAddress once per device, on the first call with that device
-// current (so that first call should come before any stream capture).
+// loads the library until the process exits.  Every call looks up its
+// address on the current device with cudaGetSymbolAddress (a cached address
+// would go stale when the context is recreated, e.g. after cudaDeviceReset).
 // Every call reuses the whole array and overwrites what the previous call
 // left there; nothing in it has to start at zero (each region is fully
 // written before it is read).  Two calls whose work overlaps on the GPU
@@ -30,7 +30,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -41,7 +40,6 @@
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -65,9 +63,6 @@ __global__ void write_chunk_kernel(const __grid_constant__ TableChunk c) {
     c.dst[i] = c.data[i];
 }
 
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 aao_status noalloc_fail(aao_status st, const std::string& msg) {
@@ -75,21 +70,13 @@ aao_status noalloc_fail(aao_status st, const std::string& msg) {
   return st;
 }
 
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device, looked up on every call.
 aao_status scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(AAO_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(AAO_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return noalloc_fail(AAO_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return noalloc_fail(AAO_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return AAO_OK;
 }
 
