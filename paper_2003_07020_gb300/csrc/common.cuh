@@ -552,16 +552,29 @@ __device__ void fft_forward_fused(T* buf, int logN, const T* q, int logNq, const
   __syncthreads();
 }
 
-// (double) f from the bits for zero and normal f (exact, like the conversion, but with integer operations: the
-// FP64<->FP32 conversions issue on the FP64 pipe of this GPU, under 1 per clock per SM); denormal and
-// non-finite f take the conversion.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0 || ex == 255) return (double)f;
-  return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3)),
-                          (int)((u & 0x7u) << 29));
+// (double) f * 2^d (d in {-1, 0, 1}) from the bits of f, exactly, with integer operations only: the FP64<->FP32
+// conversions issue on the FP64 pipe of this GPU (under 1 per clock per SM), and a conversion kept for the rare
+// cases would be evaluated for every element when the compiler turns the branch into a select.  Zero keeps its
+// sign, a subnormal f is normalised (its leading one at bit p of the significand gives the exponent p - 149),
+// infinities and NaNs keep their payload (the quiet bit moves to the FP64 quiet bit).
+__device__ __forceinline__ double f2d_exact(float f, int d = 0) {
+  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned long long bits;
+  if (ex == 255u) {
+    bits = sign | (0x7ffull << 52) | ((unsigned long long)man << 29);
+  } else if (ex != 0u) {
+    bits = sign | ((unsigned long long)(ex + 896u + d) << 52) | ((unsigned long long)man << 29);
+  } else if (man == 0u) {
+    bits = sign;
+  } else {
+    const int p = 31 - __clz((int)man);  // 0 <= p <= 22
+    bits = sign | ((unsigned long long)(p + 874 + d) << 52) |
+           (((unsigned long long)man << (52 - p)) & 0xfffffffffffffull);
+  }
+  return __longlong_as_double((long long)bits);
 }
+__device__ __forceinline__ double f2d_bits(float f) { return f2d_exact(f, 0); }
 
 // Copies the quarter twiddle table (n4 entries) from global to shared memory.
 template <typename T>

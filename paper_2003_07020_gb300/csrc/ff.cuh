@@ -25,15 +25,19 @@ __device__ __forceinline__ float2 ff_from_double(double x) {
 }
 __device__ __forceinline__ double ff_to_double(float2 x) { return (double)x.x + (double)x.y; }
 
+// The conversions of ff_from_double out of line: a call is never evaluated speculatively, so the rare branch of
+// ff_split costs the common one nothing on the FP64 pipe.
+static __device__ __noinline__ float2 ff_from_double_call(double x) { return ff_from_double(x); }
+
 // The same split with integer operations only (FP64<->FP32 conversions issue on the FP64 pipe, under 1 per
 // clock per SM on this GPU): for 2^-74 <= |x| < 2^127, hi = x truncated to its 24 leading significant bits
 // (exact in FP32) and lo = the remaining 29 bits correctly rounded to FP32 (|lo| < ulp(hi)), so
-// |hi + lo - x| <= 2^-48 |x|.  Other x (zero, tiny, huge, non-finite) take the conversions.
+// |hi + lo - x| <= 2^-48 |x|.  Other x (zero, tiny, huge, non-finite) take the conversions, out of line.
 __device__ __forceinline__ float2 ff_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
   const int e = (int)((hw >> 20) & 0x7ffu);  // biased exponent of x
-  if (e < 949 || e > 1150) return ff_from_double(x);
+  if (e < 949 || e > 1150) return ff_from_double_call(x);
   const unsigned int sign = hw & 0x80000000u;
   const float hi = __uint_as_float(sign | ((unsigned int)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
   const unsigned int r = lw & 0x1fffffffu;  // lo = r 2^(e - 1075), r < 2^29

@@ -258,7 +258,6 @@ __device__ __forceinline__ void mid_fused_any(int r, uint32_t* buf, int logL, co
 }
 
 __device__ __forceinline__ double ldd(const double* p) { return __ldg(p); }
-__device__ __forceinline__ double ldd(const float* p) { return f2d_bits(__ldg(p)); }
 
 // Quantisation pre-pass, one CTA per row: V[k][i] = round(v[k][i] 2^(58 - e_v)) with the row's
 // largest magnitude below 2^e_v (int64, |V| < 2^58); rowscale[k] = 2^(e_v - 58) (0 for a zero row,
@@ -501,15 +500,6 @@ __device__ __forceinline__ int pow2_exponent(double s, bool& fast) {
   return ex - 1023;
 }
 
-// Widened FP32 value times 2^d (|d| <= 1) from the bits for zero and normal f; other f take the FP64 pipe.
-__device__ __forceinline__ double f2d_bits_pow2(float f, int d) {
-  const unsigned int u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0 || ex == 255) return (double)f * (d > 0 ? 2.0 : 0.5);
-  return __hiloint2double((int)((u & 0x80000000u) | ((ex + 896u + (unsigned)d) << 20) | ((u & 0x7fffffu) >> 3)),
-                          (int)((u & 0x7u) << 29));
-}
-
 // The BDF2 band of time row k at element i (Eq. 2.5: row 0 the BDF1 start): v_k, 1.5 v_k - 2 v_{k-1}, or
 // 1.5 v_k - 2 v_{k-1} + 0.5 v_{k-2}; vk points at v_k[i], rows are `stride` apart.  FP32 rows are widened with
 // the factors 2 and 1/2 folded into the exponent (two FP64 operations for a full band instead of three).
@@ -523,9 +513,9 @@ __device__ __forceinline__ double bdf_band(const double* vk, size_t stride, int 
 __device__ __forceinline__ double bdf_band(const float* vk, size_t stride, int k) {
   const double a = f2d_bits(__ldg(vk));
   if (k == 0) return a;
-  const double b2 = -f2d_bits_pow2(__ldg(vk - stride), 1);
+  const double b2 = -f2d_exact(__ldg(vk - stride), 1);
   if (k == 1) return fma(1.5, a, b2);
-  return fma(1.5, a, b2 + f2d_bits_pow2(__ldg(vk - 2 * stride), -1));
+  return fma(1.5, a, b2 + f2d_exact(__ldg(vk - 2 * stride), -1));
 }
 
 // Chunks per row of the epilogue: about 8 elements per thread of a 256-thread CTA, so that a matvec's
@@ -578,7 +568,7 @@ __global__ void __launch_bounds__(256) ntt_epilogue_kernel(const TIn* __restrict
     double out = bdf_band(vk + i, (size_t)M, k) + y;
     if (rk) out = rk[i] - out;
     wk[i] = out;
-    sq += out * out;
+    if constexpr (NVMAX == 0) sq += out * out;  // the fused-dots launch has no sq_partial
     if (NVMAX > 0) {
       const float wh = ff_split(out).x;
 #pragma unroll
@@ -603,6 +593,7 @@ template <typename TIn>
 cudaError_t launch_ntt(const TIn* v, const double* rhs, double* w, double* sq_partial, int M, int Nt, int logL,
                        const NttTables& t, uint32_t* res, double* rowscale, cudaStream_t s,
                        FusedDots fd = FusedDots{nullptr, 0, 0, nullptr}) {
+  if (fd.partial && sq_partial) return cudaErrorInvalidValue;  // the fused-dots epilogue forms no sums of squares
   const int L = 1 << logL;
   const size_t smem = (size_t)(L + L / 32 + 1) * sizeof(uint32_t);
   cudaError_t e = allow_max_dynamic_smem(ntt_conv_kernel);
