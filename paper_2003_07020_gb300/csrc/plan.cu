@@ -883,7 +883,7 @@ aao_status check_problem(const aao_problem* prob, const aao_opts* o) {
   return AAO_OK;
 }
 
-// aao_gmres_solve with each restart cycle replayed as one CUDA graph (1D); nF = ||F|| > 0.
+// aao_gmres_solve with each restart cycle replayed as one CUDA graph (1D and 2D); nF = ||F|| > 0.
 aao_status gmres_solve_graph(aao_plan* p, const double* F, double* U, aao_info* info, double nF,
                              bool zero_guess) {
   if (!p->cycle_exec || p->graph_fno != p->fno) TRY(build_cycle_graph(p));
