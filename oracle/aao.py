@@ -58,7 +58,7 @@ def matvec(K, tau, V):
 
 
 def matvec_rows(g_scaled, V, rows, cols):
-    """Selected entries of calA v, each computed on its own.
+    """Selected entries of calA v (Eq. 12; the Toeplitz product of Sec. 3.2), each computed on its own.
 
     ``g_scaled[d]`` = c * g_d with c = tau*kappa/h^alpha, so that -tau K has
     entries g_scaled[|i-l|].  Returns W[rows[q], cols[q]] for every q:
@@ -81,7 +81,7 @@ def matvec_rows(g_scaled, V, rows, cols):
 
 
 def matvec_2d(Kx, Ky, tau, V):
-    """calA v for the 2D system, K = I (x) Kx + Ky (x) I (x fastest).
+    """calA v for the 2D system (Eq. 12 with K of Eq. 4.2), K = I (x) Kx + Ky (x) I (x fastest).
 
     Row k: sum_j C[k, j] V[j] - tau (V[k] Kx^T + Ky V[k]) with V[k] of shape
     (My, Mx).  Library matmuls only.

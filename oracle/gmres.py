@@ -13,7 +13,8 @@ import numpy as np
 
 
 def fgmres(matvec, precond, F, tol=1e-10, restart=20, max_cycles=50, x0=None):
-    """Solve matvec(U) = F.  ``matvec`` and ``precond`` map arrays of F's
+    """Right-preconditioned restarted flexible GMRES (Sec. 4, the outer solver of Example 1) with modified
+    Gram-Schmidt.  Solve matvec(U) = F.  ``matvec`` and ``precond`` map arrays of F's
     shape to arrays of F's shape.  Returns (U, info) with info holding the
     total number of inner iterations ``iters``, ``cycles`` and the final true
     relative residual ``trr``."""

@@ -89,7 +89,7 @@ def precond_apply(K, tau, eps, V):
 
 
 def time_dft_half(V, eps):
-    """Step-(a) in the unnormalised half-spectrum form used by the GPU path:
+    """Step-(a) (Sec. 3.1, Eq. 1.6a; the half spectrum of Sec. 3.2) in the unnormalised form used by the GPU path:
     zhat_n = sum_k eps^{k/Nt} theta^{n k} v_k for n = 0 .. Nt/2.
 
     Equals sqrt(Nt) z1_n of :func:`precond_apply` (a dense complex matmul with
@@ -126,7 +126,8 @@ def time_idft_half(X, eps, Nt):
 
 
 def strang_symbol(g_scaled, M):
-    """First column s of the Strang circulant of the symmetric Toeplitz matrix
+    """Step (b)'s circulant preconditioner (Sec. 3.1; the paper does not define a spatial Strang form, so
+    the standard one is taken).  First column s of the Strang circulant of the symmetric Toeplitz matrix
     with first column g_scaled[0 .. M-1]: s_k = g_k for k <= M//2 and
     s_k = g_{M-k} otherwise.  Returns (s, eigenvalues), the eigenvalues being
     the DFT of s (real, since s is symmetric)."""
@@ -136,7 +137,7 @@ def strang_symbol(g_scaled, M):
 
 
 def cocg(A, b, Pinv, tol, maxit, x0=None):
-    """Preconditioned COCG for the complex symmetric system A x = b.
+    """Preconditioned COCG for the complex symmetric system A x = b (a shifted system of Step (b), Sec. 3.1).
 
     Conjugate-orthogonal CG (van der Vorst and Melissen): preconditioned CG
     with the bilinear form (u, w) = u^T w instead of u^H w.  ``Pinv`` applies
@@ -172,13 +173,13 @@ def cocg(A, b, Pinv, tol, maxit, x0=None):
 
 
 def shifted_system(g_scaled, M, lam):
-    """Dense lambda I + c T, with c T given by g_scaled (= -tau K)."""
+    """Dense lambda I + c T, with c T given by g_scaled (= -tau K): shifted system n of Step (b), Sec. 3.1."""
     idx = np.abs(np.arange(M)[:, None] - np.arange(M)[None, :])
     return lam * np.eye(M) + g_scaled[idx]
 
 
 def strang_inverse(g_scaled, M, lam):
-    """The map r -> (lambda I + c S)^{-1} r for the Strang circulant S,
+    """Step (b)'s preconditioner solve (Sec. 3.1): the map r -> (lambda I + c S)^{-1} r for the Strang circulant S,
     as a dense solve with the circulant matrix (library routine)."""
     s, _ = strang_symbol(g_scaled, M)
     P = lam * np.eye(M) + sla.circulant(s)
@@ -212,7 +213,8 @@ def dst1_matrix(M):
 
 
 def tau_inverse(g_scaled, M, lam):
-    """The map r -> (lambda I + tau(T))^{-1} r as a dense solve (library routine)."""
+    """The map r -> (lambda I + tau(T))^{-1} r (the tau preconditioner of Sec. 3.2, Eq. 3.9) as a dense solve
+    (library routine)."""
     P = lam * np.eye(M) + tau_matrix(g_scaled, M)
     lu = sla.lu_factor(P)
     return lambda r: sla.lu_solve(lu, r)
@@ -253,7 +255,7 @@ def P_eps_poly_apply(K, tau, eps, V, m, K_pre=None):
 
 
 def P_eps_matvec(K, tau, eps, Z):
-    """P_eps z = vec(Z C_eps^T) - tau vec(K Z) in the row layout (dense C_eps and
+    """P_eps z (Sec. 3.1, P_eps = C_eps (x) I - tau I (x) K) = vec(Z C_eps^T) - tau vec(K Z) in the row layout (dense C_eps and
     K; library matmuls).  For checking a computed z ~= P_eps^{-1} v by its
     residual at sizes where P_eps is too large to form."""
     Z = np.asarray(Z, dtype=np.float64)
@@ -286,7 +288,7 @@ def precond_apply_2d(Kx, Ky, tau, eps, V):
 
 
 def strang2d_inverse(gx_scaled, gy_scaled, Mx, My, lam):
-    """The map r -> (lambda I + I (x) S_x + S_y (x) I)^{-1} r for the 2D Strang (BCCB) preconditioner of the
+    """Step (b)'s 2D preconditioner solve (Sec. 3.1, K of Eq. 4.2).  The map r -> (lambda I + I (x) S_x + S_y (x) I)^{-1} r for the 2D Strang (BCCB) preconditioner of the
     Kronecker-sum system (x fastest, r of shape (My, Mx)): S_x, S_y the Strang circulants of the scaled
     Toeplitz matrices with first columns gx_scaled, gy_scaled (:func:`strang_symbol`).  A BCCB matrix is
     diagonalised by the 2D DFT, so the solve divides the 2D DFT of r by lambda + eig_x[k] + eig_y[l] (library
@@ -298,7 +300,8 @@ def strang2d_inverse(gx_scaled, gy_scaled, Mx, My, lam):
 
 
 def P_eps_matvec_2d(Kx, Ky, tau, eps, Z):
-    """P_eps z for the 2D system: row k is sum_j C_eps[k, j] Z[j] - tau (Z[k] Kx^T + Ky Z[k])."""
+    """P_eps z for the 2D system (Sec. 3.1 with K of Eq. 4.2): row k is sum_j C_eps[k, j] Z[j] - tau (Z[k] Kx^T +
+    Ky Z[k])."""
     Z = np.asarray(Z, dtype=np.float64)
     Nt = Z.shape[0]
     W = np.einsum("kj,jyx->kyx", C_eps(Nt, eps), Z)
