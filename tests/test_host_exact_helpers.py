@@ -2,7 +2,8 @@
 
 The exact-integer matvec (Sec. 3.2, the Toeplitz product c T v_k) rests on steps that must be exact or correctly
 rounded: Garner's CRT of the four residues, the rounding of the reconstructed integer times a power of two to
-FP64, the exact FP32 -> FP64 widening, and the BDF2 band of C (Eq. 1.7).  Their device code is plain integer and
+FP64, the exact FP32 -> FP64 widening, and the BDF2 band of C (Eq. 1.7); the mixed Arnoldi basis rests on the
+FP64 -> float-float split.  Their device code is plain integer and
 floating-point C++, so this test compiles the same source text for the host (the few CUDA intrinsics they use
 are given host definitions) and compares every result with Python's exact Fraction arithmetic, which rounds
 to nearest even like the FP64 conversion it stands in for.
@@ -28,7 +29,11 @@ SHIMS = r"""
 #define __device__
 #define __forceinline__ inline
 #define __restrict__
+#define __noinline__ __attribute__((noinline))
 struct uint2 { uint32_t x, y; };
+struct float2 { float x, y; };
+static inline float __double2float_rn(double x) { return (float)x; }
+static inline float __uint_as_float(unsigned u) { float f; memcpy(&f, &u, 4); return f; }
 static inline int __clz(int x) { return x ? __builtin_clz((unsigned)x) : 32; }
 static inline int __clzll(unsigned long long x) { return x ? __builtin_clzll(x) : 64; }
 static inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
@@ -62,6 +67,12 @@ int main(int argc, char** argv) {
       float f; memcpy(&f, &u, 4);
       printf("%016llx\n", (unsigned long long)__double_as_longlong(f2d_exact(f, d)));
     }
+  } else if (mode == 3) {  // FP64 bits -> ff_split hi, lo as FP32 bits
+    unsigned long long u;
+    while (scanf("%llx", &u) == 1) {
+      const float2 s = ff_split(__longlong_as_double((long long)u));
+      printf("%08x %08x\n", __float_as_uint(s.x), __float_as_uint(s.y));
+    }
   } else {  // v_{k-2} v_{k-1} v_k as FP32 bits, k -> band of FP32 rows and of the same values as FP64 rows
     unsigned a, b, cc; int k;
     while (scanf("%x %x %x %d", &a, &b, &cc, &k) == 4) {
@@ -85,12 +96,14 @@ def _source():
     ntt = open(os.path.join(CSRC, "ntt.cu")).read()
     common = open(os.path.join(CSRC, "common.cuh")).read()
     kern = open(os.path.join(CSRC, "kernels.h")).read()
+    ff = open(os.path.join(CSRC, "ff.cuh")).read()
     primes = _between(kern, "constexpr int kNttPrimes", "constexpr uint32_t kNttGen")
     parts = [
         SHIMS, primes, "constexpr int NP = kNttPrimes;\n",
         _between(ntt, "template <int Q> struct Prime", "__device__ __forceinline__ int pad32"),
         _between(common, "__device__ __forceinline__ double f2d_exact", "// Copies the quarter"),
         _between(ntt, "template <int B> __device__ __forceinline__ uint32_t gstep", "// Chunks per row"),
+        _between(ff, "__device__ __forceinline__ float2 ff_from_double(double x)", "__device__ __forceinline__ float2 ff_mul"),
         MAIN,
     ]
     return "\n".join(parts), [int(x) for x in primes.split("{")[1].split("}")[0].replace("u", "").split(",")]
@@ -231,3 +244,42 @@ def test_bdf2_band_matches_eq_1_7(harness):
             assert abs(Fraction(got) - exact) <= scale / 2 ** 51, (v, k, got)
         if k < 2:
             assert x == y == _round(exact), (v, k, x, y)
+
+
+def test_float_float_split_of_fp64(harness):
+    # the FP64 -> (hi, lo) split of the mixed Arnoldi basis: for 2^-74 <= |x| < 2^127 hi is x cut to 24 significant
+    # bits and lo the rest rounded to FP32, |hi + lo - x| <= 2^-48 |x|; other x take the conversions
+    # (hi = x rounded to FP32, lo = (x - hi) rounded to FP32)
+    import numpy as np
+
+    exe, _ = harness
+    rng = random.Random(17)
+    xs = [0.0, -0.0, 1.0, -1.0, 2.0 ** -74, 2.0 ** -75, 2.0 ** 127, 2.0 ** 127 * 1.5, 2.0 ** 128, 1e-300, 5e-324,
+          float("inf"), float("-inf"), float("nan"), 1.0 + 2.0 ** -30, (1 << 53) - 1.0]
+    for _ in range(30000):
+        r = rng.random()
+        if r < 0.8:
+            x = rng.gauss(0, 1) * 2.0 ** rng.randint(-80, 130)
+        else:
+            x = struct.unpack("<d", struct.pack("<Q", rng.getrandbits(64)))[0]
+        xs.append(x)
+    lines = ["%016x" % struct.unpack("<Q", struct.pack("<d", x))[0] for x in xs]
+    out = _run(exe, 3, lines)
+    for x, o in zip(xs, out):
+        hi, lo = [struct.unpack("<f", struct.pack("<I", int(h, 16)))[0] for h in o.split()]
+        if x != x:
+            assert hi != hi, o
+            continue
+        e = (struct.unpack("<Q", struct.pack("<d", x))[0] >> 52) & 0x7FF
+        if 949 <= e <= 1150:
+            err = abs(Fraction(hi) + Fraction(lo) - Fraction(x))
+            assert err <= abs(Fraction(x)) / 2 ** 48, (x, hi, lo)
+            assert abs(Fraction(hi)) <= abs(Fraction(x)) and (hi == 0.0) == (x == 0.0), (x, hi)
+            assert abs(lo) <= abs(hi) * 2.0 ** -23, (x, hi, lo)
+        else:
+            with np.errstate(over="ignore", invalid="ignore"):
+                want_hi = float(np.float32(x))
+                want_lo = float(np.float32(x - want_hi)) if want_hi == want_hi and abs(want_hi) != float("inf") else None
+            assert hi == want_hi or (hi != hi and want_hi != want_hi), (x, hi, want_hi)
+            if want_lo is not None:
+                assert lo == want_lo, (x, lo, want_lo)
